@@ -1,0 +1,153 @@
+/*
+ * fbim.h -- C ABI of the GB300 fluctuating boundary integral method (FBIM) library.
+ *
+ * The library applies the periodic 2D single-layer Stokeslet matrix M of
+ * Bao, Rachh, Keaveny, Greengard & Donev, "A fluctuating boundary integral
+ * method for Brownian suspensions" (J. Comput. Phys. 2018), by the positively
+ * split Ewald sum (Sec. 3.2), solves the first-kind mobility problem (Sec. 3.1,
+ * Eq. discreteSaddlePoint) with block-diagonal preconditioned GMRES (Sec. 3.4),
+ * draws the random slip M^1/2 W (Sec. 3.3) and advances Brownian rigid bodies
+ * with the Euler-Maruyama random-finite-difference step (Sec. 4.4, Eq. EM-RFD).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Bodies are indexed beta = 0..n_b-1 and carry the same reference shape,
+ *   sampled at n_p equispaced parameters s_j = 2 pi j / n_p (Sec. 3.1).  Node
+ *   m = beta * n_p + j sits at x_m = q_beta + R(theta_beta) gamma_ref(s_j).
+ * - Q (body coordinates) is double [n_b][3] = (q_x, q_y, theta); F (forces and
+ *   torques) and U (velocities and angular velocities) are double [n_b][3].
+ * - Node vectors (forces mu, velocities v, slips) are double [n_b * n_p][2],
+ *   body-major.  mu_m is the force carried by node m (Sec. 3.1, mu = psi Ds).
+ * - "_dev" pointers are device pointers on the handle's device; "_host"
+ *   pointers are host memory.  The caller owns every array it passes; the
+ *   library owns only its workspace, released by fbim_destroy.
+ * - Work is enqueued on the handle's stream (fbim_params.stream).  Calls that
+ *   return scalars (iteration counts, residuals) synchronise that stream.
+ * - Every call returns an fbim_status; no call aborts the process or throws.
+ *   The text of the last error is available from fbim_last_error.
+ * - Viscosity eta and kT enter as given; the paper's tests use eta = kT = 1.
+ */
+#ifndef FBIM_H
+#define FBIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fbim_handle_s* fbim_handle;
+
+typedef enum {
+    FBIM_OK = 0,
+    FBIM_ERR_INVALID_ARG = 1,   /* bad size, pointer or parameter                          */
+    FBIM_ERR_CUDA = 2,          /* a CUDA / cuFFT / cuBLAS call failed                       */
+    FBIM_ERR_OOM = 3,           /* device allocation failed                                  */
+    FBIM_ERR_OVERLAP = 4,       /* two bodies' nodes closer than allowed (quadrature breaks) */
+    FBIM_ERR_NONFINITE = 5,     /* NaN or Inf in an input or an iterate                      */
+    FBIM_ERR_NOT_CONVERGED = 6, /* iteration cap reached; partial result written             */
+    FBIM_ERR_TIMEOUT = 7,       /* a bounded device wait expired                             */
+    FBIM_ERR_SETUP = 8          /* precomputation failed (rule, eigen gap, ...)             */
+} fbim_status;
+
+typedef enum { FBIM_FP64 = 0, FBIM_FP32 = 1 } fbim_precision;
+
+typedef struct {
+    int    precision;     /* fbim_precision of the Ewald operator (pairs, spread, FFT, interp).
+                             Krylov vectors, residuals and the Alpert band are always FP64.   */
+    int    alpert_order;  /* 4 (default) or 8: order of the log-singular correction, Sec. 4.1 */
+    int    grid;          /* FFT grid side M (even); <= 0 selects it from tol, Sec. 3.2        */
+    int    support;       /* Gaussian support P (odd);  <= 0 selects it from tol, Sec. 3.2     */
+    double eta;           /* viscosity, default 1                                               */
+    void*  stream;        /* cudaStream_t to enqueue on; NULL = the legacy default stream       */
+    int    device;        /* CUDA device ordinal, default 0                                     */
+    int    restart;       /* GMRES restart length, default 60                                   */
+} fbim_params;
+
+/* Ewald parameters the library settled on (fbim_get_info). */
+typedef struct {
+    int    n_b, n_p, n_nodes;
+    double L, xi, r_c, tol;
+    int    n_box;         /* cells per side, r_c = L / n_box                      */
+    int    grid;          /* M                                                     */
+    int    support;       /* P                                                     */
+    double eta_s;         /* Gaussian shape parameter of the spreading kernel      */
+    double h;             /* grid spacing L / M                                    */
+    int    alpert_order, alpert_nodes, alpert_window, alpert_band;
+    int    precision;
+} fbim_info;
+
+/* Fill *p with defaults: FP64, order 4, automatic grid and support, eta = 1,
+ * default stream, device 0, restart 60. */
+fbim_status fbim_default_params(fbim_params* p);
+
+/* Parameter rules of Sec. 3.2 (host only, no device needed).
+ * Given the box side L, the cutoff r_c (<= 0: L / 3) and the tolerance tol:
+ *   n_box = floor(L / r_c) (>= 3), r_c = L / n_box,
+ *   xi    = sqrt(ln(C_r / tol)) / r_c with C_r = 100       (real-space error C_r e^{-xi^2 r_c^2} <= tol),
+ *   grid  = smallest even 2^a 3^b 5^c 7^d >= xi L sqrt(ln(C_w / tol)) * 2 / pi, C_w = 1
+ *                                                         (wave-space error C_w e^{-k_max^2/4xi^2} <= tol),
+ *   P     = smallest odd >= 2 ln(1/tol) / pi               (NUFFT error e^{-pi P/2} <= tol),
+ *   eta_s = (2 w xi / m)^2 with w = P h / 2, m = sqrt(pi P) (Gaussian shape; grid is refined
+ *                                                          until eta_s < 1).
+ * xi_in > 0 overrides xi.  Any output pointer may be NULL. */
+fbim_status fbim_choose_ewald(double L, double r_c, double tol, double xi_in,
+                              int* n_box, double* r_c_out, double* xi, int* grid,
+                              int* support, double* eta_s);
+
+/* Create a handle for n_b bodies of one shape.
+ *   ref_nodes_host: double [n_p][2], gamma_ref(s_j) relative to the tracking point.
+ *   Q_host:         double [n_b][3], initial body coordinates.
+ *   L:              periodic box side.  r_c: real-space cutoff (<= 0: automatic).
+ *   xi:             splitting parameter (<= 0: from tol).  tol: Ewald tolerance.
+ *   opt:            NULL for defaults.
+ * Precomputes the Alpert band of the reference body (Sec. 3.2, rotated per body),
+ * sorts the nodes into cells, plans the FFTs.  Returns FBIM_ERR_OVERLAP if two
+ * bodies' nodes are closer than 1e-12 L. */
+fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const double* ref_nodes_host,
+                       const double* Q_host, double L, double r_c, double xi, double tol,
+                       const fbim_params* opt);
+
+/* Move the bodies: Q_dev double [n_b][3] (device).  Rebuilds node positions and cells. */
+fbim_status fbim_update_config(fbim_handle h, const double* Q_dev);
+
+/* v = M mu with M = M(t) + M(a)_sym + M(w) (Sec. 3.2).  mu_dev, v_dev: double [N][2]. */
+fbim_status fbim_apply_stokeslet(fbim_handle h, const double* mu_dev, double* v_dev);
+
+/* v = M(r) mu = (M(t) + M(a)_sym) mu, the real-space part only (Sec. 3.2, Eq. Mreal-decompose). */
+fbim_status fbim_apply_real(fbim_handle h, const double* mu_dev, double* v_dev);
+
+/* v = M(w) mu, the wave-space part only (Sec. 3.2, Eq. Mwave-factorization). */
+fbim_status fbim_apply_wave(fbim_handle h, const double* mu_dev, double* v_dev);
+
+/* Information about the handle's parameters. */
+fbim_status fbim_get_info(fbim_handle h, fbim_info* info);
+
+/* Per-stage CUDA-event timers of the operator (tracing).  With timing on, every
+ * operator call records an event after each stage on the handle's stream and
+ * synchronises at its end; fbim_stage_times returns the accumulated milliseconds
+ * and call counts of the stages, in this order: gather, spread, forward FFT,
+ * Fourier scale, inverse FFT, real-space pairs, interpolation, finish (scatter +
+ * Alpert band).  Turning timing on or off resets the accumulators. */
+fbim_status fbim_set_timing(fbim_handle h, int on);
+fbim_status fbim_stage_times(fbim_handle h, double* ms, long long* calls, int n);
+
+/* Release the handle and its device workspace.  NULL is accepted. */
+void fbim_destroy(fbim_handle h);
+
+/* Text of the last error on h (or of the last failed fbim_setup when h is NULL). */
+const char* fbim_last_error(fbim_handle h);
+
+/* Host E1(z) as used by the library's setup (exponential integral, Sec. 3.2 Eq. expint);
+ * exported so that its accuracy can be tested without a GPU. */
+double fbim_host_expint_e1(double z);
+
+/* Nodes v_k and weights w_k of the library's log-singular end correction (Sec. 3.1) and
+ * its window a; v and w must hold order - 1 doubles.  Host only. */
+fbim_status fbim_host_alpert_rule(int order, double* v, double* w, int* a);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FBIM_H */

@@ -147,11 +147,12 @@ def apply_real_rows(X: np.ndarray, mu: np.ndarray, rows, L: float, xi: float, et
     Xf = X.reshape(-1, 2)
     out = np.zeros((len(rows), 2))
     cache = {}
+    src = np.nonzero(np.any(mu != 0.0, axis=1))[0]      # zero forces contribute nothing
     for t, m in enumerate(rows):
-        r = Xf[m] - Xf
+        r = Xf[m] - Xf[src]
         G = ewald.g_real_periodic(r, L, xi, eta)
-        G[m] = 0.0
-        out[t] = np.einsum("nab,nb->a", G, mu)
+        G[src == m] = 0.0
+        out[t] = np.einsum("nab,nb->a", G, mu[src])
         b = m // n_p
         if b not in cache:
             Ma = alpert_body(X[b], xi, eta, order)
@@ -162,17 +163,30 @@ def apply_real_rows(X: np.ndarray, mu: np.ndarray, rows, L: float, xi: float, et
 
 
 def apply_wave_rows(Xf: np.ndarray, mu: np.ndarray, rows, L: float, xi: float, eta: float = 1.0,
-                    modes=None, chunk: int = 200000) -> np.ndarray:
-    """M(w) mu at listed rows by the direct non-uniform Fourier sum (sources: nonzero mu only)."""
-    kvec, B = modes if modes is not None else ewald.wave_modes(L, xi)
+                    cut: float = ewald.WAVE_CUT) -> np.ndarray:
+    """M(w) mu at listed rows by the direct non-uniform Fourier sum (sources: nonzero mu only).
+
+    The lattice sum over kappa in [-K, K]^2 with k^2/(4 xi^2) <= cut uses the
+    separability e^{-i k.x} = e^{-i k_x x} e^{-i k_y y}: the source transform
+    S(kappa) = sum_n mu_n e^{-i k.x_n} is the matrix product Ex^T diag(mu) Ey.
+    """
+    kmax = 2.0 * xi * np.sqrt(cut)
+    K = int(np.ceil(kmax * L / (2.0 * np.pi)))
+    kap = np.arange(-K, K + 1) * (2.0 * np.pi / L)
     src = np.nonzero(np.any(mu != 0.0, axis=1))[0]
-    out = np.zeros((len(rows), 2))
-    for k0 in range(0, kvec.shape[0], chunk):
-        kv = kvec[k0:k0 + chunk]
-        Bk = B[k0:k0 + chunk]
-        ph = Xf[src] @ kv.T                                     # [S, K]
-        Shat = np.exp(-1j * ph).T @ mu[src]                     # [K, 2]
-        u = np.einsum("kab,kb->ka", Bk, Shat)                   # [K, 2]
-        e = np.exp(1j * (Xf[rows] @ kv.T))                      # [R, K]
-        out += np.real(e @ u)
+    Ex = np.exp(-1j * np.outer(Xf[src, 0], kap))            # [S, 2K+1]
+    Ey = np.exp(-1j * np.outer(Xf[src, 1], kap))
+    Sx = Ex.T @ (mu[src, 0:1] * Ey)                          # [kx, ky]
+    Sy = Ex.T @ (mu[src, 1:2] * Ey)
+    kx, ky = np.meshgrid(kap, kap, indexing="ij")
+    k2 = kx * kx + ky * ky
+    keep = (k2 > 0) & (k2 / (4.0 * xi * xi) <= cut)
+    k2s = np.where(keep, k2, 1.0)
+    sc = np.where(keep, ewald.hasimoto(np.sqrt(k2s), xi) / k2s, 0.0)
+    Ux = sc * ((1.0 - kx * kx / k2s) * Sx - kx * ky / k2s * Sy)
+    Uy = sc * (-kx * ky / k2s * Sx + (1.0 - ky * ky / k2s) * Sy)
+    Fx = np.exp(1j * np.outer(Xf[rows, 0], kap))             # [R, 2K+1]
+    Fy = np.exp(1j * np.outer(Xf[rows, 1], kap))
+    out = np.stack([np.real(np.sum((Fx @ Ux) * Fy, axis=1)),
+                    np.real(np.sum((Fx @ Uy) * Fy, axis=1))], axis=1)
     return out / (eta * L * L)

@@ -1,0 +1,214 @@
+"""GB300 FBIM: Python binding of the C ABI in include/fbim.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``libfbim.so`` built in-tree by ``paper_1709_01480_gb300.build``.  There is no
+CPU fallback; importing this package without the built library raises.
+
+Arrays are torch tensors on the handle's device (float64, contiguous) or raw
+device addresses (int).  Host-side inputs of ``FBIM(...)`` are numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfbim.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_1709_01480_gb300.build` "
+        "(there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FBIM_FP64, FBIM_FP32 = 0, 1
+STATUS = {0: "FBIM_OK", 1: "FBIM_ERR_INVALID_ARG", 2: "FBIM_ERR_CUDA", 3: "FBIM_ERR_OOM",
+          4: "FBIM_ERR_OVERLAP", 5: "FBIM_ERR_NONFINITE", 6: "FBIM_ERR_NOT_CONVERGED",
+          7: "FBIM_ERR_TIMEOUT", 8: "FBIM_ERR_SETUP"}
+
+# every symbol declared in include/fbim.h
+EXPORTS = [
+    "fbim_default_params", "fbim_choose_ewald", "fbim_setup", "fbim_update_config",
+    "fbim_apply_stokeslet", "fbim_apply_real", "fbim_apply_wave", "fbim_get_info",
+    "fbim_destroy", "fbim_last_error", "fbim_host_expint_e1", "fbim_host_alpert_rule",
+    "fbim_set_timing", "fbim_stage_times",
+]
+STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
+
+
+class FbimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("alpert_order", ctypes.c_int), ("grid", ctypes.c_int),
+                ("support", ctypes.c_int), ("eta", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int), ("restart", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_b", ctypes.c_int), ("n_p", ctypes.c_int), ("n_nodes", ctypes.c_int),
+                ("L", ctypes.c_double), ("xi", ctypes.c_double), ("r_c", ctypes.c_double),
+                ("tol", ctypes.c_double), ("n_box", ctypes.c_int), ("grid", ctypes.c_int),
+                ("support", ctypes.c_int), ("eta_s", ctypes.c_double), ("h", ctypes.c_double),
+                ("alpert_order", ctypes.c_int), ("alpert_nodes", ctypes.c_int),
+                ("alpert_window", ctypes.c_int), ("alpert_band", ctypes.c_int), ("precision", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+_lib.fbim_default_params.argtypes = [ctypes.POINTER(Params)]
+_lib.fbim_choose_ewald.argtypes = [_D, _D, _D, _D, _IP, _DP, _DP, _IP, _IP, _DP]
+_lib.fbim_setup.argtypes = [ctypes.POINTER(_P), _I, _I, _DP, _DP, _D, _D, _D, _D, ctypes.POINTER(Params)]
+_lib.fbim_update_config.argtypes = [_P, _P]
+_lib.fbim_apply_stokeslet.argtypes = [_P, _P, _P]
+_lib.fbim_apply_real.argtypes = [_P, _P, _P]
+_lib.fbim_apply_wave.argtypes = [_P, _P, _P]
+_lib.fbim_get_info.argtypes = [_P, ctypes.POINTER(Info)]
+_lib.fbim_destroy.argtypes = [_P]
+_lib.fbim_destroy.restype = None
+_lib.fbim_last_error.argtypes = [_P]
+_lib.fbim_last_error.restype = ctypes.c_char_p
+_lib.fbim_host_expint_e1.argtypes = [_D]
+_lib.fbim_host_expint_e1.restype = _D
+_lib.fbim_host_alpert_rule.argtypes = [_I, _DP, _DP, _IP]
+_lib.fbim_set_timing.argtypes = [_P, _I]
+_lib.fbim_stage_times.argtypes = [_P, _DP, ctypes.POINTER(ctypes.c_longlong), _I]
+
+
+def lib():
+    return _lib
+
+
+def _check(status, handle=None):
+    if status != 0:
+        msg = _lib.fbim_last_error(handle)
+        raise FbimError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def host_expint_e1(z: float) -> float:
+    return _lib.fbim_host_expint_e1(float(z))
+
+
+def host_alpert_rule(order: int = 4):
+    v = np.zeros(order - 1)
+    w = np.zeros(order - 1)
+    a = ctypes.c_int(0)
+    _check(_lib.fbim_host_alpert_rule(order, _dptr(v), _dptr(w), ctypes.byref(a)))
+    return v, w, a.value
+
+
+def choose_ewald(L, r_c, tol, xi=0.0):
+    nb, M, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc, x, es = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.fbim_choose_ewald(L, r_c, tol, xi, ctypes.byref(nb), ctypes.byref(rc), ctypes.byref(x),
+                                  ctypes.byref(M), ctypes.byref(P), ctypes.byref(es)))
+    return dict(n_box=nb.value, r_c=rc.value, xi=x.value, grid=M.value, support=P.value, eta_s=es.value)
+
+
+class FBIM:
+    """One suspension of rigid bodies of a single shape in a periodic box."""
+
+    def __init__(self, ref_nodes, Q, L, *, tol=1e-8, r_c=0.0, xi=0.0, precision="fp64", order=4,
+                 grid=0, support=0, eta=1.0, stream=None, device=0, restart=60):
+        ref = np.ascontiguousarray(ref_nodes, dtype=np.float64)
+        Qh = np.ascontiguousarray(Q, dtype=np.float64)
+        self.n_p = ref.shape[0]
+        self.n_b = Qh.shape[0]
+        p = Params()
+        _lib.fbim_default_params(ctypes.byref(p))
+        p.precision = FBIM_FP32 if precision == "fp32" else FBIM_FP64
+        p.alpert_order = order
+        p.grid = grid
+        p.support = support
+        p.eta = eta
+        p.device = device
+        p.restart = restart
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        p.stream = stream
+        self._stream = stream
+        h = ctypes.c_void_p()
+        _check(_lib.fbim_setup(ctypes.byref(h), self.n_b, self.n_p, _dptr(ref), _dptr(Qh), float(L),
+                               float(r_c), float(xi), float(tol), ctypes.byref(p)))
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def info(self):
+        i = Info()
+        _check(_lib.fbim_get_info(self._h, ctypes.byref(i)), self._h)
+        return i.as_dict()
+
+    @property
+    def n(self):
+        return self.n_b * self.n_p
+
+    def _out(self, like, shape):
+        import torch
+        return torch.empty(shape, dtype=torch.float64, device=like.device)
+
+    def apply_stokeslet(self, mu, out=None):
+        v = out if out is not None else self._out(mu, (self.n, 2))
+        _check(_lib.fbim_apply_stokeslet(self._h, _ptr(mu), _ptr(v)), self._h)
+        return v
+
+    def apply_real(self, mu, out=None):
+        v = out if out is not None else self._out(mu, (self.n, 2))
+        _check(_lib.fbim_apply_real(self._h, _ptr(mu), _ptr(v)), self._h)
+        return v
+
+    def apply_wave(self, mu, out=None):
+        v = out if out is not None else self._out(mu, (self.n, 2))
+        _check(_lib.fbim_apply_wave(self._h, _ptr(mu), _ptr(v)), self._h)
+        return v
+
+    def set_timing(self, on: bool):
+        _check(_lib.fbim_set_timing(self._h, 1 if on else 0), self._h)
+
+    def stage_times(self):
+        ms = np.zeros(len(STAGES))
+        calls = (ctypes.c_longlong * len(STAGES))()
+        _check(_lib.fbim_stage_times(self._h, _dptr(ms), calls, len(STAGES)), self._h)
+        return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(STAGES)}
+
+    def update_config(self, Q_dev):
+        _check(_lib.fbim_update_config(self._h, _ptr(Q_dev)), self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.fbim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,305 @@
+// C ABI entry points: handle life cycle and the Ewald operators.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "fbim_internal.h"
+
+using fbim::set_global_error;
+
+namespace {
+
+template <typename F>
+fbim_status guarded(fbim_handle h, F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        if (h) h->fail("host allocation failed");
+        return FBIM_ERR_OOM;
+    } catch (...) {
+        if (h) h->fail("unexpected host exception");
+        return FBIM_ERR_SETUP;
+    }
+}
+
+void release(fbim_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    for (auto& e : h->ev)
+        if (e) cudaEventDestroy(e);
+    fbim::free_ewald(h);
+    cudaFree(h->ref);
+    cudaFree(h->Q);
+    cudaFree(h->x);
+    cudaFree(h->cell);
+    cudaFree(h->cell_start);
+    cudaFree(h->cell_fill);
+    cudaFree(h->perm);
+    cudaFree(h->slot);
+    cudaFree(h->flags);
+    cudaFree(h->band_dev);
+    delete h;
+}
+
+fbim_status check_flags(fbim_handle h) {
+    int f[4];
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(f, h->flags, sizeof(f), cudaMemcpyDeviceToHost, h->stream));
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (f[0]) {
+        h->fail("non-finite body coordinates");
+        return FBIM_ERR_NONFINITE;
+    }
+    if (f[1]) {
+        h->fail("two nodes coincide (overlapping bodies)");
+        return FBIM_ERR_OVERLAP;
+    }
+    return FBIM_OK;
+}
+
+}  // namespace
+
+extern "C" fbim_status fbim_default_params(fbim_params* p) {
+    if (!p) return FBIM_ERR_INVALID_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->precision = FBIM_FP64;
+    p->alpert_order = 4;
+    p->grid = 0;
+    p->support = 0;
+    p->eta = 1.0;
+    p->stream = nullptr;
+    p->device = 0;
+    p->restart = 60;
+    return FBIM_OK;
+}
+
+extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const double* ref_nodes_host,
+                                  const double* Q_host, double L, double r_c, double xi, double tol,
+                                  const fbim_params* opt) {
+    if (!out || n_b <= 0 || n_p < 8 || !ref_nodes_host || !Q_host || !(L > 0) || !(tol > 0 && tol < 1)) {
+        set_global_error("fbim_setup: invalid argument");
+        return FBIM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    fbim_params p;
+    fbim_default_params(&p);
+    if (opt) p = *opt;
+    if (p.precision != FBIM_FP64 && p.precision != FBIM_FP32) {
+        set_global_error("fbim_setup: precision must be FBIM_FP64 or FBIM_FP32");
+        return FBIM_ERR_INVALID_ARG;
+    }
+    if ((long long)n_b * n_p > (1LL << 30)) {
+        set_global_error("fbim_setup: too many nodes");
+        return FBIM_ERR_INVALID_ARG;
+    }
+    fbim_handle h = new (std::nothrow) fbim_handle_s();
+    if (!h) return FBIM_ERR_OOM;
+    fbim_status st = guarded(h, [&]() -> fbim_status {
+        h->n_b = n_b;
+        h->n_p = n_p;
+        h->N = n_b * n_p;
+        h->L = L;
+        h->tol = tol;
+        h->eta = p.eta > 0 ? p.eta : 1.0;
+        h->order = p.alpert_order ? p.alpert_order : 4;
+        h->precision = p.precision;
+        h->device = p.device;
+        h->restart = p.restart > 0 ? p.restart : 60;
+        h->stream = (cudaStream_t)p.stream;
+        h->host_ref.assign(ref_nodes_host, ref_nodes_host + 2 * n_p);
+        for (int i = 0; i < 3 * n_b; ++i)
+            if (!std::isfinite(Q_host[i])) {
+                h->fail("non-finite body coordinates");
+                return FBIM_ERR_NONFINITE;
+            }
+        FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
+        // the end-correction rule fixes the band; r_c defaults to r_Alpert / 0.6 (Sec. 4.1)
+        std::vector<double> v, w;
+        int a;
+        std::string err;
+        if (fbim::alpert_rule(h->order, v, w, a, err) != FBIM_OK) {
+            h->fail(err);
+            return FBIM_ERR_SETUP;
+        }
+        int band = a - 1;
+        for (double vk : v) band = std::max(band, (int)std::floor(vk) + (h->order + 2) / 2);
+        if (2 * band + 1 > n_p) {
+            h->fail("n_p too small for the Alpert correction band");
+            return FBIM_ERR_INVALID_ARG;
+        }
+        double r_alpert = 0;
+        for (int i = 0; i < n_p; ++i) {
+            int k = (i + band) % n_p;
+            double dx = ref_nodes_host[2 * i] - ref_nodes_host[2 * k];
+            double dy = ref_nodes_host[2 * i + 1] - ref_nodes_host[2 * k + 1];
+            r_alpert = std::max(r_alpert, std::sqrt(dx * dx + dy * dy));
+        }
+        double rc_req = r_c > 0 ? r_c : r_alpert / 0.6;
+        if (rc_req > L / 3) rc_req = L / 3;
+        int nbox, M, P;
+        double rc, xx, es;
+        if (fbim::choose_ewald(L, rc_req, tol, xi, nbox, rc, xx, M, P, es, err) != FBIM_OK) {
+            h->fail(err);
+            return FBIM_ERR_INVALID_ARG;
+        }
+        if (p.grid > 0) M = p.grid + (p.grid & 1);
+        if (p.support > 0) P = p.support | 1;
+        h->n_box = nbox;
+        h->r_c = rc;
+        h->xi = xx;
+        h->M = M;
+        h->P = P;
+        h->h = L / M;
+        {
+            double wdt = P * h->h / 2.0, m = std::sqrt(M_PI * P);
+            h->eta_s = std::pow(2.0 * wdt * h->xi / m, 2);
+        }
+        if (!(h->eta_s < 1.0) || P > M || P > 31) {
+            h->fail("Gaussian support/grid inconsistent (need eta_s < 1, P <= min(M, 31))");
+            return FBIM_ERR_INVALID_ARG;
+        }
+        std::vector<double> bandv;
+        FBIM_TRY(fbim::alpert_reference_band(h, bandv));
+        const size_t N = h->N, nc = (size_t)h->n_cell();
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->ref, 2 * n_p * sizeof(double)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->Q, 3 * n_b * sizeof(double)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->x, 2 * N * sizeof(double)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->cell, N * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->cell_start, (nc + 1) * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->cell_fill, nc * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->perm, N * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->slot, N * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->flags, 4 * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->band_dev, bandv.size() * sizeof(double)));
+        FBIM_CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, 4 * sizeof(int), h->stream));
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(h->ref, ref_nodes_host, 2 * n_p * sizeof(double), cudaMemcpyHostToDevice,
+                                         h->stream));
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(h->Q, Q_host, 3 * n_b * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(h->band_dev, bandv.data(), bandv.size() * sizeof(double),
+                                         cudaMemcpyHostToDevice, h->stream));
+        FBIM_TRY(fbim::build_geometry(h));
+        if (h->precision == FBIM_FP32) FBIM_TRY(fbim::ensure_ewald<float>(h));
+        FBIM_TRY(fbim::ensure_ewald<double>(h));
+        return check_flags(h);
+    });
+    if (st != FBIM_OK) {
+        set_global_error(h->err);
+        release(h);
+        return st;
+    }
+    *out = h;
+    return FBIM_OK;
+}
+
+extern "C" fbim_status fbim_update_config(fbim_handle h, const double* Q_dev) {
+    if (!h || !Q_dev) return FBIM_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> fbim_status {
+        FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(h->Q, Q_dev, 3 * h->n_b * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+        return fbim::build_geometry(h);
+    });
+}
+
+static fbim_status apply_which(fbim_handle h, const double* mu, double* v, int which) {
+    if (!h || !mu || !v) return FBIM_ERR_INVALID_ARG;
+    if ((((uintptr_t)mu) | ((uintptr_t)v)) & 15) {
+        h->fail("mu and v must be 16-byte aligned");
+        return FBIM_ERR_INVALID_ARG;
+    }
+    return guarded(h, [&]() -> fbim_status {
+        FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
+        if (h->precision == FBIM_FP32) return fbim::apply_operator<float>(h, mu, v, which);
+        return fbim::apply_operator<double>(h, mu, v, which);
+    });
+}
+
+extern "C" fbim_status fbim_apply_stokeslet(fbim_handle h, const double* mu_dev, double* v_dev) {
+    return apply_which(h, mu_dev, v_dev, 3);
+}
+
+extern "C" fbim_status fbim_apply_real(fbim_handle h, const double* mu_dev, double* v_dev) {
+    return apply_which(h, mu_dev, v_dev, 1);
+}
+
+extern "C" fbim_status fbim_apply_wave(fbim_handle h, const double* mu_dev, double* v_dev) {
+    return apply_which(h, mu_dev, v_dev, 2);
+}
+
+extern "C" fbim_status fbim_get_info(fbim_handle h, fbim_info* info) {
+    if (!h || !info) return FBIM_ERR_INVALID_ARG;
+    info->n_b = h->n_b;
+    info->n_p = h->n_p;
+    info->n_nodes = h->N;
+    info->L = h->L;
+    info->xi = h->xi;
+    info->r_c = h->r_c;
+    info->tol = h->tol;
+    info->n_box = h->n_box;
+    info->grid = h->M;
+    info->support = h->P;
+    info->eta_s = h->eta_s;
+    info->h = h->h;
+    info->alpert_order = h->order;
+    info->alpert_nodes = h->aj;
+    info->alpert_window = h->aa;
+    info->alpert_band = h->band;
+    info->precision = h->precision;
+    return FBIM_OK;
+}
+
+extern "C" void fbim_destroy(fbim_handle h) { release(h); }
+
+extern "C" const char* fbim_last_error(fbim_handle h) { return h ? h->err.c_str() : fbim::global_error(); }
+
+// ---------------------------------------------------------------------------
+// Stage timing
+// ---------------------------------------------------------------------------
+void fbim_handle_s::mark_begin() {
+    if (!timing) return;
+    cudaEventRecord(ev[0], stream);
+    n_ev = 1;
+}
+
+void fbim_handle_s::mark(int stage) {
+    if (!timing || n_ev <= 0 || n_ev >= 16) return;
+    cudaEventRecord(ev[n_ev], stream);
+    ev_stage[n_ev] = stage;
+    ++n_ev;
+}
+
+void fbim_handle_s::collect() {
+    if (!timing || n_ev < 2) return;
+    cudaEventSynchronize(ev[n_ev - 1]);
+    for (int i = 1; i < n_ev; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+        stage_ms[ev_stage[i]] += ms;
+        stage_calls[ev_stage[i]] += 1;
+    }
+    n_ev = 0;
+}
+
+extern "C" fbim_status fbim_set_timing(fbim_handle h, int on) {
+    if (!h) return FBIM_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> fbim_status {
+        FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
+        if (on && !h->ev[0])
+            for (auto& e : h->ev) FBIM_CUDA_TRY(h, cudaEventCreate(&e));
+        h->timing = on != 0;
+        for (int i = 0; i < FBIM_N_STAGES; ++i) {
+            h->stage_ms[i] = 0;
+            h->stage_calls[i] = 0;
+        }
+        h->n_ev = 0;
+        return FBIM_OK;
+    });
+}
+
+extern "C" fbim_status fbim_stage_times(fbim_handle h, double* ms, long long* calls, int n) {
+    if (!h || !ms || n <= 0) return FBIM_ERR_INVALID_ARG;
+    for (int i = 0; i < n && i < FBIM_N_STAGES; ++i) {
+        ms[i] = h->stage_ms[i];
+        if (calls) calls[i] = h->stage_calls[i];
+    }
+    return FBIM_OK;
+}

@@ -1,0 +1,134 @@
+// Internal state and helpers of the FBIM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cublas_v2.h>
+
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/fbim.h"
+
+// stage ids for the operator's event timers
+enum {
+    FBIM_ST_GATHER = 0, FBIM_ST_SPREAD, FBIM_ST_FFT_F, FBIM_ST_SCALE, FBIM_ST_FFT_I,
+    FBIM_ST_PAIRS, FBIM_ST_INTERP, FBIM_ST_FINISH, FBIM_N_STAGES
+};
+
+namespace fbim {
+
+// ---------------------------------------------------------------------------
+// Error plumbing: every internal call returns fbim_status; the message lands
+// in the handle (or in a thread-local slot before a handle exists).
+// ---------------------------------------------------------------------------
+void set_global_error(const std::string& msg);
+const char* global_error();
+
+#define FBIM_CUDA_TRY(h, expr)                                                         \
+    do {                                                                               \
+        cudaError_t e__ = (expr);                                                      \
+        if (e__ != cudaSuccess) {                                                      \
+            (h)->fail(std::string(#expr) + ": " + cudaGetErrorString(e__));            \
+            return e__ == cudaErrorMemoryAllocation ? FBIM_ERR_OOM : FBIM_ERR_CUDA;    \
+        }                                                                              \
+    } while (0)
+
+#define FBIM_CUFFT_TRY(h, expr)                                                        \
+    do {                                                                               \
+        cufftResult r__ = (expr);                                                      \
+        if (r__ != CUFFT_SUCCESS) {                                                    \
+            (h)->fail(std::string(#expr) + ": cufft error " + std::to_string((int)r__)); \
+            return FBIM_ERR_CUDA;                                                      \
+        }                                                                              \
+    } while (0)
+
+#define FBIM_TRY(expr)                                                                 \
+    do {                                                                               \
+        fbim_status s__ = (expr);                                                      \
+        if (s__ != FBIM_OK) return s__;                                                \
+    } while (0)
+
+// Device buffers of one precision of the Ewald operator.
+template <typename T>
+struct EwaldBuffers {
+    void* off = nullptr;     // [N] T2: node offset from its cell's lower corner, cell-sorted
+    int2* gbase = nullptr;   // [N] nearest grid point (ix, iy) of each node, cell-sorted
+    void* gfrac = nullptr;   // [N] T2: x / h - base, in [-1/2, 1/2], cell-sorted
+    void* mu_s = nullptr;    // [N] T2: forces in cell-sorted order
+    void* v_s = nullptr;     // [N] T2: velocities in cell-sorted order
+    T* grid = nullptr;       // [2][M][M] real grid (component-major)
+    void* spec = nullptr;    // [2][M][M/2+1] complex half spectrum
+    cufftHandle plan_f = 0;  // R2C / D2Z, batch 2
+    cufftHandle plan_i = 0;  // C2R / Z2D, batch 2
+    bool ready = false;
+};
+
+}  // namespace fbim
+
+struct fbim_handle_s {
+    // ---- parameters -------------------------------------------------------
+    int n_b = 0, n_p = 0, N = 0;
+    double L = 0, xi = 0, r_c = 0, tol = 0, eta = 1;
+    int n_box = 0, M = 0, P = 0;
+    double eta_s = 0, h = 0;
+    int order = 4, aj = 0, aa = 0, band = 0;  // Alpert: nodes per side, window, half band
+    int precision = FBIM_FP64;
+    int device = 0;
+    int restart = 60;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // ---- geometry (device) -------------------------------------------------
+    double* ref = nullptr;       // [n_p][2]
+    double* Q = nullptr;         // [n_b][3]
+    double* x = nullptr;         // [N][2] node positions wrapped into [0, L)
+    int* cell = nullptr;         // [N] cell id of each node (body order)
+    int* cell_start = nullptr;   // [n_cell + 1]
+    int* cell_fill = nullptr;    // [n_cell]
+    int* perm = nullptr;         // [N] slot -> node
+    int* slot = nullptr;         // [N] node -> slot
+    int* flags = nullptr;        // [4] device error flags
+    double* band_dev = nullptr;  // [n_p][2 band + 1][2][2] symmetrised M(a)_ref
+
+    fbim::EwaldBuffers<double> e64;
+    fbim::EwaldBuffers<float> e32;
+
+    std::vector<double> host_ref;
+
+    // ---- stage timing (fbim_set_timing) ------------------------------------
+    bool timing = false;
+    cudaEvent_t ev[16] = {};
+    int n_ev = 0;
+    int ev_stage[16] = {};
+    double stage_ms[FBIM_N_STAGES] = {};
+    long long stage_calls[FBIM_N_STAGES] = {};
+    void mark(int stage);          // record an event closing `stage` (no-op unless timing)
+    void mark_begin();             // record the opening event of a timed operator call
+    void collect();                // synchronise and accumulate the recorded intervals
+
+    int n_cell() const { return n_box * n_box; }
+    void fail(const std::string& m) { err = m; }
+};
+
+namespace fbim {
+
+// host setup pieces (setup_host.cu)
+double host_e1(double z);
+fbim_status alpert_rule(int order, std::vector<double>& v, std::vector<double>& w, int& a, std::string& err);
+fbim_status alpert_reference_band(fbim_handle_s* h, std::vector<double>& band_out);
+fbim_status choose_ewald(double L, double r_c, double tol, double xi_in, int& n_box, double& r_c_out,
+                         double& xi, int& M, int& P, double& eta_s, std::string& err);
+
+// geometry (geometry.cu)
+fbim_status build_geometry(fbim_handle_s* h);
+
+// operators (ewald_ops.cu)
+template <typename T> fbim_status ensure_ewald(fbim_handle_s* h);
+template <typename T> fbim_status refresh_offsets(fbim_handle_s* h);
+// which: bit 0 = real space (pairs + Alpert), bit 1 = wave space
+template <typename T> fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int which);
+void free_ewald(fbim_handle_s* h);
+
+}  // namespace fbim

@@ -1,0 +1,177 @@
+"""GPU parity of the Ewald matvec v = M mu (Sec. 3.2) against the CPU oracle.
+
+Bar: FP64 path within 1e-10 of the oracle (relative to max |v|) at Ewald
+tolerance 1e-12 on both sides; FP32 path within 2e-5 (float rounding of the
+pair sum, spreading, FFT and interpolation, about 1e-6 each, with margin).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import fbim_synth
+from oracle import singlelayer
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 2e-5
+
+
+def _xi(L, n_box, tol):
+    # Sec. 3.2 real-space rule with C_r = 100: xi = sqrt(ln(C_r / tol)) / r_c
+    return math.sqrt(math.log(100.0 / tol)) / (L / n_box)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    return t
+
+
+@pytest.fixture(scope="module")
+def fb():
+    import paper_1709_01480_gb300 as fb
+    return fb
+
+
+def _case(n_b, n_p, L, seed, gap=0.2):
+    ref = fbim_synth.starfish_ref_nodes(n_p)
+    Q = fbim_synth.place_bodies(n_b, L, ref, gap, seed)
+    return ref, Q
+
+
+def _oracle_parts(ref, Q, L, xi, order=4):
+    X = singlelayer.node_positions(Q, ref)
+    M, (Mt, Ma, Mw) = singlelayer.single_layer(X, L, xi, order=order, parts=True)
+    return M, Mt + Ma, Mw
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+CASES = [
+    # (n_b, n_p, L, seed, n_box) -- tiny workload, a ragged 3-body case, a 12-body case
+    (4, 64, 4.0, 0, 6),
+    (3, 48, 3.2, 5, 4),
+    (12, 32, 5.0, 9, 7),
+]
+
+
+@pytest.mark.parametrize("n_b,n_p,L,seed,n_box", CASES)
+def test_fp64_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
+    ref, Q = _case(n_b, n_p, L, seed)
+    tol = 1e-12
+    xi = _xi(L, n_box, tol)
+    op = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, precision="fp64")
+    assert op.info["n_box"] == n_box
+    M, Mr, Mw = _oracle_parts(ref, Q, L, xi)
+    rng = np.random.default_rng(seed + 100)
+    mu = rng.standard_normal((n_b * n_p, 2))
+    mu_d = torch.tensor(mu, dtype=torch.float64, device="cuda")
+    for fn, A in ((op.apply_real, Mr), (op.apply_wave, Mw), (op.apply_stokeslet, M)):
+        v = fn(mu_d).cpu().numpy()
+        expect = (A @ mu.reshape(-1)).reshape(-1, 2)
+        assert _rel(v, expect) < FP64_TOL, (fn.__name__, _rel(v, expect))
+    op.close()
+
+
+@pytest.mark.parametrize("n_b,n_p,L,seed,n_box", CASES[:2])
+def test_fp32_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
+    ref, Q = _case(n_b, n_p, L, seed)
+    tol = 1e-8
+    xi = _xi(L, n_box, tol)
+    op = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, precision="fp32")
+    M, Mr, Mw = _oracle_parts(ref, Q, L, xi)
+    rng = np.random.default_rng(seed + 200)
+    mu = rng.standard_normal((n_b * n_p, 2))
+    mu_d = torch.tensor(mu, dtype=torch.float64, device="cuda")
+    for fn, A in ((op.apply_real, Mr), (op.apply_wave, Mw), (op.apply_stokeslet, M)):
+        v = fn(mu_d).cpu().numpy()
+        expect = (A @ mu.reshape(-1)).reshape(-1, 2)
+        assert _rel(v, expect) < FP32_TOL, (fn.__name__, _rel(v, expect))
+    op.close()
+
+
+def test_single_body_and_zero_input(torch, fb):
+    ref, Q = _case(1, 64, 3.0, 1)
+    xi = _xi(3.0, 4, 1e-12)
+    op = fb.FBIM(ref, Q, 3.0, tol=1e-12, r_c=0.75, xi=xi)
+    M, _, _ = _oracle_parts(ref, Q, 3.0, xi)
+    mu = np.random.default_rng(3).standard_normal((64, 2))
+    v = op.apply_stokeslet(torch.tensor(mu, device="cuda")).cpu().numpy()
+    assert _rel(v, (M @ mu.reshape(-1)).reshape(-1, 2)) < FP64_TOL
+    z = op.apply_stokeslet(torch.zeros((64, 2), dtype=torch.float64, device="cuda"))
+    assert float(z.abs().max()) == 0.0
+    op.close()
+
+
+def test_update_config_moves_bodies(torch, fb):
+    ref, Q = _case(4, 64, 4.0, 0)
+    xi = _xi(4.0, 6, 1e-12)
+    op = fb.FBIM(ref, Q, 4.0, tol=1e-12, r_c=4.0 / 6, xi=xi)
+    Q2 = Q.copy()
+    Q2[:, 0] += 1.3          # translate across the periodic boundary
+    Q2[:, 2] += 0.4          # rotate
+    op.update_config(torch.tensor(Q2, device="cuda"))
+    M, _, _ = _oracle_parts(ref, Q2, 4.0, xi)
+    mu = np.random.default_rng(4).standard_normal((256, 2))
+    v = op.apply_stokeslet(torch.tensor(mu, device="cuda")).cpu().numpy()
+    assert _rel(v, (M @ mu.reshape(-1)).reshape(-1, 2)) < FP64_TOL
+    op.close()
+
+
+N_BOX_FULL = 115   # r_c ~ 0.504 on the 1024-starfish box
+
+
+@pytest.fixture(scope="module")
+def full_size():
+    """131072 nodes at Ewald tolerance 1e-8: forces on one body, sampled target rows.
+
+    The oracle sums the real space over all images and the wave space over all
+    modes with k^2/4xi^2 <= 30 (terms beyond are < 1e-13 of the leading ones).
+    """
+    w = fbim_synth.workload("starfish1024_np128_phi0.25")
+    xi = _xi(w.L, N_BOX_FULL, w.tol)
+    X = singlelayer.node_positions(w.Q, w.ref_nodes)
+    src_body = 17
+    mu = np.zeros((w.n, 2))
+    rng = np.random.default_rng(11)
+    mu[src_body * w.n_p:(src_body + 1) * w.n_p] = rng.standard_normal((w.n_p, 2))
+    d = np.linalg.norm((w.Q[:, :2] - w.Q[src_body, :2] + w.L / 2) % w.L - w.L / 2, axis=1)
+    near = np.argsort(d)[1:4]
+    rows = list(range(src_body * w.n_p, src_body * w.n_p + w.n_p, 8))
+    for b in near:
+        rows += list(range(b * w.n_p, (b + 1) * w.n_p, 16))
+    rows += [int(r) for r in rng.choice(w.n, 24, replace=False)]
+    expect = (singlelayer.apply_real_rows(X, mu, rows, w.L, xi)
+              + singlelayer.apply_wave_rows(X.reshape(-1, 2), mu, rows, w.L, xi, cut=30.0))
+    return w, xi, mu, rows, expect
+
+
+@pytest.mark.parametrize("precision,tol_rel", [("fp64", 1e-7), ("fp32", 3e-5)])
+def test_full_size_sampled_rows_match_oracle(torch, fb, full_size, precision, tol_rel):
+    # the GPU truncates at its 1e-8 Ewald tolerance: the bar is a small multiple of it
+    w, xi, mu, rows, expect = full_size
+    op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=w.L / N_BOX_FULL, xi=xi, precision=precision)
+    v = op.apply_stokeslet(torch.tensor(mu, device="cuda")).cpu().numpy()
+    got = v[rows]
+    assert _rel(got, expect) < tol_rel, _rel(got, expect)
+    op.close()
+
+
+def test_full_size_operator_is_symmetric_and_positive(torch, fb, full_size):
+    w = full_size[0]
+    op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=w.L / N_BOX_FULL, precision="fp64")
+    g = torch.Generator(device="cuda").manual_seed(5)
+    mu = torch.randn((w.n, 2), dtype=torch.float64, device="cuda", generator=g)
+    nu = torch.randn((w.n, 2), dtype=torch.float64, device="cuda", generator=g)
+    Mmu = op.apply_stokeslet(mu)
+    Mnu = op.apply_stokeslet(nu)
+    a = float((nu * Mmu).sum())
+    b = float((mu * Mnu).sum())
+    assert abs(a - b) <= 1e-12 * float(Mmu.abs().sum()) * float(nu.abs().max())
+    assert float((mu * Mmu).sum()) > 0.0
+    op.close()
