@@ -86,8 +86,10 @@ fbim_status fbim_default_params(fbim_params* p);
  * Given the box side L, the cutoff r_c (<= 0: L / 3) and the tolerance tol:
  *   n_box = floor(L / r_c) (>= 3), r_c = L / n_box,
  *   xi    = sqrt(ln(C_r / tol)) / r_c with C_r = 100       (real-space error C_r e^{-xi^2 r_c^2} <= tol),
- *   grid  = smallest even 2^a 3^b 5^c 7^d >= xi L sqrt(ln(C_w / tol)) * 2 / pi, C_w = 1
- *                                                         (wave-space error C_w e^{-k_max^2/4xi^2} <= tol),
+ *   grid  = smallest even 2^a 3^b 5^c 7^d >= k_max L / pi, with k_max the smallest
+ *           wavenumber where C_w H^(k_max) = C_w (1 + q) e^{-q} <= tol, q = k_max^2/4xi^2,
+ *           C_w = 1 (the paper's wave-space bound C_w e^{-q} <= tol, with the Hasimoto
+ *           prefactor 1 + q kept),
  *   P     = smallest odd >= 2 ln(1/tol) / pi               (NUFFT error e^{-pi P/2} <= tol),
  *   eta_s = (2 w xi / m)^2 with w = P h / 2, m = sqrt(pi P) (Gaussian shape; grid is refined
  *                                                          until eta_s < 1).

@@ -51,7 +51,7 @@ double host_e1(double zd) {
 }
 
 // ---------------------------------------------------------------------------
-// Parameter rules (Sec. 3.2): C_r e^{-xi^2 r_c^2} <= tol, C_w e^{-k_max^2/4 xi^2} <= tol,
+// Parameter rules (Sec. 3.2): C_r e^{-xi^2 r_c^2} <= tol, C_w H^(k_max) <= tol,
 // e^{-pi P / 2} <= tol, m = sqrt(pi P), eta_s = (2 w xi / m)^2 with w = P h / 2.
 // ---------------------------------------------------------------------------
 static bool nice_size(int n) {
@@ -81,7 +81,12 @@ fbim_status choose_ewald(double L, double r_c, double tol, double xi_in, int& n_
     }
     r_c_out = L / n_box;
     xi = xi_in > 0 ? xi_in : std::sqrt(std::log(C_r / tol)) / r_c_out;
-    double kmax = 2.0 * xi * std::sqrt(std::log(C_w / tol));
+    // Wave space: the first dropped mode must satisfy C_w H^(k_max) <= tol, where the
+    // Hasimoto factor H^ = (1 + q) e^{-q}, q = k^2/4xi^2, carries the polynomial
+    // prefactor that a bare C_w e^{-q} bound leaves out.  Solve q = ln(C_w/tol) + ln(1 + q).
+    double q = std::log(C_w / tol);
+    for (int it = 0; it < 50; ++it) q = std::log(C_w / tol) + std::log1p(q);
+    double kmax = 2.0 * xi * std::sqrt(q);
     M = next_nice_even((int)std::ceil(kmax * L / M_PI));
     P = (int)std::ceil(2.0 * std::log(1.0 / tol) / M_PI);
     if (P % 2 == 0) ++P;

@@ -63,8 +63,8 @@ def test_parameter_rules_bound_the_truncation_errors(fb):
         p = fb.choose_ewald(L, rc, tol)
         xi, M, P = p["xi"], p["grid"], p["support"]
         assert 100 * math.exp(-(xi * p["r_c"]) ** 2) <= tol * (1 + 1e-9)
-        kmax = math.pi * M / L
-        assert math.exp(-kmax ** 2 / (4 * xi ** 2)) <= tol
+        q = (math.pi * M / L) ** 2 / (4 * xi ** 2)
+        assert (1 + q) * math.exp(-q) <= tol          # Hasimoto weight of the first dropped mode
         assert P % 2 == 1 and math.exp(-math.pi * P / 2) <= tol
         assert M % 2 == 0 and 0 < p["eta_s"] < 1
 

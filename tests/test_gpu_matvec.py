@@ -1,8 +1,9 @@
 """GPU parity of the Ewald matvec v = M mu (Sec. 3.2) against the CPU oracle.
 
-Bar: FP64 path within 1e-10 of the oracle (relative to max |v|) at Ewald
-tolerance 1e-12 on both sides; FP32 path within 2e-5 (float rounding of the
-pair sum, spreading, FFT and interpolation, about 1e-6 each, with margin).
+Bar: FP64 path within 1e-10 of the oracle (relative to max |v|) with the
+library's Ewald tolerance at 1e-13 (its truncations then sit near 1e-12,
+the oracle's near 1e-20); FP32 path within 2e-5 (float rounding of the pair
+sum, spreading, FFT and interpolation; measured 2.6e-7 to 4.3e-7).
 """
 import math
 
@@ -15,7 +16,7 @@ from oracle import singlelayer
 pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-10
-FP32_TOL = 2e-5
+FP32_TOL = 2e-6
 
 
 def _xi(L, n_box, tol):
@@ -56,14 +57,14 @@ CASES = [
     # (n_b, n_p, L, seed, n_box) -- tiny workload, a ragged 3-body case, a 12-body case
     (4, 64, 4.0, 0, 6),
     (3, 48, 3.2, 5, 4),
-    (12, 32, 5.0, 9, 7),
+    (12, 32, 6.5, 9, 8),
 ]
 
 
 @pytest.mark.parametrize("n_b,n_p,L,seed,n_box", CASES)
 def test_fp64_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
     ref, Q = _case(n_b, n_p, L, seed)
-    tol = 1e-12
+    tol = 1e-13
     xi = _xi(L, n_box, tol)
     op = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, precision="fp64")
     assert op.info["n_box"] == n_box
@@ -74,6 +75,7 @@ def test_fp64_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
     for fn, A in ((op.apply_real, Mr), (op.apply_wave, Mw), (op.apply_stokeslet, M)):
         v = fn(mu_d).cpu().numpy()
         expect = (A @ mu.reshape(-1)).reshape(-1, 2)
+        print(f"fp64 {n_b}x{n_p} {fn.__name__}: rel err {_rel(v, expect):.3e}")
         assert _rel(v, expect) < FP64_TOL, (fn.__name__, _rel(v, expect))
     op.close()
 
@@ -91,14 +93,15 @@ def test_fp32_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
     for fn, A in ((op.apply_real, Mr), (op.apply_wave, Mw), (op.apply_stokeslet, M)):
         v = fn(mu_d).cpu().numpy()
         expect = (A @ mu.reshape(-1)).reshape(-1, 2)
+        print(f"fp32 {n_b}x{n_p} {fn.__name__}: rel err {_rel(v, expect):.3e}")
         assert _rel(v, expect) < FP32_TOL, (fn.__name__, _rel(v, expect))
     op.close()
 
 
 def test_single_body_and_zero_input(torch, fb):
     ref, Q = _case(1, 64, 3.0, 1)
-    xi = _xi(3.0, 4, 1e-12)
-    op = fb.FBIM(ref, Q, 3.0, tol=1e-12, r_c=0.75, xi=xi)
+    xi = _xi(3.0, 4, 1e-13)
+    op = fb.FBIM(ref, Q, 3.0, tol=1e-13, r_c=0.75, xi=xi)
     M, _, _ = _oracle_parts(ref, Q, 3.0, xi)
     mu = np.random.default_rng(3).standard_normal((64, 2))
     v = op.apply_stokeslet(torch.tensor(mu, device="cuda")).cpu().numpy()
@@ -110,8 +113,8 @@ def test_single_body_and_zero_input(torch, fb):
 
 def test_update_config_moves_bodies(torch, fb):
     ref, Q = _case(4, 64, 4.0, 0)
-    xi = _xi(4.0, 6, 1e-12)
-    op = fb.FBIM(ref, Q, 4.0, tol=1e-12, r_c=4.0 / 6, xi=xi)
+    xi = _xi(4.0, 6, 1e-13)
+    op = fb.FBIM(ref, Q, 4.0, tol=1e-13, r_c=4.0 / 6, xi=xi)
     Q2 = Q.copy()
     Q2[:, 0] += 1.3          # translate across the periodic boundary
     Q2[:, 2] += 0.4          # rotate
@@ -158,6 +161,7 @@ def test_full_size_sampled_rows_match_oracle(torch, fb, full_size, precision, to
     op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=w.L / N_BOX_FULL, xi=xi, precision=precision)
     v = op.apply_stokeslet(torch.tensor(mu, device="cuda")).cpu().numpy()
     got = v[rows]
+    print(f"full size {precision}: rel err {_rel(got, expect):.3e}")
     assert _rel(got, expect) < tol_rel, _rel(got, expect)
     op.close()
 
