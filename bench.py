@@ -245,10 +245,19 @@ def run_gpu(args):
 
     M, N = info["grid"], w.n
     n_pairs = pair_count(singlelayer_positions(w), w.L, info["r_c"])
-    algo_bytes = {  # minimum DRAM bytes per launch, FP32 operator
-        "gather": N * (4 + 16 + 8), "spread": 24 * N + 8 * M * M, "fft_fwd": 8 * M * M + 16 * M * (M // 2 + 1),
-        "scale": 32 * M * (M // 2 + 1), "fft_inv": 16 * M * (M // 2 + 1) + 8 * M * M,
-        "interp": 8 * M * M + 32 * N, "finish": N * (4 + 8 + 16 + 16),
+    n_entries = info["pair_entries"]
+    # minimum DRAM bytes per launch of each stage, FP32 operator (grids: 2 components x 4 B;
+    # half spectrum: 2 x M (M/2 + 1) complex x 8 B; node vectors: 8 B per node and order)
+    spec_b = 16 * M * (M // 2 + 1)
+    algo_bytes = {
+        "gather": N * (4 + 4 + 16 + 8 + 8),            # perm, tperm, mu (FP64), two FP32 copies
+        "spread": 24 * N + 8 * M * M,                   # tbase, tfrac, mu_t; grid written once
+        "fft_fwd": 8 * M * M + spec_b,
+        "scale": 2 * spec_b,
+        "fft_inv": spec_b + 8 * M * M,
+        "pairs": 16 * n_entries + 8 * N + 8 * N,        # pair list streamed once, mu_s, v_s
+        "interp": 8 * M * M + 24 * N + 8 * N,
+        "finish": N * (4 + 4 + 8 + 8 + 16 + 16) + 16 * N,   # slots, v_s, v_t, mu band reads, v
     }
     st32 = stage["fp32"]
     hbm_stages = {k: v_ for k, v_ in st32.items() if k in algo_bytes}
@@ -284,7 +293,7 @@ def run_gpu(args):
         val, t_full, sample = oracle_matvec_rate(w, xi)
         cpu = {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
 
-    launches_per_step = 8  # gather, spread, scale, pairs, interp, finish + 2 cuFFT calls (library)
+    launches_per_step = 6  # gather, spread, scale, pairs, interp, finish (+ 2 cuFFT calls, library)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -292,7 +301,9 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_nodes": N, "n_bodies": w.n_b, "box": w.L, "tol": w.tol,
                        "xi": info["xi"], "r_c": info["r_c"], "grid": M, "support": info["support"],
-                       "n_pairs_within_rc": n_pairs, "l2": "flushed (256 MB write) before every timed step",
+                       "n_pairs_within_rc": n_pairs, "pair_entries": n_entries, "tile": info["tile"],
+                       "wave_variant": info["wave_variant"], "variant_ms": info["variant_ms"],
+                       "l2": "flushed (256 MB write) before every timed step",
                        "operator": "FP32 Ewald operator, FP64 Alpert band"},
             "plain_fp64": {"value": world * w.n / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64},
             "stage_ms": {"fp32": st32, "fp64": stage["fp64"]},
@@ -320,7 +331,7 @@ def singlelayer_positions(w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -63,6 +63,8 @@ typedef struct {
     void*  stream;        /* cudaStream_t to enqueue on; NULL = the legacy default stream       */
     int    device;        /* CUDA device ordinal, default 0                                     */
     int    restart;       /* GMRES restart length, default 60                                   */
+    int    autotune;      /* wave-space kernels: 1 (default) time both variants at setup and keep
+                             the faster; 0 shared-memory tile kernels; 2 warp-per-node kernels */
 } fbim_params;
 
 /* Ewald parameters the library settled on (fbim_get_info). */
@@ -76,6 +78,11 @@ typedef struct {
     double h;             /* grid spacing L / M                                    */
     int    alpert_order, alpert_nodes, alpert_window, alpert_band;
     int    precision;
+    int    tile;          /* wave-space tile side (divides grid)                   */
+    long long pair_entries;  /* stored real-space pair entries of the handle's precision
+                                (ordered pairs within r_c plus sliced-ELL padding)     */
+    int    wave_variant;     /* spread/interp kernels in use: 0 tile, 1 warp-per-node  */
+    double variant_ms[2];    /* autotuner timings (ms) of spread + interp per variant  */
 } fbim_info;
 
 /* Fill *p with defaults: FP64, order 4, automatic grid and support, eta = 1,

@@ -38,6 +38,12 @@ void release(fbim_handle h) {
     cudaFree(h->slot);
     cudaFree(h->flags);
     cudaFree(h->band_dev);
+    cudaFree(h->gbase);
+    cudaFree(h->tile_start);
+    cudaFree(h->tile_fill);
+    cudaFree(h->tperm);
+    cudaFree(h->tslot);
+    cudaFree(h->tile_tmp);
     delete h;
 }
 
@@ -69,6 +75,7 @@ extern "C" fbim_status fbim_default_params(fbim_params* p) {
     p->stream = nullptr;
     p->device = 0;
     p->restart = 60;
+    p->autotune = 1;
     return FBIM_OK;
 }
 
@@ -104,6 +111,7 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         h->precision = p.precision;
         h->device = p.device;
         h->restart = p.restart > 0 ? p.restart : 60;
+        h->autotune = p.autotune;
         h->stream = (cudaStream_t)p.stream;
         h->host_ref.assign(ref_nodes_host, ref_nodes_host + 2 * n_p);
         for (int i = 0; i < 3 * n_b; ++i)
@@ -143,6 +151,32 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         }
         if (p.grid > 0) M = p.grid + (p.grid & 1);
         if (p.support > 0) P = p.support | 1;
+        // wave-space tiles: TS divides M, TS <= 64, and a node's window (P - 1)/2 points
+        // to each side never reaches past the neighbouring tile
+        auto tile_side = [](int m) {
+            int best = 0;
+            for (int d = 1; d <= 64 && d <= m; ++d)
+                if (m % d == 0) best = d;
+            return best;
+        };
+        int TS = tile_side(M);
+        while (TS < std::max(16, (P - 1) / 2) && TS < M) {
+            if (p.grid > 0) {
+                h->fail("grid side must have a divisor in [16, 64] (wave-space tiling)");
+                return FBIM_ERR_INVALID_ARG;
+            }
+            M += 2;
+            while (true) {
+                int r = M;
+                for (int f : {2, 3, 5, 7})
+                    while (r % f == 0) r /= f;
+                if (r == 1) break;
+                M += 2;
+            }
+            TS = tile_side(M);
+        }
+        h->TS = TS;
+        h->n_tile = M / TS;
         h->n_box = nbox;
         h->r_c = rc;
         h->xi = xx;
@@ -153,12 +187,25 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
             double wdt = P * h->h / 2.0, m = std::sqrt(M_PI * P);
             h->eta_s = std::pow(2.0 * wdt * h->xi / m, 2);
         }
-        if (!(h->eta_s < 1.0) || P > M || P > 31) {
-            h->fail("Gaussian support/grid inconsistent (need eta_s < 1, P <= min(M, 31))");
+        if (!(h->eta_s < 1.0) || P > M || P > 23) {
+            h->fail("Gaussian support/grid inconsistent (need eta_s < 1, P <= min(M, 23), i.e. tol >= 1e-15)");
             return FBIM_ERR_INVALID_ARG;
         }
         std::vector<double> bandv;
         FBIM_TRY(fbim::alpert_reference_band(h, bandv));
+        // Chebyshev series of the smooth part of E1 on [0, xi^2 r_c^2]
+        h->zmax = h->xi * h->xi * h->r_c * h->r_c * (1.0 + 1e-6);
+        {
+            std::vector<double> c64, c32;
+            fbim::e1_chebyshev(h->zmax, 44, c64);
+            fbim::e1_chebyshev(h->zmax, 30, c32);
+            h->cheb64.deg = 44;
+            h->cheb64.scale = 2.0 / h->zmax;
+            for (int k = 0; k <= 44; ++k) h->cheb64.c[k] = c64[k];
+            h->cheb32.deg = 30;
+            h->cheb32.scale = (float)(2.0 / h->zmax);
+            for (int k = 0; k <= 30; ++k) h->cheb32.c[k] = (float)c32[k];
+        }
         const size_t N = h->N, nc = (size_t)h->n_cell();
         FBIM_CUDA_TRY(h, cudaMalloc(&h->ref, 2 * n_p * sizeof(double)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->Q, 3 * n_b * sizeof(double)));
@@ -170,6 +217,13 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         FBIM_CUDA_TRY(h, cudaMalloc(&h->slot, N * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->flags, 4 * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->band_dev, bandv.size() * sizeof(double)));
+        const size_t ntl = (size_t)h->n_tile * h->n_tile;
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->gbase, N * sizeof(int2)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->tile_start, (ntl + 1) * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->tile_fill, ntl * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->tperm, N * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->tslot, N * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->tile_tmp, N * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, 4 * sizeof(int), h->stream));
         FBIM_CUDA_TRY(h, cudaMemcpyAsync(h->ref, ref_nodes_host, 2 * n_p * sizeof(double), cudaMemcpyHostToDevice,
                                          h->stream));
@@ -244,6 +298,12 @@ extern "C" fbim_status fbim_get_info(fbim_handle h, fbim_info* info) {
     info->alpert_window = h->aa;
     info->alpert_band = h->band;
     info->precision = h->precision;
+    info->tile = h->TS;
+    const bool f32 = h->precision == FBIM_FP32;
+    info->pair_entries = f32 ? h->e32.n_padded : h->e64.n_padded;
+    info->wave_variant = f32 ? h->e32.wave_variant : h->e64.wave_variant;
+    info->variant_ms[0] = f32 ? h->e32.variant_ms[0] : h->e64.variant_ms[0];
+    info->variant_ms[1] = f32 ? h->e32.variant_ms[1] : h->e64.variant_ms[1];
     return FBIM_OK;
 }
 

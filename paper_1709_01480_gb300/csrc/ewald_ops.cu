@@ -7,69 +7,40 @@
 //                Gaussian spread S, forward FFT F, the Hasimoto tensor B with both
 //                deconvolutions C folded in, inverse FFT, Gaussian interpolation S*.
 //
-// All node-indexed work runs in cell-sorted order (slot s holds node perm[s]);
-// the final kernel scatters back to body order and adds the Alpert band.
+// Layouts.  Real-space work runs in cell-sorted order (slot s holds node perm[s]).
+// Per geometry, the pairs within r_c are found once from the cell list and their
+// 2 x 2 kernel values stored in a sliced-ELL list (slices of 32 consecutive
+// targets, entries interleaved so that a warp reads 32 consecutive entries); a
+// matvec then streams the list once -- the real-space part is applied tens of
+// times per geometry inside GMRES and Lanczos, so its transcendental work
+// (E1, exp) is paid once.
+// Wave-space work runs in grid-tile order (slot t holds node tperm[t]): the grid
+// is cut into TS x TS tiles (TS divides M) and every node belongs to the tile of
+// its nearest grid point.  Spreading is owner-computes: one CTA per tile
+// accumulates, in shared memory, the Gaussians of the nodes of its own and its
+// eight neighbouring tiles that reach into it (one thread per node, P unrolled),
+// then writes its tile once -- no global atomics.  Interpolation loads the tile
+// plus a halo of (P-1)/2 points into shared memory and gathers each of the
+// tile's nodes from there.  The final kernel scatters both parts back to body
+// order and adds the Alpert band.
+//
 // Templated on the operator precision T (double: parity path; float: fast path).
 #include <cmath>
 
 #include "fbim_internal.h"
+#include "ewald_types.cuh"
 
 namespace fbim {
-
-template <typename T> struct V2;
-template <> struct V2<double> { using type = double2; };
-template <> struct V2<float> { using type = float2; };
-
-template <typename T> struct Cplx;
-template <> struct Cplx<double> { using type = cufftDoubleComplex; };
-template <> struct Cplx<float> { using type = cufftComplex; };
-
-// ---------------------------------------------------------------------------
-// E1(z) for z > 0 on the device: power series below z0, bottom-up continued
-// fraction e^{-z}/(z + 1 - 1/(z + 3 - 4/(z + 5 - ...))) above (the classical
-// expansions, Abramowitz & Stegun 5.1.11 and 5.1.22).  Term counts are fixed
-// per precision: relative error <= 1e-13 (double) and <= 2e-7 (float).
-// ---------------------------------------------------------------------------
-template <typename T> struct E1Cfg;
-template <> struct E1Cfg<double> { static constexpr double z0 = 3.0; static constexpr int ns = 36, nc = 26; };
-template <> struct E1Cfg<float> { static constexpr float z0 = 2.0f; static constexpr int ns = 14, nc = 12; };
-
-__device__ __forceinline__ double dev_exp(double a) { return exp(a); }
-__device__ __forceinline__ float dev_exp(float a) { return __expf(a); }
-__device__ __forceinline__ double dev_log(double a) { return log(a); }
-__device__ __forceinline__ float dev_log(float a) { return __logf(a); }
-
-template <typename T>
-__device__ __forceinline__ T e1_times_half_minus_exp(T z, T& e_out) {
-    // returns E1(z)/2 - e^{-z}; e_out = e^{-z}
-    T e = dev_exp(-z);
-    e_out = e;
-    T r;
-    if (z < E1Cfg<T>::z0) {
-        T term = T(1), sum = T(0);
-#pragma unroll
-        for (int k = 1; k <= E1Cfg<T>::ns; ++k) {
-            term *= -z / T(k);
-            sum += term / T(k);
-        }
-        r = T(-0.57721566490153286061) - dev_log(z) - sum;
-    } else {
-        T f = z + T(2 * E1Cfg<T>::nc + 1);
-#pragma unroll
-        for (int k = E1Cfg<T>::nc; k >= 1; --k) f = z + T(2 * k - 1) - T(k * k) / f;
-        r = e / f;
-    }
-    return T(0.5) * r - e;
-}
 
 // ---------------------------------------------------------------------------
 // Layout kernels
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_offsets(int N, const int* __restrict__ perm, const double* __restrict__ x,
-                          const int* __restrict__ cell, int n_box, double r_c, double h, int M,
-                          typename V2<T>::type* __restrict__ off, int2* __restrict__ gbase,
-                          typename V2<T>::type* __restrict__ gfrac) {
+__global__ void k_offsets(int N, const int* __restrict__ perm, const int* __restrict__ tperm,
+                          const double* __restrict__ x, const int* __restrict__ cell,
+                          const int2* __restrict__ gbase, int n_box, double r_c, double h,
+                          typename V2<T>::type* __restrict__ off, int2* __restrict__ tbase,
+                          typename V2<T>::type* __restrict__ tfrac) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     int m = perm[s];
@@ -78,41 +49,47 @@ __global__ void k_offsets(int N, const int* __restrict__ perm, const double* __r
     int cx = c % n_box, cy = c / n_box;
     off[s].x = (T)(px - cx * r_c);
     off[s].y = (T)(py - cy * r_c);
-    double gx = px / h, gy = py / h;
-    double bx = rint(gx), by = rint(gy);
-    gbase[s] = make_int2(((int)bx) % M, ((int)by) % M);
-    gfrac[s].x = (T)(gx - bx);
-    gfrac[s].y = (T)(gy - by);
+    int mt = tperm[s];
+    double qx = x[2 * mt] / h, qy = x[2 * mt + 1] / h;
+    tbase[s] = gbase[mt];
+    tfrac[s].x = (T)(qx - rint(qx));
+    tfrac[s].y = (T)(qy - rint(qy));
 }
 
 template <typename T>
-__global__ void k_gather(int N, const int* __restrict__ perm, const double2* __restrict__ mu,
-                         typename V2<T>::type* __restrict__ mu_s) {
+__global__ void k_gather(int N, const int* __restrict__ perm, const int* __restrict__ tperm, int want_s, int want_t,
+                         const double2* __restrict__ mu, typename V2<T>::type* __restrict__ mu_s,
+                         typename V2<T>::type* __restrict__ mu_t) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
-    double2 v = mu[perm[s]];
-    mu_s[s].x = (T)v.x;
-    mu_s[s].y = (T)v.y;
+    if (want_s) {
+        double2 v = mu[perm[s]];
+        mu_s[s].x = (T)v.x;
+        mu_s[s].y = (T)v.y;
+    }
+    if (want_t) {
+        double2 v = mu[tperm[s]];
+        mu_t[s].x = (T)v.x;
+        mu_t[s].y = (T)v.y;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Real space: v_t = sum_{n != t, r < r_c} G^(r)(x_t - x_n) mu_n over the 9 cells
-// around t's cell.  One thread per target in cell-sorted order: neighbouring
-// threads share most source cells, which stay in L1.
+// around t's cell.  The visit order below (cells dy, dx; slots ascending) is the
+// column order of each row of the pair list.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(128) k_pairs(int N, int n_box, T r_c, T rc2, T xi2, T pref,
-                                              const int* __restrict__ perm, const int* __restrict__ cell,
-                                              const int* __restrict__ start,
-                                              const typename V2<T>::type* __restrict__ off,
-                                              const typename V2<T>::type* __restrict__ mu_s,
-                                              typename V2<T>::type* __restrict__ v_s, int* __restrict__ flags) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
+template <typename T> struct PairEntry;
+template <> struct __align__(16) PairEntry<float> { float xx, xy, yy; int src; };
+template <> struct __align__(16) PairEntry<double> { double xx, xy, yy; long long src; };
+
+template <typename T, typename F>
+__device__ __forceinline__ void for_each_pair(int t, int n_box, T r_c, T rc2, const int* __restrict__ perm,
+                                              const int* __restrict__ cell, const int* __restrict__ start,
+                                              const typename V2<T>::type* __restrict__ off, F&& f) {
     int c = cell[perm[t]];
     int cx = c % n_box, cy = c / n_box;
     typename V2<T>::type ot = off[t];
-    T ax = 0, ay = 0;
     for (int dy = -1; dy <= 1; ++dy) {
         int ny = cy + dy;
         ny += (ny < 0) ? n_box : 0;
@@ -129,68 +106,119 @@ __global__ void __launch_bounds__(128) k_pairs(int N, int n_box, T r_c, T rc2, T
                 typename V2<T>::type os = off[s];
                 T rx = sx - os.x, ry = sy - os.y;
                 T r2 = rx * rx + ry * ry;
-                if (r2 < rc2 && s != t) {
-                    if (r2 == T(0)) {
-                        atomicOr(&flags[1], 1);
-                        continue;
-                    }
-                    T e;
-                    T a = e1_times_half_minus_exp<T>(xi2 * r2, e);
-                    T b = e / r2;
-                    typename V2<T>::type ms = mu_s[s];
-                    T rm = rx * ms.x + ry * ms.y;
-                    ax += a * ms.x + b * rx * rm;
-                    ay += a * ms.y + b * ry * rm;
-                }
+                if (r2 < rc2 && s != t) f(s, rx, ry, r2);
             }
         }
     }
-    v_s[t].x = pref * ax;
-    v_s[t].y = pref * ay;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_pair_count(int N, int n_box, T r_c, T rc2, const int* __restrict__ perm,
+                                                   const int* __restrict__ cell, const int* __restrict__ start,
+                                                   const typename V2<T>::type* __restrict__ off,
+                                                   int* __restrict__ row_count, int* __restrict__ flags) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    int n = 0;
+    for_each_pair<T>(t, n_box, r_c, rc2, perm, cell, start, off, [&](int, T, T, T r2) {
+        if (r2 == T(0))
+            atomicOr(&flags[1], 1);
+        else
+            ++n;
+    });
+    row_count[t] = n;
+}
+
+// slice_start[s] = sum over earlier slices of the longest row in the slice (one block)
+__global__ void k_slice_scan(int n_slice, int N, const int* __restrict__ row_count, int* __restrict__ slice_start) {
+    __shared__ int part[1024];
+    int tid = threadIdx.x;
+    int per = (n_slice + blockDim.x - 1) / blockDim.x;
+    int lo = min(n_slice, tid * per), hi = min(n_slice, lo + per);
+    auto len = [&](int sl) {
+        int mx = 0;
+        for (int l = 0; l < 32; ++l) {
+            int t = sl * 32 + l;
+            if (t < N) mx = max(mx, row_count[t]);
+        }
+        return mx;
+    };
+    int s = 0;
+    for (int i = lo; i < hi; ++i) s += len(i);
+    part[tid] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        int v = tid >= o ? part[tid - o] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int run = tid > 0 ? part[tid - 1] : 0;
+    for (int i = lo; i < hi; ++i) {
+        slice_start[i] = run;
+        run += len(i);
+    }
+    if (tid == blockDim.x - 1) slice_start[n_slice] = part[tid];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_pair_fill(int N, int n_box, T r_c, T rc2, T xi2, T pref, ChebE1<T> ce,
+                                                  const int* __restrict__ perm, const int* __restrict__ cell,
+                                                  const int* __restrict__ start,
+                                                  const typename V2<T>::type* __restrict__ off,
+                                                  const int* __restrict__ slice_start,
+                                                  PairEntry<T>* __restrict__ pairs) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const int sl = t >> 5, lane = t & 31;
+    const int base = slice_start[sl], len = slice_start[sl + 1] - base;
+    PairEntry<T>* row = pairs + (size_t)base * 32 + lane;
+    int k = 0;
+    for_each_pair<T>(t, n_box, r_c, rc2, perm, cell, start, off, [&](int s, T rx, T ry, T r2) {
+        if (r2 == T(0)) return;
+        T z = xi2 * r2;
+        T a = kernel_a<T>(ce, z);
+        T b = dev_div(dev_exp(-z), r2);
+        PairEntry<T> e;
+        e.xx = pref * (a + b * rx * rx);
+        e.xy = pref * (b * rx * ry);
+        e.yy = pref * (a + b * ry * ry);
+        e.src = s;
+        row[(size_t)k * 32] = e;
+        ++k;
+    });
+    for (; k < len; ++k) {
+        PairEntry<T> e;
+        e.xx = e.xy = e.yy = T(0);
+        e.src = t;
+        row[(size_t)k * 32] = e;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pair_spmv(int N, const int* __restrict__ slice_start,
+                                                  const PairEntry<T>* __restrict__ pairs,
+                                                  const typename V2<T>::type* __restrict__ mu_s,
+                                                  typename V2<T>::type* __restrict__ v_s) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const int sl = t >> 5, lane = t & 31;
+    const int base = slice_start[sl], len = slice_start[sl + 1] - base;
+    const PairEntry<T>* row = pairs + (size_t)base * 32 + lane;
+    T ax = 0, ay = 0;
+    for (int k = 0; k < len; ++k) {
+        PairEntry<T> e = row[(size_t)k * 32];
+        typename V2<T>::type m = mu_s[e.src];
+        ax = fma(e.xx, m.x, fma(e.xy, m.y, ax));
+        ay = fma(e.xy, m.x, fma(e.yy, m.y, ay));
+    }
+    v_s[t].x = ax;
+    v_s[t].y = ay;
 }
 
 // ---------------------------------------------------------------------------
 // Wave space
 // ---------------------------------------------------------------------------
-// Spread: grid_c(y) += g(y - x_n) mu_{n,c}, g(r) = (2 xi^2/(pi eta_s)) exp(-2 xi^2 r^2/eta_s),
-// over the P x P grid points nearest to x_n (Sec. 3.2, the Gaussian spreading S).
-template <typename T, int PMAX>
-__global__ void __launch_bounds__(128) k_spread(int N, int M, int P, T alpha_h2, T g0,
-                                               const int2* __restrict__ gbase,
-                                               const typename V2<T>::type* __restrict__ gfrac,
-                                               const typename V2<T>::type* __restrict__ mu_s,
-                                               T* __restrict__ grid) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    int2 b = gbase[s];
-    typename V2<T>::type f = gfrac[s];
-    typename V2<T>::type mu = mu_s[s];
-    const int hw = (P - 1) / 2;
-    T wx[PMAX], wy[PMAX];
-    for (int p = 0; p < P; ++p) {
-        T dx = T(p - hw) - f.x, dy = T(p - hw) - f.y;
-        wx[p] = dev_exp(-alpha_h2 * dx * dx);
-        wy[p] = g0 * dev_exp(-alpha_h2 * dy * dy);
-    }
-    T* gx = grid;
-    T* gy = grid + (size_t)M * M;
-    for (int q = 0; q < P; ++q) {
-        int iy = b.y + q - hw;
-        iy += (iy < 0) ? M : 0;
-        iy -= (iy >= M) ? M : 0;
-        T wyq = wy[q];
-        for (int p = 0; p < P; ++p) {
-            int ix = b.x + p - hw;
-            ix += (ix < 0) ? M : 0;
-            ix -= (ix >= M) ? M : 0;
-            T w = wyq * wx[p];
-            size_t idx = (size_t)iy * M + ix;
-            atomicAdd(&gx[idx], w * mu.x);
-            atomicAdd(&gy[idx], w * mu.y);
-        }
-    }
-}
-
 // Fourier scale between the FFTs: u(k) <- sc(k) (I - k k^T/k^2) u(k) with
 //   sc = h^4 /(eta V) (1 + k^2/4xi^2) exp(-(1 - eta_s) k^2/4xi^2) / k^2,
 // i.e. the Hasimoto tensor B (Sec. 3.2) times both Gaussian deconvolutions and
@@ -214,9 +242,10 @@ __global__ void k_scale(int M, T twopi_L, T inv4xi2, T one_minus_eta, T pref,
     }
     T kx = twopi_L * T(c), ky = twopi_L * T(ky_i);
     T k2 = kx * kx + ky * ky;
+    T ik2 = T(1) / k2;
     T q = k2 * inv4xi2;
-    T sc = pref * (T(1) + q) * dev_exp(-one_minus_eta * q) / k2;
-    T pxx = T(1) - kx * kx / k2, pyy = T(1) - ky * ky / k2, pxy = -kx * ky / k2;
+    T sc = pref * (T(1) + q) * dev_exp(-one_minus_eta * q) * ik2;
+    T pxx = T(1) - kx * kx * ik2, pyy = T(1) - ky * ky * ik2, pxy = -kx * ky * ik2;
     typename Cplx<T>::type a = ux[i], b = uy[i];
     ux[i].x = sc * (pxx * a.x + pxy * b.x);
     ux[i].y = sc * (pxx * a.y + pxy * b.y);
@@ -224,63 +253,19 @@ __global__ void k_scale(int M, T twopi_L, T inv4xi2, T one_minus_eta, T pref,
     uy[i].y = sc * (pxy * a.y + pyy * b.y);
 }
 
-// Interpolation: v_t (+)= sum_{P x P} g(x_t - y) U(y) (the h^2 weight is in k_scale).
-template <typename T, int PMAX>
-__global__ void __launch_bounds__(128) k_interp(int N, int M, int P, T alpha_h2, T g0, int accumulate,
-                                               const int2* __restrict__ gbase,
-                                               const typename V2<T>::type* __restrict__ gfrac,
-                                               const T* __restrict__ grid,
-                                               typename V2<T>::type* __restrict__ v_s) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= N) return;
-    int2 b = gbase[s];
-    typename V2<T>::type f = gfrac[s];
-    const int hw = (P - 1) / 2;
-    T wx[PMAX], wy[PMAX];
-    for (int p = 0; p < P; ++p) {
-        T dx = T(p - hw) - f.x, dy = T(p - hw) - f.y;
-        wx[p] = dev_exp(-alpha_h2 * dx * dx);
-        wy[p] = g0 * dev_exp(-alpha_h2 * dy * dy);
-    }
-    const T* gx = grid;
-    const T* gy = grid + (size_t)M * M;
-    T ax = 0, ay = 0;
-    for (int q = 0; q < P; ++q) {
-        int iy = b.y + q - hw;
-        iy += (iy < 0) ? M : 0;
-        iy -= (iy >= M) ? M : 0;
-        T rx = 0, ry = 0;
-        for (int p = 0; p < P; ++p) {
-            int ix = b.x + p - hw;
-            ix += (ix < 0) ? M : 0;
-            ix -= (ix >= M) ? M : 0;
-            size_t idx = (size_t)iy * M + ix;
-            rx += wx[p] * gx[idx];
-            ry += wx[p] * gy[idx];
-        }
-        ax += wy[q] * rx;
-        ay += wy[q] * ry;
-    }
-    if (accumulate) {
-        v_s[s].x += ax;
-        v_s[s].y += ay;
-    } else {
-        v_s[s].x = ax;
-        v_s[s].y = ay;
-    }
-}
-
-// Back to body order, plus the Alpert band: v_m = v_s[slot[m]] + R_b A_ref[j] R_b^T mu (FP64).
+// Back to body order: v_m = v_s[slot[m]] + v_t[tslot[m]] + R_b A_ref[j] R_b^T mu (FP64 band).
 template <typename T>
-__global__ void k_finish(int N, int n_p, int band, int with_alpert, const int* __restrict__ slot,
-                         const typename V2<T>::type* __restrict__ v_s, const double* __restrict__ Q,
-                         const double* __restrict__ A, const double2* __restrict__ mu,
-                         double2* __restrict__ v) {
+__global__ void k_finish(int N, int n_p, int band, int with_real, int with_wave, const int* __restrict__ slot,
+                         const int* __restrict__ tslot, const typename V2<T>::type* __restrict__ v_s,
+                         const typename V2<T>::type* __restrict__ v_t, const double* __restrict__ Q,
+                         const double* __restrict__ A, const double2* __restrict__ mu, double2* __restrict__ v) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= N) return;
-    typename V2<T>::type w = v_s[slot[m]];
-    double vx = (double)w.x, vy = (double)w.y;
-    if (with_alpert) {
+    double vx = 0, vy = 0;
+    if (with_real) {
+        typename V2<T>::type w = v_s[slot[m]];
+        vx = (double)w.x;
+        vy = (double)w.y;
         int b = m / n_p, j = m - b * n_p;
         double c, s;
         sincos(Q[3 * b + 2], &s, &c);
@@ -300,6 +285,11 @@ __global__ void k_finish(int N, int n_p, int band, int with_alpert, const int* _
         vx += c * ax - s * ay;
         vy += s * ax + c * ay;
     }
+    if (with_wave) {
+        typename V2<T>::type w = v_t[tslot[m]];
+        vx += (double)w.x;
+        vy += (double)w.y;
+    }
     v[m] = make_double2(vx, vy);
 }
 
@@ -318,15 +308,97 @@ template <> struct FftType<float> {
 template <typename T> static EwaldBuffers<T>& bufs(fbim_handle_s* h);
 template <> EwaldBuffers<double>& bufs<double>(fbim_handle_s* h) { return h->e64; }
 template <> EwaldBuffers<float>& bufs<float>(fbim_handle_s* h) { return h->e32; }
+template <typename T> static const ChebE1<T>& cheb(fbim_handle_s* h);
+template <> const ChebE1<double>& cheb<double>(fbim_handle_s* h) { return h->cheb64; }
+template <> const ChebE1<float>& cheb<float>(fbim_handle_s* h) { return h->cheb32; }
+
+// Real-space pair list for the current geometry: count, slice lengths, fill.
+template <typename T>
+static fbim_status build_pairs(fbim_handle_s* h) {
+    auto& e = bufs<T>(h);
+    using T2 = typename V2<T>::type;
+    const int N = h->N, n_slice = (N + 31) / 32;
+    const T rc = (T)h->r_c, rc2 = (T)(h->r_c * h->r_c);
+    k_pair_count<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, h->perm, h->cell, h->cell_start,
+                                                            (const T2*)e.off, e.row_count, h->flags);
+    k_slice_scan<<<1, 1024, 0, h->stream>>>(n_slice, N, e.row_count, e.slice_start);
+    int total = 0;
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(&total, e.slice_start + n_slice, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if ((size_t)total > e.pair_cap) {
+        cudaFree(e.pairs);
+        e.pairs = nullptr;
+        size_t cap = (size_t)total + total / 4 + 32;
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.pairs, cap * 32 * sizeof(PairEntry<T>)));
+        e.pair_cap = cap;
+    }
+    const T pref = (T)(1.0 / (4.0 * M_PI * h->eta));
+    k_pair_fill<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, (T)(h->xi * h->xi), pref,
+                                                           cheb<T>(h), h->perm, h->cell, h->cell_start,
+                                                           (const T2*)e.off, e.slice_start, (PairEntry<T>*)e.pairs);
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    e.n_padded = (long long)total * 32;
+    e.pairs_ready = true;
+    return FBIM_OK;
+}
 
 template <typename T>
 fbim_status refresh_offsets(fbim_handle_s* h) {
     auto& e = bufs<T>(h);
     using T2 = typename V2<T>::type;
     const int tb = 256;
-    k_offsets<T><<<(h->N + tb - 1) / tb, tb, 0, h->stream>>>(h->N, h->perm, h->x, h->cell, h->n_box, h->r_c, h->h,
-                                                             h->M, (T2*)e.off, e.gbase, (T2*)e.gfrac);
+    k_offsets<T><<<(h->N + tb - 1) / tb, tb, 0, h->stream>>>(h->N, h->perm, h->tperm, h->x, h->cell, h->gbase,
+                                                             h->n_box, h->r_c, h->h, (T2*)e.off, e.tbase,
+                                                             (T2*)e.tfrac);
     FBIM_CUDA_TRY(h, cudaGetLastError());
+    return build_pairs<T>(h);
+}
+
+// Autotuner: time spread + interpolation of both kernel variants on the current
+// geometry (forces = 1 on every node) and keep the faster one.
+template <typename T>
+static fbim_status autotune_wave(fbim_handle_s* h) {
+    auto& e = bufs<T>(h);
+    using T2 = typename V2<T>::type;
+    const size_t M = h->M;
+    const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
+    const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
+    const T ah2 = (T)(alpha * h->h * h->h);
+    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
+    std::vector<T2> ones(h->N);
+    for (auto& o : ones) o.x = o.y = T(1);
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.mu_t, ones.data(), h->N * sizeof(T2), cudaMemcpyHostToDevice, h->stream));
+    cudaEvent_t ev[3];
+    for (auto& x : ev) FBIM_CUDA_TRY(h, cudaEventCreate(&x));
+    float best = 1e30f;
+    int choice = 1;
+    for (int variant = 0; variant < 2; ++variant) {
+        float tot = 0;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(ev[0], h->stream);
+            if (variant == 1) {
+                cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream);
+                warp_spread<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.mu_t, e.grid);
+                warp_interp<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.grid, e.v_t);
+            } else {
+                tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid);
+                tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
+            }
+            cudaEventRecord(ev[1], h->stream);
+            cudaEventSynchronize(ev[1]);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (rep > 0) tot += ms;  // first repetition warms up
+        }
+        e.variant_ms[variant] = tot / 3;
+        if (tot < best) {
+            best = tot;
+            choice = variant;
+        }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    e.wave_variant = choice;
     return FBIM_OK;
 }
 
@@ -337,13 +409,18 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     using T2 = typename V2<T>::type;
     using C = typename Cplx<T>::type;
     const size_t N = h->N, M = h->M, Mh = h->M / 2 + 1;
+    const size_t n_slice = (N + 31) / 32;
     FBIM_CUDA_TRY(h, cudaMalloc(&e.off, N * sizeof(T2)));
-    FBIM_CUDA_TRY(h, cudaMalloc(&e.gbase, N * sizeof(int2)));
-    FBIM_CUDA_TRY(h, cudaMalloc(&e.gfrac, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_s, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.v_s, N * sizeof(T2)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.tbase, N * sizeof(int2)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.tfrac, N * sizeof(T2)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_t, N * sizeof(T2)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.v_t, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.grid, 2 * M * M * sizeof(T)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.spec, 2 * M * Mh * sizeof(C)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, (n_slice + 1) * sizeof(int)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.row_count, n_slice * 32 * sizeof(int)));
     int n[2] = {(int)M, (int)M};
     int inembed[2] = {(int)M, (int)M};
     int onembed[2] = {(int)M, (int)Mh};
@@ -353,24 +430,14 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
                                     FftType<T>::inv, 2));
     FBIM_CUFFT_TRY(h, cufftSetStream(e.plan_f, h->stream));
     FBIM_CUFFT_TRY(h, cufftSetStream(e.plan_i, h->stream));
+    FBIM_CUDA_TRY(h, tile_set_smem<T>(TileGeom{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2}));
     e.ready = true;
-    return refresh_offsets<T>(h);
-}
-
-template <typename T, int PMAX>
-static void launch_spread(fbim_handle_s* h, EwaldBuffers<T>& e, T ah2, T g0) {
-    using T2 = typename V2<T>::type;
-    const int tb = 128;
-    k_spread<T, PMAX><<<(h->N + tb - 1) / tb, tb, 0, h->stream>>>(h->N, h->M, h->P, ah2, g0, e.gbase,
-                                                                  (const T2*)e.gfrac, (const T2*)e.mu_s, e.grid);
-}
-
-template <typename T, int PMAX>
-static void launch_interp(fbim_handle_s* h, EwaldBuffers<T>& e, T ah2, T g0, int acc) {
-    using T2 = typename V2<T>::type;
-    const int tb = 128;
-    k_interp<T, PMAX><<<(h->N + tb - 1) / tb, tb, 0, h->stream>>>(h->N, h->M, h->P, ah2, g0, acc, e.gbase,
-                                                                   (const T2*)e.gfrac, e.grid, (T2*)e.v_s);
+    FBIM_TRY(refresh_offsets<T>(h));
+    if (h->autotune == 1)
+        FBIM_TRY(autotune_wave<T>(h));
+    else
+        e.wave_variant = h->autotune == 2 ? 1 : 0;
+    return FBIM_OK;
 }
 
 template <typename T>
@@ -380,22 +447,23 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     using T2 = typename V2<T>::type;
     using C = typename Cplx<T>::type;
     const int N = h->N, tb = 256;
-    h->mark_begin();
-    k_gather<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->perm, (const double2*)mu, (T2*)e.mu_s);
-    h->mark(FBIM_ST_GATHER);
     const bool real = which & 1, wave = which & 2;
+    h->mark_begin();
+    k_gather<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->perm, h->tperm, real, wave, (const double2*)mu,
+                                                         (T2*)e.mu_s, (T2*)e.mu_t);
+    h->mark(FBIM_ST_GATHER);
+    const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
+    const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
+    const T ah2 = (T)(alpha * h->h * h->h);
+    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
     if (wave) {
         const size_t M = h->M, Mh = h->M / 2 + 1;
-        FBIM_CUDA_TRY(h, cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream));
-        const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
-        const T ah2 = (T)(alpha * h->h * h->h);
-        const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
-        if (h->P <= 15)
-            launch_spread<T, 15>(h, e, ah2, g0);
-        else if (h->P <= 23)
-            launch_spread<T, 23>(h, e, ah2, g0);
-        else
-            launch_spread<T, 31>(h, e, ah2, g0);
+        if (e.wave_variant == 1) {
+            FBIM_CUDA_TRY(h, cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream));
+            warp_spread<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.mu_t, e.grid);
+        } else {
+            tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid);
+        }
         h->mark(FBIM_ST_SPREAD);
         FBIM_CUFFT_TRY(h, FftType<T>::f(e.plan_f, e.grid, (C*)e.spec));
         h->mark(FBIM_ST_FFT_F);
@@ -410,30 +478,20 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         h->mark(FBIM_ST_FFT_I);
     }
     if (real) {
-        const T pref = (T)(1.0 / (4.0 * M_PI * h->eta));
-        k_pairs<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, (T)h->r_c, (T)(h->r_c * h->r_c),
-                                                           (T)(h->xi * h->xi), pref, h->perm, h->cell,
-                                                           h->cell_start, (const T2*)e.off, (const T2*)e.mu_s,
-                                                           (T2*)e.v_s, h->flags);
+        k_pair_spmv<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
+                                                               (const T2*)e.mu_s, (T2*)e.v_s);
         h->mark(FBIM_ST_PAIRS);
     }
     if (wave) {
-        const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
-        const T ah2 = (T)(alpha * h->h * h->h);
-        const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
-        int acc = real ? 1 : 0;
-        if (h->P <= 15)
-            launch_interp<T, 15>(h, e, ah2, g0, acc);
-        else if (h->P <= 23)
-            launch_interp<T, 23>(h, e, ah2, g0, acc);
+        if (e.wave_variant == 1)
+            warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.grid, e.v_t);
         else
-            launch_interp<T, 31>(h, e, ah2, g0, acc);
+            tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
         h->mark(FBIM_ST_INTERP);
     }
-    if (!real && !wave) FBIM_CUDA_TRY(h, cudaMemsetAsync(e.v_s, 0, N * sizeof(T2), h->stream));
-    k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, real ? 1 : 0, h->slot,
-                                                         (const T2*)e.v_s, h->Q, h->band_dev,
-                                                         (const double2*)mu, (double2*)v);
+    k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, real ? 1 : 0, wave ? 1 : 0, h->slot,
+                                                         h->tslot, (const T2*)e.v_s, (const T2*)e.v_t, h->Q,
+                                                         h->band_dev, (const double2*)mu, (double2*)v);
     h->mark(FBIM_ST_FINISH);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     h->collect();
@@ -443,12 +501,17 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
 template <typename T>
 static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.off);
-    cudaFree(e.gbase);
-    cudaFree(e.gfrac);
     cudaFree(e.mu_s);
     cudaFree(e.v_s);
+    cudaFree(e.tbase);
+    cudaFree(e.tfrac);
+    cudaFree(e.mu_t);
+    cudaFree(e.v_t);
     cudaFree(e.grid);
     cudaFree(e.spec);
+    cudaFree(e.pairs);
+    cudaFree(e.slice_start);
+    cudaFree(e.row_count);
     if (e.plan_f) cufftDestroy(e.plan_f);
     if (e.plan_i) cufftDestroy(e.plan_i);
     e = EwaldBuffers<T>();

@@ -54,15 +54,37 @@ const char* global_error();
 template <typename T>
 struct EwaldBuffers {
     void* off = nullptr;     // [N] T2: node offset from its cell's lower corner, cell-sorted
-    int2* gbase = nullptr;   // [N] nearest grid point (ix, iy) of each node, cell-sorted
-    void* gfrac = nullptr;   // [N] T2: x / h - base, in [-1/2, 1/2], cell-sorted
-    void* mu_s = nullptr;    // [N] T2: forces in cell-sorted order
-    void* v_s = nullptr;     // [N] T2: velocities in cell-sorted order
+    void* mu_s = nullptr;    // [N] T2: forces in cell-sorted order (real space)
+    void* v_s = nullptr;     // [N] T2: real-space velocities, cell-sorted
+    int2* tbase = nullptr;   // [N] nearest grid point (ix, iy), tile-sorted
+    void* tfrac = nullptr;   // [N] T2: x / h - base in [-1/2, 1/2], tile-sorted
+    void* mu_t = nullptr;    // [N] T2: forces in tile-sorted order (wave space)
+    void* v_t = nullptr;     // [N] T2: wave-space velocities, tile-sorted
     T* grid = nullptr;       // [2][M][M] real grid (component-major)
     void* spec = nullptr;    // [2][M][M/2+1] complex half spectrum
     cufftHandle plan_f = 0;  // R2C / D2Z, batch 2
     cufftHandle plan_i = 0;  // C2R / Z2D, batch 2
+    // real-space pair list in sliced-ELL layout (slices of 32 cell-sorted targets)
+    void* pairs = nullptr;       // entries [slice_start[s] + k][32]: G tensor (xx, xy, yy) and source slot
+    int* slice_start = nullptr;  // [n_slice + 1] entry offsets (in units of 32 entries)
+    int* row_count = nullptr;    // [n_slice * 32] hits per target
+    size_t pair_cap = 0;         // allocated entries (units of 32)
+    long long n_pairs = 0;       // ordered pairs within r_c (without padding)
+    long long n_padded = 0;      // stored entries including padding
+    bool pairs_ready = false;
+    int wave_variant = 1;        // 0: tile kernels (shared memory), 1: warp-per-node kernels
+    float variant_ms[2] = {0, 0};  // autotuner timings of spread + interp per variant
     bool ready = false;
+};
+
+// Chebyshev expansion of S(z) = (E1(z) + ln z)/2 - e^{-z} on [0, zmax], so that
+// the real-space kernel coefficient E1(z)/2 - e^{-z} = S(z) - ln(z)/2.
+constexpr int kChebMax = 48;
+template <typename T>
+struct ChebE1 {
+    T c[kChebMax];
+    T scale;   // 2 / zmax
+    int deg;
 };
 
 }  // namespace fbim
@@ -91,6 +113,17 @@ struct fbim_handle_s {
     int* slot = nullptr;         // [N] node -> slot
     int* flags = nullptr;        // [4] device error flags
     double* band_dev = nullptr;  // [n_p][2 band + 1][2][2] symmetrised M(a)_ref
+    int2* gbase = nullptr;       // [N] nearest grid point of each node (body order)
+    int* tile_start = nullptr;   // [n_tile^2 + 1] wave-space tiles of TS x TS grid points
+    int* tile_fill = nullptr;    // [n_tile^2]
+    int* tperm = nullptr;        // [N] tile slot -> node
+    int* tslot = nullptr;        // [N] node -> tile slot
+    int* tile_tmp = nullptr;     // [N] tile id of each node (scratch of the sort)
+    int TS = 0, n_tile = 0;      // tile side (divides M) and tiles per side
+    int autotune = 1;            // time the wave-space kernel variants at setup
+    double zmax = 0;             // xi^2 r_c^2 (upper end of the E1 expansion)
+    fbim::ChebE1<double> cheb64{};
+    fbim::ChebE1<float> cheb32{};
 
     fbim::EwaldBuffers<double> e64;
     fbim::EwaldBuffers<float> e32;
@@ -118,6 +151,7 @@ namespace fbim {
 double host_e1(double z);
 fbim_status alpert_rule(int order, std::vector<double>& v, std::vector<double>& w, int& a, std::string& err);
 fbim_status alpert_reference_band(fbim_handle_s* h, std::vector<double>& band_out);
+void e1_chebyshev(double zmax, int deg, std::vector<double>& coef);
 fbim_status choose_ewald(double L, double r_c, double tol, double xi_in, int& n_box, double& r_c_out,
                          double& xi, int& M, int& P, double& eta_s, std::string& err);
 

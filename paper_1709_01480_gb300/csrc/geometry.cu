@@ -4,7 +4,8 @@
 // Cells are n_box x n_box squares of side r_c = L / n_box; nodes are counted
 // per cell, the counts scanned, the nodes scattered, and each cell's slots
 // sorted by node index so that the cell-sorted order (and every sum over it)
-// is deterministic.
+// is deterministic.  The same counting sort orders the nodes by the grid tile
+// of their nearest grid point, the layout of the wave-space kernels.
 #include "fbim_internal.h"
 
 namespace fbim {
@@ -12,8 +13,9 @@ namespace fbim {
 namespace {
 
 __global__ void k_nodes(int N, int n_p, const double* __restrict__ Q, const double* __restrict__ ref, double L,
-                        double r_c, int n_box, double* __restrict__ x, int* __restrict__ cell,
-                        int* __restrict__ count, int* __restrict__ flags) {
+                        double r_c, int n_box, double hgrid, int M, int TS, int n_tile, double* __restrict__ x,
+                        int* __restrict__ cell, int* __restrict__ count, int2* __restrict__ gbase,
+                        int* __restrict__ tcount, int* __restrict__ flags) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= N) return;
     int b = m / n_p, j = m - b * n_p;
@@ -39,6 +41,10 @@ __global__ void k_nodes(int N, int n_p, const double* __restrict__ Q, const doub
     int cid = cy * n_box + cx;
     cell[m] = cid;
     atomicAdd(&count[cid], 1);
+    // nearest grid point and its wave-space tile
+    int bx = ((int)rint(px / hgrid)) % M, by = ((int)rint(py / hgrid)) % M;
+    gbase[m] = make_int2(bx, by);
+    atomicAdd(&tcount[(by / TS) * n_tile + bx / TS], 1);
 }
 
 // Exclusive scan of count[0..n) into start[0..n], one block, any n.
@@ -74,6 +80,16 @@ __global__ void k_scatter(int N, const int* __restrict__ cell, const int* __rest
     perm[pos] = m;
 }
 
+__global__ void k_scatter_slots(int N, const int* __restrict__ key, const int* __restrict__ start,
+                                int* __restrict__ fill, int* __restrict__ perm, int* __restrict__ slot) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    int c = key[m];
+    int pos = start[c] + atomicAdd(&fill[c], 1);
+    perm[pos] = m;
+    slot[m] = pos;
+}
+
 __global__ void k_sort_cells(int n_cell, const int* __restrict__ start, int* __restrict__ perm,
                              int* __restrict__ slot) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -91,18 +107,36 @@ __global__ void k_sort_cells(int n_cell, const int* __restrict__ start, int* __r
     for (int i = lo; i < hi; ++i) slot[perm[i]] = i;
 }
 
+__global__ void k_tile_of(int N, const int2* __restrict__ gbase, int TS, int n_tile, int* __restrict__ tile) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    int2 b = gbase[m];
+    tile[m] = (b.y / TS) * n_tile + b.x / TS;
+}
+
 }  // namespace
 
 fbim_status build_geometry(fbim_handle_s* h) {
-    const int N = h->N, nc = h->n_cell();
+    const int N = h->N, nc = h->n_cell(), nt = h->n_tile * h->n_tile;
     FBIM_CUDA_TRY(h, cudaMemsetAsync(h->cell_fill, 0, sizeof(int) * nc, h->stream));
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(h->tile_fill, 0, sizeof(int) * nt, h->stream));
     const int tb = 256;
-    k_nodes<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->Q, h->ref, h->L, h->r_c, h->n_box, h->x, h->cell,
-                                                     h->cell_fill, h->flags);
+    k_nodes<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->Q, h->ref, h->L, h->r_c, h->n_box, h->h, h->M,
+                                                     h->TS, h->n_tile, h->x, h->cell, h->cell_fill, h->gbase,
+                                                     h->tile_fill, h->flags);
+    // cell list (real space)
     k_scan<<<1, 1024, 0, h->stream>>>(nc, h->cell_fill, h->cell_start);
     FBIM_CUDA_TRY(h, cudaMemsetAsync(h->cell_fill, 0, sizeof(int) * nc, h->stream));
     k_scatter<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->cell, h->cell_start, h->cell_fill, h->perm);
     k_sort_cells<<<(nc + tb - 1) / tb, tb, 0, h->stream>>>(nc, h->cell_start, h->perm, h->slot);
+    // grid tiles (wave space): nodes sorted by the TS x TS tile holding their nearest grid point
+    k_scan<<<1, 1024, 0, h->stream>>>(nt, h->tile_fill, h->tile_start);
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(h->tile_fill, 0, sizeof(int) * nt, h->stream));
+    k_tile_of<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->gbase, h->TS, h->n_tile, h->tile_tmp);
+    // (order inside a tile is left as scattered: wave-space sums do not depend on it
+    // beyond the rounding of the shared-memory accumulation)
+    k_scatter_slots<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->tile_tmp, h->tile_start, h->tile_fill, h->tperm,
+                                                             h->tslot);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     if (h->e64.ready) FBIM_TRY(refresh_offsets<double>(h));
     if (h->e32.ready) FBIM_TRY(refresh_offsets<float>(h));

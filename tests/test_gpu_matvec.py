@@ -61,12 +61,13 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("wave", ["tile", "warp"])
 @pytest.mark.parametrize("n_b,n_p,L,seed,n_box", CASES)
-def test_fp64_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
+def test_fp64_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box, wave):
     ref, Q = _case(n_b, n_p, L, seed)
     tol = 1e-13
     xi = _xi(L, n_box, tol)
-    op = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, precision="fp64")
+    op = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, precision="fp64", wave=wave)
     assert op.info["n_box"] == n_box
     M, Mr, Mw = _oracle_parts(ref, Q, L, xi)
     rng = np.random.default_rng(seed + 100)
@@ -75,17 +76,18 @@ def test_fp64_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
     for fn, A in ((op.apply_real, Mr), (op.apply_wave, Mw), (op.apply_stokeslet, M)):
         v = fn(mu_d).cpu().numpy()
         expect = (A @ mu.reshape(-1)).reshape(-1, 2)
-        print(f"fp64 {n_b}x{n_p} {fn.__name__}: rel err {_rel(v, expect):.3e}")
+        print(f"fp64 {wave} {n_b}x{n_p} {fn.__name__}: rel err {_rel(v, expect):.3e}")
         assert _rel(v, expect) < FP64_TOL, (fn.__name__, _rel(v, expect))
     op.close()
 
 
+@pytest.mark.parametrize("wave", ["tile", "warp"])
 @pytest.mark.parametrize("n_b,n_p,L,seed,n_box", CASES[:2])
-def test_fp32_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
+def test_fp32_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box, wave):
     ref, Q = _case(n_b, n_p, L, seed)
     tol = 1e-8
     xi = _xi(L, n_box, tol)
-    op = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, precision="fp32")
+    op = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, precision="fp32", wave=wave)
     M, Mr, Mw = _oracle_parts(ref, Q, L, xi)
     rng = np.random.default_rng(seed + 200)
     mu = rng.standard_normal((n_b * n_p, 2))
@@ -93,7 +95,7 @@ def test_fp32_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
     for fn, A in ((op.apply_real, Mr), (op.apply_wave, Mw), (op.apply_stokeslet, M)):
         v = fn(mu_d).cpu().numpy()
         expect = (A @ mu.reshape(-1)).reshape(-1, 2)
-        print(f"fp32 {n_b}x{n_p} {fn.__name__}: rel err {_rel(v, expect):.3e}")
+        print(f"fp32 {wave} {n_b}x{n_p} {fn.__name__}: rel err {_rel(v, expect):.3e}")
         assert _rel(v, expect) < FP32_TOL, (fn.__name__, _rel(v, expect))
     op.close()
 
@@ -154,14 +156,15 @@ def full_size():
     return w, xi, mu, rows, expect
 
 
+@pytest.mark.parametrize("wave", ["tile", "warp"])
 @pytest.mark.parametrize("precision,tol_rel", [("fp64", 1e-7), ("fp32", 3e-5)])
-def test_full_size_sampled_rows_match_oracle(torch, fb, full_size, precision, tol_rel):
+def test_full_size_sampled_rows_match_oracle(torch, fb, full_size, precision, tol_rel, wave):
     # the GPU truncates at its 1e-8 Ewald tolerance: the bar is a small multiple of it
     w, xi, mu, rows, expect = full_size
-    op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=w.L / N_BOX_FULL, xi=xi, precision=precision)
+    op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=w.L / N_BOX_FULL, xi=xi, precision=precision, wave=wave)
     v = op.apply_stokeslet(torch.tensor(mu, device="cuda")).cpu().numpy()
     got = v[rows]
-    print(f"full size {precision}: rel err {_rel(got, expect):.3e}")
+    print(f"full size {precision} {wave}: rel err {_rel(got, expect):.3e}")
     assert _rel(got, expect) < tol_rel, _rel(got, expect)
     op.close()
 
