@@ -130,6 +130,42 @@ fbim_status fbim_apply_real(fbim_handle h, const double* mu_dev, double* v_dev);
 /* v = M(w) mu, the wave-space part only (Sec. 3.2, Eq. Mwave-factorization). */
 fbim_status fbim_apply_wave(fbim_handle h, const double* mu_dev, double* v_dev);
 
+/* First-kind mobility solve (Sec. 3.1, Eq. discreteSaddlePoint):
+ *     [[M, -K], [-K^T, 0]] [mu; U] = -[slip; F]
+ * by right-preconditioned flexible GMRES with the block-diagonal preconditioner
+ * of Sec. 3.4.  FP64 handles iterate on the FP64 operator; FP32 handles run
+ * iterative refinement (FP64 residual b - A x, FP32-operator corrections).
+ *   F_dev:    double [n_b][3] forces and torques (device).
+ *   slip_dev: double [N][2] random slip, or NULL for none.
+ *   tol:      relative residual |b - A x| / |b| to reach (measured with the FP64 operator).
+ *   max_iter: cap on GMRES iterations (all refinement steps together).
+ *   U_dev:    double [n_b][3] output velocities (device).  mu_dev: NULL or double [N][2].
+ *   iters, rel_residual: NULL or outputs.  Synchronises the stream.
+ * Returns FBIM_ERR_NOT_CONVERGED (with the partial result written) if the cap is hit. */
+fbim_status fbim_mobility_solve(fbim_handle h, const double* F_dev, const double* slip_dev, double tol,
+                                int max_iter, double* U_dev, double* mu_dev, int* iters,
+                                double* rel_residual);
+
+/* Random slip v = M^1/2 W with <v v^T> = (2 kT / dt) M by the positive split (Sec. 3.3,
+ * Eq. sqrtM-split): sqrt(2 kT/dt) [G^+ (G M(r) G^T)^1/2 W(r) + (M(w))^1/2 W(w)], the
+ * near field by preconditioned Lanczos (Sec. 3.4, Eq. preconditioned-real-part) to
+ * relative tolerance tol, the far field on the Fourier grid (Eq. sqrtMwave).
+ *   W_r_dev: double [N][2] standard normals, or NULL to draw them from Philox
+ *            (seed, stream 0, counter) at index 2 m + c.
+ *   Z_w_dev: double [M][M][2][2] standard normals (grid index j_y, j_x, component,
+ *            real/imaginary; M = fbim_info.grid), or NULL to draw them from Philox
+ *            (seed, stream 1, counter) at index ((j_y M + j_x) 2 + comp) 2 + re/im.
+ *   slip_dev: double [N][2] output.  lanczos_iters: NULL or output.  Synchronises. */
+fbim_status fbim_brownian_slip(fbim_handle h, uint64_t seed, uint64_t counter, double kT, double dt,
+                               const double* W_r_dev, const double* Z_w_dev, double tol, int max_iter,
+                               double* slip_dev, int* lanczos_iters);
+
+/* n standard normals of (seed, stream, counter) from Philox4x32-10 and Box-Muller:
+ * normal i is element i mod 2 of block i / 2, counter block = (i/2 low, i/2 high,
+ * stream, counter), key = (seed low, seed high).  out_dev: double [n] (device). */
+fbim_status fbim_philox_normals(fbim_handle h, uint64_t seed, uint32_t stream, uint32_t counter, size_t n,
+                                double* out_dev);
+
 /* Information about the handle's parameters. */
 fbim_status fbim_get_info(fbim_handle h, fbim_info* info);
 

@@ -13,7 +13,8 @@ Eq. sqrtM-split):
                   here by dense eigendecomposition (principal square root).
 * ``far_field``   (eta V)^-1/2 sum_kappa e^{i k.x} B^1/2(k) W(kappa) with
                   B^1/2 = H^^1/2 / k (I - k^ k^^T)          (Sec. 3.3, Eq. sqrtMwave),
-                  as a direct sum over the same lattice of modes as an M x M grid.
+                  as a direct sum over the same lattice of modes as an M x M grid,
+                  without the Nyquist lines (see the reading below).
 * ``hermitian_noise`` builds W(kappa) on that lattice from standard normals
                   Z [M, M, 2, 2] (Sec. 3.3: zero mode 0; the three Nyquist modes
                   real N(0, I); other modes a + i b with a, b ~ N(0, I/2) and
@@ -26,7 +27,12 @@ same covariance.  Eigenvalues below 1e-12 of the largest are treated as
 spurious and zeroed.  Of each conjugate pair of modes, the member with the
 smaller linear index j_y M + j_x (j = kappa mod M) is the canonical one and
 takes a = Z[..., 0]/sqrt 2, b = Z[..., 1]/sqrt 2; a self-conjugate mode takes
-Z[..., 0].  At the Nyquist modes the sum keeps the real part.
+Z[..., 0].  The far-field sum leaves out the Nyquist lines kappa_x = -M/2 and
+kappa_y = -M/2 (including the three real Nyquist modes that Sec. 3.3 draws from
+N(0, I)): on an M-point grid such a mode stands for both +k_N and -k_N, so its
+gridded interpolation is not the value of the single lattice mode, and the grid
+is chosen so that the Hasimoto weight there is below the Ewald tolerance; the
+covariance changes by less than that tolerance.
 
 Parity: pinned by the covariance identities (the far field's covariance is
 M^(w); G^+ G M^(r)_ref G^T G^+T = M^(r)_ref, Sec. 3.4) and the statistical
@@ -116,7 +122,8 @@ def far_field(Xf: np.ndarray, L: float, xi: float, Z: np.ndarray, eta: float = 1
     ky, kx = np.meshgrid(kap, kap, indexing="ij")
     kvec = np.stack([kx.ravel(), ky.ravel()], axis=1) * (2.0 * np.pi / L)
     Wf = W.reshape(-1, 2)
-    nz = np.any(kvec != 0.0, axis=1)
+    nyq = ((ky == -(M // 2)) | (kx == -(M // 2))).ravel()
+    nz = np.any(kvec != 0.0, axis=1) & ~nyq
     kvec, Wf = kvec[nz], Wf[nz]
     k2 = np.sum(kvec * kvec, axis=1)
     s = np.sqrt(ewald.hasimoto(np.sqrt(k2), xi)) / np.sqrt(k2)      # H^1/2 / k

@@ -68,8 +68,9 @@ def mobility(M: np.ndarray, K: np.ndarray) -> np.ndarray:
 
 
 def pinv_sym(M: np.ndarray, rel: float = 1e-12) -> np.ndarray:
+    """Pseudo-inverse of a symmetric matrix: eigenvalues with |lam| <= rel max|lam| dropped."""
     lam, V = np.linalg.eigh(M)
-    keep = lam > rel * np.max(np.abs(lam))
+    keep = np.abs(lam) > rel * np.max(np.abs(lam))
     return (V[:, keep] / lam[keep]) @ V[:, keep].T
 
 

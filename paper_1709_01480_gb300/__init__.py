@@ -34,7 +34,8 @@ EXPORTS = [
     "fbim_default_params", "fbim_choose_ewald", "fbim_setup", "fbim_update_config",
     "fbim_apply_stokeslet", "fbim_apply_real", "fbim_apply_wave", "fbim_get_info",
     "fbim_destroy", "fbim_last_error", "fbim_host_expint_e1", "fbim_host_alpert_rule",
-    "fbim_set_timing", "fbim_stage_times",
+    "fbim_set_timing", "fbim_stage_times", "fbim_mobility_solve", "fbim_brownian_slip",
+    "fbim_philox_normals",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -91,6 +92,9 @@ _lib.fbim_host_expint_e1.argtypes = [_D]
 _lib.fbim_host_expint_e1.restype = _D
 _lib.fbim_host_alpert_rule.argtypes = [_I, _DP, _DP, _IP]
 _lib.fbim_set_timing.argtypes = [_P, _I]
+_lib.fbim_mobility_solve.argtypes = [_P, _P, _P, _D, _I, _P, _P, _IP, _DP]
+_lib.fbim_brownian_slip.argtypes = [_P, ctypes.c_uint64, ctypes.c_uint64, _D, _D, _P, _P, _D, _I, _P, _IP]
+_lib.fbim_philox_normals.argtypes = [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_size_t, _P]
 _lib.fbim_stage_times.argtypes = [_P, _DP, ctypes.POINTER(ctypes.c_longlong), _I]
 
 
@@ -196,6 +200,37 @@ class FBIM:
         v = out if out is not None else self._out(mu, (self.n, 2))
         _check(_lib.fbim_apply_wave(self._h, _ptr(mu), _ptr(v)), self._h)
         return v
+
+    def mobility_solve(self, F, slip=None, tol=1e-6, max_iter=500, want_mu=False, check=True):
+        """Solve the saddle system; returns (U [n_b, 3], mu or None, iterations, relative residual)."""
+        import torch
+        U = torch.empty((self.n_b, 3), dtype=torch.float64, device=F.device)
+        mu = torch.empty((self.n, 2), dtype=torch.float64, device=F.device) if want_mu else None
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        st = _lib.fbim_mobility_solve(self._h, _ptr(F), None if slip is None else _ptr(slip), float(tol),
+                                      int(max_iter), _ptr(U), None if mu is None else _ptr(mu),
+                                      ctypes.byref(it), ctypes.byref(res))
+        if check or st not in (0, 6):
+            _check(st, self._h)
+        return U, mu, it.value, res.value
+
+    def brownian_slip(self, kT=1.0, dt=1.0, W_r=None, Z_w=None, seed=0, counter=0, tol=1e-6, max_iter=200):
+        """Random slip [N, 2]; returns (slip, Lanczos iterations)."""
+        import torch
+        dev = W_r.device if W_r is not None else torch.device("cuda", self.device)
+        out = torch.empty((self.n, 2), dtype=torch.float64, device=dev)
+        it = ctypes.c_int(0)
+        _check(_lib.fbim_brownian_slip(self._h, int(seed), int(counter), float(kT), float(dt),
+                                       None if W_r is None else _ptr(W_r), None if Z_w is None else _ptr(Z_w),
+                                       float(tol), int(max_iter), _ptr(out), ctypes.byref(it)), self._h)
+        return out, it.value
+
+    def philox_normals(self, n, seed=0, stream=0, counter=0):
+        import torch
+        out = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", self.device))
+        _check(_lib.fbim_philox_normals(self._h, int(seed), int(stream), int(counter), int(n), _ptr(out)), self._h)
+        return out
 
     def set_timing(self, on: bool):
         _check(_lib.fbim_set_timing(self._h, 1 if on else 0), self._h)

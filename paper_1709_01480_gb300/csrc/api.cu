@@ -44,6 +44,8 @@ void release(fbim_handle h) {
     cudaFree(h->tperm);
     cudaFree(h->tslot);
     cudaFree(h->tile_tmp);
+    cudaFree(h->rot);
+    fbim::free_solver(h);
     delete h;
 }
 
@@ -193,6 +195,7 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         }
         std::vector<double> bandv;
         FBIM_TRY(fbim::alpert_reference_band(h, bandv));
+        h->host_band = bandv;
         // Chebyshev series of the smooth part of E1 on [0, xi^2 r_c^2]
         h->zmax = h->xi * h->xi * h->r_c * h->r_c * (1.0 + 1e-6);
         {
@@ -224,6 +227,7 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         FBIM_CUDA_TRY(h, cudaMalloc(&h->tperm, N * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->tslot, N * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->tile_tmp, N * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->rot, 2 * n_b * sizeof(double)));
         FBIM_CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, 4 * sizeof(int), h->stream));
         FBIM_CUDA_TRY(h, cudaMemcpyAsync(h->ref, ref_nodes_host, 2 * n_p * sizeof(double), cudaMemcpyHostToDevice,
                                          h->stream));

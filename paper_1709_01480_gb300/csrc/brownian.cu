@@ -1,0 +1,305 @@
+// Random slip by the positively split Ewald sum (Sec. 3.3, Eq. sqrtM-split):
+//     slip = sqrt(2 kT/dt) [ G^+ (G M(r) G^T)^1/2 W(r) + (M(w))^1/2 W(w) ]
+// with the block-diagonal G_b = R_b G_ref R_b^T of Sec. 3.4 (Eqs.
+// preconditioned-real-part, Gprecond-decomp, Gprecond-precompute).
+//
+// Near field: Lanczos iteration for f(A) w, f = sqrt, A = G M(r) G^T (the real-
+// space operator in the handle's precision, G as one GEMM over all bodies), with
+// full FP64 reorthogonalisation; after k steps y_k = |w| V_k f(T_k) e_1 and the
+// iteration stops when |y_k - y_{k-1}| <= tol |y_k|, which needs only the small
+// coefficient vectors because V_k is orthonormal.  Ritz values below zero (from
+// the small negative eigenvalues the symmetrised Alpert block can leave) are
+// clipped to zero.
+// Far field: the wave-space noise pipeline (ewald_ops.cu).
+#include <cublas_v2.h>
+
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "ewald_types.cuh"
+#include "fbim_internal.h"
+
+#include "solver.cuh"
+
+namespace fbim {
+
+fbim_status ensure_solver(fbim_handle_s* h);
+
+namespace {
+
+__global__ void k_philox_normals(size_t n, unsigned long long seed, unsigned stream, unsigned counter,
+                                 double* __restrict__ out) {
+    size_t blk = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * blk >= n) return;
+    double2 z = philox_normals(seed, stream, counter, blk);
+    out[2 * blk] = z.x;
+    if (2 * blk + 1 < n) out[2 * blk + 1] = z.y;
+}
+
+template <typename T>
+__global__ void k_rot_in2(int N, int n_p, const double* __restrict__ rot, const double* __restrict__ in,
+                          T* __restrict__ z) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    int b = m / n_p;
+    double c = rot[2 * b], s = rot[2 * b + 1];
+    double ux = in[2 * m], uy = in[2 * m + 1];
+    z[2 * m] = (T)(c * ux + s * uy);
+    z[2 * m + 1] = (T)(-s * ux + c * uy);
+}
+
+template <typename T>
+__global__ void k_rot_out(int N, int n_p, const double* __restrict__ rot, const T* __restrict__ g,
+                          double* __restrict__ out) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    int b = m / n_p;
+    double c = rot[2 * b], s = rot[2 * b + 1];
+    double gx = (double)g[2 * m], gy = (double)g[2 * m + 1];
+    out[2 * m] = c * gx - s * gy;
+    out[2 * m + 1] = s * gx + c * gy;
+}
+
+__global__ void k_combine(int n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                          double* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+#define FBIM_CUBLAS_TRY2(h, expr)                                                       \
+    do {                                                                                \
+        cublasStatus_t s__ = (expr);                                                    \
+        if (s__ != CUBLAS_STATUS_SUCCESS) {                                             \
+            (h)->fail(std::string(#expr) + ": cublas error " + std::to_string((int)s__)); \
+            return FBIM_ERR_CUDA;                                                       \
+        }                                                                               \
+    } while (0)
+
+// out_b = R_b B_ref R_b^T in_b for every body (B_ref = G_ref or G_ref^+), precision T.
+template <typename T>
+fbim_status block_apply(fbim_handle_s* h, const T* Bref, const double* in, double* out) {
+    Solver* S = h->solver;
+    const int N = h->N;
+    T* z = (T*)S->zbuf;
+    T* g = (T*)S->gbuf;
+    k_rot_in2<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, h->n_p, h->rot, in, z);
+    const int n2 = S->n2;
+    cublasStatus_t st;
+    if (std::is_same<T, float>::value) {
+        const float one = 1.f, zero = 0.f;
+        st = cublasSgemm(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, n2, h->n_b, n2, &one, (const float*)Bref, n2,
+                         (const float*)z, n2, &zero, (float*)g, n2);
+    } else {
+        const double one = 1.0, zero = 0.0;
+        st = cublasDgemm(S->blas, CUBLAS_OP_N, CUBLAS_OP_N, n2, h->n_b, n2, &one, (const double*)Bref, n2,
+                         (const double*)z, n2, &zero, (double*)g, n2);
+    }
+    if (st != CUBLAS_STATUS_SUCCESS) {
+        h->fail("block_apply: GEMM failed");
+        return FBIM_ERR_CUDA;
+    }
+    k_rot_out<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, h->n_p, h->rot, g, out);
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    return FBIM_OK;
+}
+
+// Eigen-decomposition of a small symmetric matrix by cyclic Jacobi rotations
+// (row-major, in place; V gets the eigenvectors as columns).
+void jacobi_eig(std::vector<double>& A, int n, std::vector<double>& V) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off < 1e-30) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[(size_t)p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                double theta = (aqq - app) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {
+                    double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - s * vkq;
+                    V[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+// coefficients c = |w| sqrt(T) e_1 of the Lanczos approximation (negative Ritz values clipped)
+std::vector<double> lanczos_coeffs(const std::vector<double>& alpha, const std::vector<double>& beta, int k,
+                                   double wnorm) {
+    std::vector<double> A((size_t)k * k, 0.0), V;
+    for (int i = 0; i < k; ++i) {
+        A[(size_t)i * k + i] = alpha[i];
+        if (i + 1 < k) {
+            A[(size_t)i * k + i + 1] = beta[i];
+            A[(size_t)(i + 1) * k + i] = beta[i];
+        }
+    }
+    jacobi_eig(A, k, V);
+    std::vector<double> c(k, 0.0);
+    for (int j = 0; j < k; ++j) {
+        double lam = A[(size_t)j * k + j];
+        double f = lam > 0 ? std::sqrt(lam) : 0.0;
+        double w = f * V[(size_t)0 * k + j];  // e_1^T v_j
+        for (int i = 0; i < k; ++i) c[i] += V[(size_t)i * k + j] * w;
+    }
+    for (auto& x : c) x *= wnorm;
+    return c;
+}
+
+template <typename T>
+fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_iter, double* y, int& iters) {
+    Solver* S = h->solver;
+    const int n = 2 * h->N;
+    if (S->lanczos_max < max_iter + 1) {
+        cudaFree(S->lz);
+        cudaFree(S->lh);
+        S->lz = nullptr;
+        S->lh = nullptr;
+        S->lanczos_max = 0;
+        FBIM_CUDA_TRY(h, cudaMalloc(&S->lz, sizeof(double) * (size_t)n * (max_iter + 1)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&S->lh, sizeof(double) * 2 * (size_t)(max_iter + 1)));
+        S->lanczos_max = max_iter + 1;
+    }
+    const T* G = std::is_same<T, float>::value ? (const T*)S->G32 : (const T*)S->G64;
+    const T* Gd = std::is_same<T, float>::value ? (const T*)S->Gd32 : (const T*)S->Gd64;
+    cublasHandle_t B = S->blas;
+    double wn = 0;
+    FBIM_CUBLAS_TRY2(h, cublasDnrm2(B, n, W, 1, &wn));
+    iters = 0;
+    if (wn == 0) {
+        FBIM_CUDA_TRY(h, cudaMemsetAsync(y, 0, sizeof(double) * n, h->stream));
+        return FBIM_OK;
+    }
+    double* Vl = S->lz;
+    double* tmp = S->w;   // [>= n] scratch from the GMRES workspace
+    double* tmp2 = S->r;
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(Vl, W, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+    double inv = 1.0 / wn;
+    FBIM_CUBLAS_TRY2(h, cublasDscal(B, n, &inv, Vl, 1));
+    std::vector<double> alpha, beta, cprev, c;
+    const double one = 1.0, mone = -1.0, zero = 0.0;
+    std::vector<double> hc(2 * (max_iter + 1));
+    for (int k = 0; k < max_iter; ++k) {
+        double* vk = Vl + (size_t)k * n;
+        // w = G M(r) G^T v_k
+        FBIM_TRY(block_apply<T>(h, G, vk, tmp));
+        FBIM_TRY(apply_operator<T>(h, tmp, tmp2, 1));
+        FBIM_TRY(block_apply<T>(h, G, tmp2, tmp));
+        // alpha_k and full reorthogonalisation (classical Gram-Schmidt, twice)
+        FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, Vl, n, tmp, 1, &zero, S->lh, 1));
+        FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, Vl, n, S->lh, 1, &one, tmp, 1));
+        FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, Vl, n, tmp, 1, &zero,
+                                        S->lh + (max_iter + 1), 1));
+        FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, Vl, n, S->lh + (max_iter + 1), 1, &one,
+                                        tmp, 1));
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->lh, sizeof(double) * 2 * (max_iter + 1),
+                                         cudaMemcpyDeviceToHost, h->stream));
+        double bn = 0;
+        FBIM_CUBLAS_TRY2(h, cublasDnrm2(B, n, tmp, 1, &bn));
+        FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        alpha.push_back(hc[k] + hc[(max_iter + 1) + k]);
+        beta.push_back(bn);
+        ++iters;
+        c = lanczos_coeffs(alpha, beta, k + 1, wn);
+        double dn = 0, cn = 0;
+        for (int i = 0; i <= k; ++i) {
+            double prev = i < (int)cprev.size() ? cprev[i] : 0.0;
+            dn += (c[i] - prev) * (c[i] - prev);
+            cn += c[i] * c[i];
+        }
+        cprev = c;
+        if (!std::isfinite(bn) || !std::isfinite(cn)) {
+            h->fail("Lanczos iterate is not finite");
+            return FBIM_ERR_NONFINITE;
+        }
+        bool converged = (k > 0 && std::sqrt(dn) <= tol * std::sqrt(cn)) || bn <= 1e-14 * wn;
+        if (converged || k + 1 == max_iter) break;
+        double ib = 1.0 / bn;
+        double* vn = Vl + (size_t)(k + 1) * n;
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(vn, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+        FBIM_CUBLAS_TRY2(h, cublasDscal(B, n, &ib, vn, 1));
+    }
+    // y = G^+ V c
+    const int k = (int)c.size();
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->lh, c.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+    FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_N, n, k, &one, Vl, n, S->lh, 1, &zero, tmp, 1));
+    FBIM_TRY(block_apply<T>(h, Gd, tmp, y));
+    return FBIM_OK;
+}
+
+}  // namespace
+
+fbim_status brownian_slip(fbim_handle_s* h, unsigned long long seed, unsigned long long counter, double kT, double dt,
+                          const double* W_r, const double* Z_w, double tol, int max_iter, double* slip,
+                          int* lanczos_iters) {
+    FBIM_TRY(ensure_solver(h));
+    Solver* S = h->solver;
+    const int n = 2 * h->N;
+    double* Wn = S->d;  // [>= n] scratch
+    if (!W_r) {
+        k_philox_normals<<<(unsigned)((n / 2 + 256) / 256), 256, 0, h->stream>>>((size_t)n, seed, 0u,
+                                                                                (unsigned)counter, Wn);
+        FBIM_CUDA_TRY(h, cudaGetLastError());
+        W_r = Wn;
+    }
+    int it = 0;
+    double* near = S->t;
+    double* far = slip;
+    if (h->precision == FBIM_FP32) {
+        FBIM_TRY(near_field<float>(h, W_r, tol, max_iter, near, it));
+        FBIM_TRY(apply_noise<float>(h, Z_w, seed, (unsigned)counter, far));
+    } else {
+        FBIM_TRY(near_field<double>(h, W_r, tol, max_iter, near, it));
+        FBIM_TRY(apply_noise<double>(h, Z_w, seed, (unsigned)counter, far));
+    }
+    const double sc = std::sqrt(2.0 * kT / dt);
+    k_combine<<<(n + 255) / 256, 256, 0, h->stream>>>(n, sc, near, sc, far, slip);
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (lanczos_iters) *lanczos_iters = it;
+    return FBIM_OK;
+}
+
+}  // namespace fbim
+
+extern "C" fbim_status fbim_brownian_slip(fbim_handle h, uint64_t seed, uint64_t counter, double kT, double dt,
+                                          const double* W_r_dev, const double* Z_w_dev, double tol, int max_iter,
+                                          double* slip_dev, int* lanczos_iters) {
+    if (!h || !slip_dev || !(dt > 0) || !(kT >= 0) || !(tol > 0) || max_iter <= 0) return FBIM_ERR_INVALID_ARG;
+    try {
+        if (cudaSetDevice(h->device) != cudaSuccess) return FBIM_ERR_CUDA;
+        return fbim::brownian_slip(h, seed, counter, kT, dt, W_r_dev, Z_w_dev, tol, max_iter, slip_dev,
+                                   lanczos_iters);
+    } catch (...) {
+        h->fail("unexpected host exception in fbim_brownian_slip");
+        return FBIM_ERR_SETUP;
+    }
+}
+
+extern "C" fbim_status fbim_philox_normals(fbim_handle h, uint64_t seed, uint32_t stream, uint32_t counter,
+                                           size_t n, double* out_dev) {
+    if (!h || !out_dev) return FBIM_ERR_INVALID_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return FBIM_ERR_CUDA;
+    if (n == 0) return FBIM_OK;
+    fbim::k_philox_normals<<<(unsigned)(((n + 1) / 2 + 255) / 256), 256, 0, h->stream>>>(n, seed, stream, counter,
+                                                                                    out_dev);
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    return FBIM_OK;
+}

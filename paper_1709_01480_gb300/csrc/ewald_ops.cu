@@ -498,6 +498,103 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     return FBIM_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Far-field noise (Sec. 3.3, Eq. sqrtMwave): (M(w))^1/2 W(w) = S* F* C* B^1/2 W(w).
+// The half spectrum is filled directly with
+//   u(k) = h^2 (eta V)^-1/2 (1 + k^2/4xi^2)^1/2 e^{-(1 - eta_s) k^2/8xi^2} / k (I - k k^T/k^2) W(kappa)
+// (B^1/2 with one Gaussian deconvolution and the interpolation weight h^2), then
+// inverse FFT and interpolation.  W(kappa) follows the Hermitian layout of the
+// oracle: of each conjugate pair the member with the smaller index j_y M + j_x
+// (j = kappa mod M) takes (Z[..][0] + i Z[..][1]) / sqrt 2, the other its conjugate;
+// kappa = 0 and the Nyquist lines are zero (their Hasimoto weight is below the
+// tolerance by the grid rule).  Z[j_y][j_x][comp][re/im] are standard normals,
+// given by the caller or drawn from Philox stream 1 at index
+// ((j_y M + j_x) 2 + comp) 2 + re/im.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_noise_spec(int M, T twopi_L, T inv4xi2, T one_minus_eta, T pref, const double* __restrict__ Z,
+                             unsigned long long seed, unsigned counter, typename Cplx<T>::type* __restrict__ spec) {
+    const int Mh = M / 2 + 1;
+    const size_t n = (size_t)M * Mh;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int r = (int)(i / Mh), c = (int)(i - (size_t)r * Mh);
+    typename Cplx<T>::type* ux = spec;
+    typename Cplx<T>::type* uy = spec + n;
+    if ((r == 0 && c == 0) || c == M / 2 || r == M / 2) {
+        ux[i].x = ux[i].y = T(0);
+        uy[i].x = uy[i].y = T(0);
+        return;
+    }
+    // canonical member of the conjugate pair {(r, c), (-r mod M, -c mod M)}
+    int jy = r, jx = c;
+    double sg = 1.0;
+    if (r > M / 2) {
+        jy = M - r;
+        jx = (M - c) % M;
+        sg = -1.0;
+    }
+    double zr[2], zi[2];
+    const size_t base = (size_t)jy * M + jx;
+    if (Z) {
+        const double* z = Z + base * 4;
+        zr[0] = z[0];
+        zi[0] = z[1];
+        zr[1] = z[2];
+        zi[1] = z[3];
+    } else {
+        double2 a = philox_normals(seed, 1u, counter, base * 2);
+        double2 b = philox_normals(seed, 1u, counter, base * 2 + 1);
+        zr[0] = a.x;
+        zi[0] = a.y;
+        zr[1] = b.x;
+        zi[1] = b.y;
+    }
+    const double is2 = 0.70710678118654752440;
+    const T wxr = (T)(zr[0] * is2), wxi = (T)(sg * zi[0] * is2);
+    const T wyr = (T)(zr[1] * is2), wyi = (T)(sg * zi[1] * is2);
+    const int ky_i = r < M / 2 ? r : r - M;
+    const T kx = twopi_L * T(c), ky = twopi_L * T(ky_i);
+    const T k2 = kx * kx + ky * ky;
+    const T ik2 = T(1) / k2;
+    const T q = k2 * inv4xi2;
+    const T sc = pref * sqrt((T(1) + q) * ik2) * dev_exp(T(-0.5) * one_minus_eta * q);
+    const T pxx = T(1) - kx * kx * ik2, pyy = T(1) - ky * ky * ik2, pxy = -kx * ky * ik2;
+    ux[i].x = sc * (pxx * wxr + pxy * wyr);
+    ux[i].y = sc * (pxx * wxi + pxy * wyi);
+    uy[i].x = sc * (pxy * wxr + pyy * wyr);
+    uy[i].y = sc * (pxy * wxi + pyy * wyi);
+}
+
+template <typename T>
+fbim_status apply_noise(fbim_handle_s* h, const double* Z, unsigned long long seed, unsigned counter, double* out) {
+    FBIM_TRY(ensure_ewald<T>(h));
+    auto& e = bufs<T>(h);
+    using T2 = typename V2<T>::type;
+    using C = typename Cplx<T>::type;
+    const int N = h->N, tb = 256;
+    const size_t M = h->M, Mh = h->M / 2 + 1, ns = M * Mh;
+    const double V = h->L * h->L;
+    k_noise_spec<T><<<(unsigned)((ns + tb - 1) / tb), tb, 0, h->stream>>>(
+        (int)M, (T)(2.0 * M_PI / h->L), (T)(1.0 / (4.0 * h->xi * h->xi)), (T)(1.0 - h->eta_s),
+        (T)(h->h * h->h / std::sqrt(h->eta * V)), Z, seed, counter, (C*)e.spec);
+    FBIM_CUFFT_TRY(h, FftType<T>::i(e.plan_i, (C*)e.spec, e.grid));
+    const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
+    const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
+    const T ah2 = (T)(alpha * h->h * h->h);
+    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
+    if (e.wave_variant == 1)
+        warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.grid, e.v_t);
+    else
+        tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
+    k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, 0, 1, h->slot, h->tslot,
+                                                         (const T2*)e.v_s, (const T2*)e.v_t, h->Q, h->band_dev,
+                                                         (const double2*)out, (double2*)out);
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    return FBIM_OK;
+}
+
 template <typename T>
 static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.off);
@@ -528,5 +625,7 @@ template fbim_status refresh_offsets<double>(fbim_handle_s*);
 template fbim_status refresh_offsets<float>(fbim_handle_s*);
 template fbim_status apply_operator<double>(fbim_handle_s*, const double*, double*, int);
 template fbim_status apply_operator<float>(fbim_handle_s*, const double*, double*, int);
+template fbim_status apply_noise<double>(fbim_handle_s*, const double*, unsigned long long, unsigned, double*);
+template fbim_status apply_noise<float>(fbim_handle_s*, const double*, unsigned long long, unsigned, double*);
 
 }  // namespace fbim

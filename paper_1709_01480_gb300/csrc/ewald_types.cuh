@@ -35,6 +35,39 @@ __device__ __forceinline__ T kernel_a(const ChebE1<T>& ce, T z) {
     return S - T(0.5) * dev_log(z);
 }
 
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of
+//   (hi0, lo0) = mulhilo(0xD2511F53, x0), (hi1, lo1) = mulhilo(0xCD9E8D57, x2),
+//   x = (hi1 ^ x1 ^ k0, lo1, hi0 ^ x3 ^ k1, lo0),
+// with the key bumped by (0x9E3779B9, 0xBB67AE85) between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 x, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const unsigned hi0 = __umulhi(0xD2511F53u, x.x), lo0 = 0xD2511F53u * x.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, x.z), lo1 = 0xCD9E8D57u * x.z;
+        x = make_uint4(hi1 ^ x.y ^ k.x, lo1, hi0 ^ x.w ^ k.y, lo0);
+    }
+    return x;
+}
+
+// Two standard normals from block `idx` of (seed, stream, counter): 53-bit uniforms
+// u1 = (x0, x1), u2 = (x2, x3) in (0, 1), Box-Muller in FP64.
+__device__ __forceinline__ double2 philox_normals(unsigned long long seed, unsigned stream, unsigned counter,
+                                                  unsigned long long idx) {
+    uint4 c = make_uint4((unsigned)(idx & 0xffffffffull), (unsigned)(idx >> 32), stream, counter);
+    uint2 k = make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+    uint4 x = philox4x32_10(c, k);
+    const double u1 = ((double)(x.x >> 5) * 67108864.0 + (double)(x.y >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+    const double u2 = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+    const double rad = sqrt(-2.0 * log(u1));
+    double s, c2;
+    sincospi(2.0 * u2, &s, &c2);
+    return make_double2(rad * c2, rad * s);
+}
+
 struct TileGeom {
     int M, TS, n_tile, P, hw;
 };

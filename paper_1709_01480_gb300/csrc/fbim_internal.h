@@ -129,6 +129,9 @@ struct fbim_handle_s {
     fbim::EwaldBuffers<float> e32;
 
     std::vector<double> host_ref;
+    std::vector<double> host_band;   // symmetrised M(a)_ref band (host copy)
+    double* rot = nullptr;           // [n_b][2] (cos theta, sin theta) of each body
+    struct Solver* solver = nullptr; // preconditioners and Krylov workspace (solver.cu)
 
     // ---- stage timing (fbim_set_timing) ------------------------------------
     bool timing = false;
@@ -152,17 +155,26 @@ double host_e1(double z);
 fbim_status alpert_rule(int order, std::vector<double>& v, std::vector<double>& w, int& a, std::string& err);
 fbim_status alpert_reference_band(fbim_handle_s* h, std::vector<double>& band_out);
 void e1_chebyshev(double zmax, int deg, std::vector<double>& coef);
+void g_real_host(double rx, double ry, double xi, double eta, double G[4]);
+void reference_blocks(fbim_handle_s* h, const std::vector<double>& band_sym, std::vector<double>& Mr,
+                      std::vector<double>& Mfull);
 fbim_status choose_ewald(double L, double r_c, double tol, double xi_in, int& n_box, double& r_c_out,
                          double& xi, int& M, int& P, double& eta_s, std::string& err);
 
 // geometry (geometry.cu)
 fbim_status build_geometry(fbim_handle_s* h);
 
+// solvers (solver.cu)
+void free_solver(fbim_handle_s* h);
+
 // operators (ewald_ops.cu)
 template <typename T> fbim_status ensure_ewald(fbim_handle_s* h);
 template <typename T> fbim_status refresh_offsets(fbim_handle_s* h);
 // which: bit 0 = real space (pairs + Alpert), bit 1 = wave space
 template <typename T> fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int which);
+// far-field noise (M(w))^1/2 W(w) into out [N][2]; Z = caller normals [M][M][2][2] or NULL (Philox)
+template <typename T>
+fbim_status apply_noise(fbim_handle_s* h, const double* Z, unsigned long long seed, unsigned counter, double* out);
 void free_ewald(fbim_handle_s* h);
 
 }  // namespace fbim

@@ -114,6 +114,15 @@ __global__ void k_tile_of(int N, const int2* __restrict__ gbase, int TS, int n_t
     tile[m] = (b.y / TS) * n_tile + b.x / TS;
 }
 
+__global__ void k_rot(int n_b, const double* __restrict__ Q, double* __restrict__ rot) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_b) return;
+    double c, s;
+    sincos(Q[3 * b + 2], &s, &c);
+    rot[2 * b] = c;
+    rot[2 * b + 1] = s;
+}
+
 }  // namespace
 
 fbim_status build_geometry(fbim_handle_s* h) {
@@ -137,6 +146,7 @@ fbim_status build_geometry(fbim_handle_s* h) {
     // beyond the rounding of the shared-memory accumulation)
     k_scatter_slots<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->tile_tmp, h->tile_start, h->tile_fill, h->tperm,
                                                              h->tslot);
+    k_rot<<<(h->n_b + tb - 1) / tb, tb, 0, h->stream>>>(h->n_b, h->Q, h->rot);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     if (h->e64.ready) FBIM_TRY(refresh_offsets<double>(h));
     if (h->e32.ready) FBIM_TRY(refresh_offsets<float>(h));

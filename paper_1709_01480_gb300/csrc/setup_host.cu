@@ -345,8 +345,6 @@ fbim_status alpert_rule(int order, std::vector<double>& vout, std::vector<double
 // l are Lagrange weights over the order+2 nodes nearest to the auxiliary point.
 // Stored symmetrised, (M(a) + M(a)^T)/2, as [n_p][2 band + 1][2][2].
 // ---------------------------------------------------------------------------
-namespace {
-
 void g_real_host(double rx, double ry, double xi, double eta, double G[4]) {
     double r2 = rx * rx + ry * ry;
     double z = xi * xi * r2;
@@ -359,6 +357,8 @@ void g_real_host(double rx, double ry, double xi, double eta, double G[4]) {
     G[2] = G[1];
     G[3] = c * (a + b * ry * ry);
 }
+
+namespace {
 
 struct TrigCurve {
     int n;
@@ -468,6 +468,112 @@ fbim_status alpert_reference_band(fbim_handle_s* h, std::vector<double>& band_ou
             d[3] = 0.5 * (a1[3] + a2[3]);
         }
     return FBIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Dense reference blocks for the preconditioners (Sec. 3.4): the reference body
+// alone in the periodic box.
+//   M(r)_ref = M(t)_ref + M(a)_ref,sym      (real space, used by the Lanczos G_ref)
+//   M_ref    = M(r)_ref + M(w)_ref          (used by the GMRES block preconditioner)
+// M(w)_ref[m][n] = G^(w)_xi(x_m - x_n) is evaluated through the periodic Stokeslet,
+// which the Hasimoto split reproduces for any splitting parameter: with a second,
+// small xi' (real space over a few images, a few hundred Fourier modes),
+//   G^(w)_xi(r) = sum_p G^(r)_xi'(r + pL) + G^(w)_xi'(r) - sum_p G^(r)_xi(r + pL),
+// and at r = 0 the log singularities cancel to (1/4 pi eta) ln(xi/xi') I.
+// Row-major [2 n_p][2 n_p], index 2 m + c.
+// ---------------------------------------------------------------------------
+void reference_blocks(fbim_handle_s* h, const std::vector<double>& band_sym, std::vector<double>& Mr,
+                      std::vector<double>& Mfull) {
+    const int n = h->n_p, n2 = 2 * n;
+    const double L = h->L, xi = h->xi, eta = h->eta;
+    const double* X = h->host_ref.data();
+    Mr.assign((size_t)n2 * n2, 0.0);
+    Mfull.assign((size_t)n2 * n2, 0.0);
+    auto add = [&](std::vector<double>& A, int m, int k, const double G[4], double s) {
+        A[(size_t)(2 * m) * n2 + 2 * k] += s * G[0];
+        A[(size_t)(2 * m) * n2 + 2 * k + 1] += s * G[1];
+        A[(size_t)(2 * m + 1) * n2 + 2 * k] += s * G[2];
+        A[(size_t)(2 * m + 1) * n2 + 2 * k + 1] += s * G[3];
+    };
+    const double cut = 8.0 / xi, cut2 = cut * cut;
+    // M(t)_ref: G^(r)_xi over the periodic images, m != n (the p = 0 self term excluded)
+    for (int m = 0; m < n; ++m)
+        for (int k = 0; k < n; ++k) {
+            const int ni = (int)std::ceil(cut / L) + 1;
+            for (int px = -ni; px <= ni; ++px)
+                for (int py = -ni; py <= ni; ++py) {
+                    if (m == k && px == 0 && py == 0) continue;
+                    double rx = X[2 * m] - X[2 * k] + px * L, ry = X[2 * m + 1] - X[2 * k + 1] + py * L;
+                    double r2 = rx * rx + ry * ry;
+                    if (r2 >= cut2 || r2 == 0) continue;
+                    double G[4];
+                    g_real_host(rx, ry, xi, eta, G);
+                    add(Mr, m, k, G, 1.0);
+                }
+        }
+    // + M(a)_ref (symmetrised band)
+    const int B = 2 * h->band + 1;
+    for (int m = 0; m < n; ++m)
+        for (int o = -h->band; o <= h->band; ++o) {
+            int k = ((m + o) % n + n) % n;
+            const double* a = &band_sym[((size_t)m * B + (o + h->band)) * 4];
+            add(Mr, m, k, a, 1.0);
+        }
+    Mfull = Mr;
+    // M(w)_ref through the small-xi' Ewald sum
+    const double xp = 6.0 / L;
+    const double cutp = 8.0 / xp;
+    const int nip = (int)std::ceil(cutp / L) + 1;
+    const double kcut = 2.0 * xp * std::sqrt(40.0);
+    const int kmax = (int)std::ceil(kcut * L / (2.0 * M_PI));
+    struct Mode { double kx, ky, w; };
+    std::vector<Mode> modes;
+    for (int a = -kmax; a <= kmax; ++a)
+        for (int b = -kmax; b <= kmax; ++b) {
+            if (a == 0 && b == 0) continue;
+            double kx = 2.0 * M_PI * a / L, ky = 2.0 * M_PI * b / L, k2 = kx * kx + ky * ky;
+            if (k2 > kcut * kcut) continue;
+            double q = k2 / (4.0 * xp * xp);
+            modes.push_back({kx, ky, (1.0 + q) * std::exp(-q) / k2 / (eta * L * L)});
+        }
+    for (int m = 0; m < n; ++m)
+        for (int k = m; k < n; ++k) {
+            double rx0 = X[2 * m] - X[2 * k], ry0 = X[2 * m + 1] - X[2 * k + 1];
+            double G[4] = {0, 0, 0, 0};
+            for (const Mode& md : modes) {
+                double c = std::cos(md.kx * rx0 + md.ky * ry0) * md.w;
+                double k2 = md.kx * md.kx + md.ky * md.ky;
+                G[0] += c * (1.0 - md.kx * md.kx / k2);
+                G[1] -= c * md.kx * md.ky / k2;
+                G[3] += c * (1.0 - md.ky * md.ky / k2);
+            }
+            G[2] = G[1];
+            for (int px = -nip; px <= nip; ++px)
+                for (int py = -nip; py <= nip; ++py) {
+                    double rx = rx0 + px * L, ry = ry0 + py * L;
+                    double r2 = rx * rx + ry * ry;
+                    if (r2 == 0) continue;
+                    double Gp[4], Gx[4];
+                    if (r2 < cutp * cutp) {
+                        g_real_host(rx, ry, xp, eta, Gp);
+                        for (int t = 0; t < 4; ++t) G[t] += Gp[t];
+                    }
+                    if (r2 < cut2) {
+                        g_real_host(rx, ry, xi, eta, Gx);
+                        for (int t = 0; t < 4; ++t) G[t] -= Gx[t];
+                    }
+                }
+            if (m == k) {
+                double d = std::log(xi / xp) / (4.0 * M_PI * eta);
+                G[0] += d;
+                G[3] += d;
+            }
+            add(Mfull, m, k, G, 1.0);
+            if (k != m) {
+                double Gt[4] = {G[0], G[2], G[1], G[3]};
+                add(Mfull, k, m, Gt, 1.0);
+            }
+        }
 }
 
 }  // namespace fbim

@@ -1,0 +1,608 @@
+// First-kind mobility solve (Sec. 3.1, Eq. discreteSaddlePoint) by right-
+// preconditioned flexible GMRES with the block-diagonal preconditioner of
+// Sec. 3.4 (Eqs. preconditionerGMRES, approximate-body-mobility, M-block-inverse).
+//
+// Unknowns x = [mu; U] (2N + 3 n_b, FP64); the saddle operator is
+//     A x = [ M mu - K U ; -K^T mu ],  right-hand side b = -[slip; F].
+// The preconditioner solves, body by body, [[M~, -K], [-K^T, 0]] [mu; U] = [r_mu; r_U]
+// with M~_bb^+ = R_b M_ref^+ R_b^T:
+//     z = R^T r_mu,  g = M_ref^+ z  (one GEMM over all bodies),
+//     U' = -N~_ref (R^T r_U + K_ref^T g),  mu' = g + H U'  (H = M_ref^+ K_ref),
+//     mu = R mu',  U = R U'   (R acts on (u_x, u_y) and leaves omega alone),
+// where N~_ref = (K_ref^T M_ref^+ K_ref)^-1 is 3 x 3.  M_ref is the reference
+// body alone in the periodic box (host-built, eigendecomposed with cuSOLVER);
+// eigenvalues below 1e-12 of the largest in magnitude are dropped from the
+// pseudo-inverse (a slightly negative near-null mode is kept, not dropped).
+//
+// Precision: FBIM_FP64 handles run FGMRES on the FP64 operator.  FBIM_FP32
+// handles run iterative refinement: the outer residual b - A x uses the FP64
+// operator; each correction is an FGMRES solve with the FP32 operator and an
+// FP32 preconditioner GEMM; Krylov vectors and orthogonalisation stay FP64.
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "fbim_internal.h"
+
+#include "solver.cuh"
+
+namespace fbim {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_rot_in(int N, int n_p, const double* __restrict__ rot, const double* __restrict__ in,
+                         T* __restrict__ z) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    int b = m / n_p;
+    double c = rot[2 * b], s = rot[2 * b + 1];
+    double ux = in[2 * m], uy = in[2 * m + 1];
+    z[2 * m] = (T)(c * ux + s * uy);
+    z[2 * m + 1] = (T)(-s * ux + c * uy);
+}
+
+// One block per body: U' = -N~ (R^T r_U + K_ref^T g), mu = R (g + H U').
+template <typename T>
+__global__ void k_body_solve(int n_p, const double* __restrict__ ref, const double* __restrict__ rot,
+                             const T* __restrict__ g, const T* __restrict__ H, const double* __restrict__ rU,
+                             double nt0, double nt1, double nt2, double nt3, double nt4, double nt5, double nt6,
+                             double nt7, double nt8, double* __restrict__ out_mu, double* __restrict__ out_U) {
+    const int b = blockIdx.x;
+    const int n2 = 2 * n_p;
+    const T* gb = g + (size_t)b * n2;
+    double sx = 0, sy = 0, st = 0;
+    for (int j = threadIdx.x; j < n_p; j += blockDim.x) {
+        double gx = (double)gb[2 * j], gy = (double)gb[2 * j + 1];
+        sx += gx;
+        sy += gy;
+        st += ref[2 * j] * gy - ref[2 * j + 1] * gx;
+    }
+    __shared__ double red[3][32];
+    __shared__ double Up[3];
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        st += __shfl_xor_sync(0xffffffffu, st, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = sx;
+        red[1][warp] = sy;
+        red[2][warp] = st;
+    }
+    __syncthreads();
+    const double c = rot[2 * b], s = rot[2 * b + 1];
+    if (threadIdx.x == 0) {
+        double tx = 0, ty = 0, tt = 0;
+        for (int w = 0; w < nw; ++w) {
+            tx += red[0][w];
+            ty += red[1][w];
+            tt += red[2][w];
+        }
+        // R^T r_U + K_ref^T g
+        double ax = c * rU[3 * b] + s * rU[3 * b + 1] + tx;
+        double ay = -s * rU[3 * b] + c * rU[3 * b + 1] + ty;
+        double at = rU[3 * b + 2] + tt;
+        double u0 = -(nt0 * ax + nt1 * ay + nt2 * at);
+        double u1 = -(nt3 * ax + nt4 * ay + nt5 * at);
+        double u2 = -(nt6 * ax + nt7 * ay + nt8 * at);
+        Up[0] = u0;
+        Up[1] = u1;
+        Up[2] = u2;
+        out_U[3 * b] = c * u0 - s * u1;
+        out_U[3 * b + 1] = s * u0 + c * u1;
+        out_U[3 * b + 2] = u2;
+    }
+    __syncthreads();
+    const double u0 = Up[0], u1 = Up[1], u2 = Up[2];
+    for (int i = threadIdx.x; i < n_p; i += blockDim.x) {
+        double mx = (double)gb[2 * i] + (double)H[2 * i] * u0 + (double)H[n2 + 2 * i] * u1 +
+                    (double)H[2 * n2 + 2 * i] * u2;
+        double my = (double)gb[2 * i + 1] + (double)H[2 * i + 1] * u0 + (double)H[n2 + 2 * i + 1] * u1 +
+                    (double)H[2 * n2 + 2 * i + 1] * u2;
+        size_t m = (size_t)b * n_p + i;
+        out_mu[2 * m] = c * mx - s * my;
+        out_mu[2 * m + 1] = s * mx + c * my;
+    }
+}
+
+// y_mu -= K U at every node; y_U = -K^T mu per body (one block per body).
+__global__ void k_saddle_K(int n_p, const double* __restrict__ ref, const double* __restrict__ rot,
+                           const double* __restrict__ mu, const double* __restrict__ U, double* __restrict__ ymu,
+                           double* __restrict__ yU) {
+    const int b = blockIdx.x;
+    const double c = rot[2 * b], s = rot[2 * b + 1];
+    const double ux = U[3 * b], uy = U[3 * b + 1], om = U[3 * b + 2];
+    double fx = 0, fy = 0, tq = 0;
+    for (int j = threadIdx.x; j < n_p; j += blockDim.x) {
+        // x - q = R gamma_ref
+        double rx = c * ref[2 * j] - s * ref[2 * j + 1];
+        double ry = s * ref[2 * j] + c * ref[2 * j + 1];
+        size_t m = (size_t)b * n_p + j;
+        ymu[2 * m] -= ux - om * ry;
+        ymu[2 * m + 1] -= uy + om * rx;
+        double mx = mu[2 * m], my = mu[2 * m + 1];
+        fx += mx;
+        fy += my;
+        tq += rx * my - ry * mx;
+    }
+    __shared__ double red[3][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        tq += __shfl_xor_sync(0xffffffffu, tq, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
+        red[0][warp] = fx;
+        red[1][warp] = fy;
+        red[2][warp] = tq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, bb = 0, cc = 0;
+        for (int w = 0; w < nw; ++w) {
+            a += red[0][w];
+            bb += red[1][w];
+            cc += red[2][w];
+        }
+        yU[3 * b] = -a;
+        yU[3 * b + 1] = -bb;
+        yU[3 * b + 2] = -cc;
+    }
+}
+
+__global__ void k_axpby(int n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_neg_rhs(int n_mu, int n_U, const double* __restrict__ slip, const double* __restrict__ F,
+                          double* __restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_mu)
+        b[i] = slip ? -slip[i] : 0.0;
+    else if (i < n_mu + n_U)
+        b[i] = -F[i - n_mu];
+}
+
+__global__ void k_check_finite(int n, const double* __restrict__ x, int* __restrict__ flag) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(x[i])) atomicOr(flag, 1);
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+#define FBIM_CUBLAS_TRY(h, expr)                                                        \
+    do {                                                                                \
+        cublasStatus_t s__ = (expr);                                                    \
+        if (s__ != CUBLAS_STATUS_SUCCESS) {                                             \
+            (h)->fail(std::string(#expr) + ": cublas error " + std::to_string((int)s__)); \
+            return FBIM_ERR_CUDA;                                                       \
+        }                                                                               \
+    } while (0)
+
+// Symmetric eigendecomposition of A (row-major n x n, symmetric) with cuSOLVER.
+fbim_status eig_sym(fbim_handle_s* h, const std::vector<double>& A, int n, std::vector<double>& lam,
+                    std::vector<double>& V) {
+    cusolverDnHandle_t sol = nullptr;
+    if (cusolverDnCreate(&sol) != CUSOLVER_STATUS_SUCCESS) {
+        h->fail("cusolverDnCreate failed");
+        return FBIM_ERR_CUDA;
+    }
+    cusolverDnSetStream(sol, h->stream);
+    double *dA = nullptr, *dW = nullptr, *work = nullptr;
+    int* info = nullptr;
+    int lwork = 0;
+    fbim_status st = FBIM_OK;
+    auto done = [&]() {
+        cudaFree(dA);
+        cudaFree(dW);
+        cudaFree(work);
+        cudaFree(info);
+        cusolverDnDestroy(sol);
+    };
+    if (cudaMalloc(&dA, sizeof(double) * n * n) != cudaSuccess || cudaMalloc(&dW, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc(&info, sizeof(int)) != cudaSuccess) {
+        done();
+        h->fail("eig_sym: allocation failed");
+        return FBIM_ERR_OOM;
+    }
+    cudaMemcpyAsync(dA, A.data(), sizeof(double) * n * n, cudaMemcpyHostToDevice, h->stream);
+    if (cusolverDnDsyevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, dW, &lwork) !=
+            CUSOLVER_STATUS_SUCCESS ||
+        cudaMalloc(&work, sizeof(double) * lwork) != cudaSuccess) {
+        done();
+        h->fail("eig_sym: workspace failed");
+        return FBIM_ERR_CUDA;
+    }
+    if (cusolverDnDsyevd(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, dA, n, dW, work, lwork, info) !=
+        CUSOLVER_STATUS_SUCCESS) {
+        done();
+        h->fail("cusolverDnDsyevd failed");
+        return FBIM_ERR_CUDA;
+    }
+    lam.resize(n);
+    V.resize((size_t)n * n);
+    int hinfo = 0;
+    cudaMemcpyAsync(lam.data(), dW, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(V.data(), dA, sizeof(double) * n * n, cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess || hinfo != 0) {
+        h->fail("eig_sym: eigensolver did not converge");
+        st = FBIM_ERR_SETUP;
+    }
+    done();
+    // V is column-major from cuSOLVER (symmetric input): column k = eigenvector k
+    return st;
+}
+
+template <typename Dst>
+fbim_status upload(fbim_handle_s* h, Dst** dst, const std::vector<double>& src) {
+    std::vector<Dst> tmp(src.begin(), src.end());
+    FBIM_CUDA_TRY(h, cudaMalloc(dst, sizeof(Dst) * tmp.size()));
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(*dst, tmp.data(), sizeof(Dst) * tmp.size(), cudaMemcpyHostToDevice, h->stream));
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return FBIM_OK;
+}
+
+// f(A) = V diag(f(lam)) V^T over the eigenvalues kept (others -> 0); row-major result.
+// signed = true keeps |lam| > rel max|lam| (pseudo-inverse of an indefinite block);
+// signed = false keeps lam > rel max|lam| (square roots: non-positive modes are spurious).
+std::vector<double> matrix_function(const std::vector<double>& lam, const std::vector<double>& V, int n, double rel,
+                                    double (*f)(double), bool keep_negative) {
+    double lmax = 0;
+    for (double l : lam) lmax = std::max(lmax, std::fabs(l));
+    std::vector<double> fl(n, 0.0);
+    for (int k = 0; k < n; ++k)
+        if ((keep_negative ? std::fabs(lam[k]) : lam[k]) > rel * lmax) fl[k] = f(lam[k]);
+    std::vector<double> out((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double acc = 0;
+            for (int k = 0; k < n; ++k) acc += V[(size_t)k * n + i] * fl[k] * V[(size_t)k * n + j];
+            out[(size_t)i * n + j] = acc;
+        }
+    return out;
+}
+
+fbim_status setup_solver(fbim_handle_s* h) {
+    if (h->solver) return FBIM_OK;
+    Solver* S = new Solver();
+    h->solver = S;
+    const int n_p = h->n_p, n2 = 2 * n_p;
+    S->n2 = n2;
+    S->n = 2 * h->N + 3 * h->n_b;
+    S->ld = (S->n + 31) / 32 * 32;
+    S->restart = h->restart;
+    std::vector<double> Mr, Mf;
+    reference_blocks(h, h->host_band, Mr, Mf);
+    // block preconditioner: M_ref^+, H = M_ref^+ K_ref, N~ = (K_ref^T M_ref^+ K_ref)^-1
+    std::vector<double> lam, V;
+    FBIM_TRY(eig_sym(h, Mf, n2, lam, V));
+    // the Alpert correction can leave the near-null normal mode slightly negative:
+    // the pseudo-inverse keeps it (it is a genuine eigenvalue of the block)
+    std::vector<double> Mp = matrix_function(lam, V, n2, 1e-12, [](double l) { return 1.0 / l; }, true);
+    const double* g = h->host_ref.data();
+    std::vector<double> K((size_t)n2 * 3, 0.0);  // row-major n2 x 3
+    for (int j = 0; j < n_p; ++j) {
+        K[(2 * j) * 3 + 0] = 1.0;
+        K[(2 * j + 1) * 3 + 1] = 1.0;
+        K[(2 * j) * 3 + 2] = -g[2 * j + 1];
+        K[(2 * j + 1) * 3 + 2] = g[2 * j];
+    }
+    std::vector<double> Hm((size_t)n2 * 3, 0.0);  // column-major n2 x 3
+    for (int i = 0; i < n2; ++i)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0;
+            for (int k = 0; k < n2; ++k) acc += Mp[(size_t)i * n2 + k] * K[k * 3 + c];
+            Hm[(size_t)c * n2 + i] = acc;
+        }
+    double KH[9];
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            double acc = 0;
+            for (int k = 0; k < n2; ++k) acc += K[k * 3 + a] * Hm[(size_t)c * n2 + k];
+            KH[a * 3 + c] = acc;
+        }
+    // 3 x 3 inverse by cofactors
+    double det = KH[0] * (KH[4] * KH[8] - KH[5] * KH[7]) - KH[1] * (KH[3] * KH[8] - KH[5] * KH[6]) +
+                 KH[2] * (KH[3] * KH[7] - KH[4] * KH[6]);
+    if (!(std::fabs(det) > 0)) {
+        h->fail("reference body mobility is singular");
+        return FBIM_ERR_SETUP;
+    }
+    double* N = S->Nt;
+    N[0] = (KH[4] * KH[8] - KH[5] * KH[7]) / det;
+    N[1] = (KH[2] * KH[7] - KH[1] * KH[8]) / det;
+    N[2] = (KH[1] * KH[5] - KH[2] * KH[4]) / det;
+    N[3] = (KH[5] * KH[6] - KH[3] * KH[8]) / det;
+    N[4] = (KH[0] * KH[8] - KH[2] * KH[6]) / det;
+    N[5] = (KH[2] * KH[3] - KH[0] * KH[5]) / det;
+    N[6] = (KH[3] * KH[7] - KH[4] * KH[6]) / det;
+    N[7] = (KH[1] * KH[6] - KH[0] * KH[7]) / det;
+    N[8] = (KH[0] * KH[4] - KH[1] * KH[3]) / det;
+    FBIM_TRY(upload(h, &S->Mpinv64, Mp));
+    FBIM_TRY(upload(h, &S->Mpinv32, Mp));
+    FBIM_TRY(upload(h, &S->H64, Hm));
+    FBIM_TRY(upload(h, &S->H32, Hm));
+    // Lanczos preconditioner: G_ref = M(r)_ref^{-1/2}, G_ref^+ = M(r)_ref^{1/2} (symmetric choice)
+    std::vector<double> lr, Vr;
+    FBIM_TRY(eig_sym(h, Mr, n2, lr, Vr));
+    std::vector<double> G = matrix_function(lr, Vr, n2, 1e-12, [](double l) { return 1.0 / std::sqrt(l); }, false);
+    std::vector<double> Gd = matrix_function(lr, Vr, n2, 1e-12, [](double l) { return std::sqrt(l); }, false);
+    FBIM_TRY(upload(h, &S->G64, G));
+    FBIM_TRY(upload(h, &S->Gd64, Gd));
+    FBIM_TRY(upload(h, &S->G32, G));
+    FBIM_TRY(upload(h, &S->Gd32, Gd));
+    // Krylov workspace
+    const size_t n = S->n, m = S->restart, ld = S->ld;
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->V, sizeof(double) * ld * (m + 1)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->Z, sizeof(double) * ld * m));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->w, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->r, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->d, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->t, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->hcol, sizeof(double) * 2 * (m + 1)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->zbuf, sizeof(double) * 2 * h->N));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->gbuf, sizeof(double) * 2 * h->N));
+    if (cublasCreate(&S->blas) != CUBLAS_STATUS_SUCCESS) {
+        h->fail("cublasCreate failed");
+        return FBIM_ERR_CUDA;
+    }
+    cublasSetStream(S->blas, h->stream);
+    return FBIM_OK;
+}
+
+}  // namespace
+
+void free_solver(fbim_handle_s* h) {
+    Solver* S = h->solver;
+    if (!S) return;
+    for (void* p : {(void*)S->Mpinv64, (void*)S->Mpinv32, (void*)S->H64, (void*)S->H32, (void*)S->G64,
+                    (void*)S->Gd64, (void*)S->G32, (void*)S->Gd32, (void*)S->V, (void*)S->Z, (void*)S->w,
+                    (void*)S->r, (void*)S->d, (void*)S->t, (void*)S->hcol, S->zbuf, S->gbuf, (void*)S->lz,
+                    (void*)S->lh})
+        cudaFree(p);
+    if (S->blas) cublasDestroy(S->blas);
+    delete S;
+    h->solver = nullptr;
+}
+
+fbim_status ensure_solver(fbim_handle_s* h) { return setup_solver(h); }
+
+// ---------------------------------------------------------------------------
+// operators on x = [mu; U]
+// ---------------------------------------------------------------------------
+template <typename T>
+static fbim_status saddle_apply(fbim_handle_s* h, const double* x, double* y) {
+    const int N2 = 2 * h->N;
+    FBIM_TRY(apply_operator<T>(h, x, y, 3));
+    k_saddle_K<<<h->n_b, 128, 0, h->stream>>>(h->n_p, h->ref, h->rot, x, x + N2, y, y + N2);
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    return FBIM_OK;
+}
+
+template <typename T> struct Gemm;
+template <> struct Gemm<double> {
+    static cublasStatus_t run(cublasHandle_t b, int m, int n, int k, const double* A, const double* B, double* C) {
+        const double one = 1.0, zero = 0.0;
+        return cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, m, B, k, &zero, C, m);
+    }
+};
+template <> struct Gemm<float> {
+    static cublasStatus_t run(cublasHandle_t b, int m, int n, int k, const float* A, const float* B, float* C) {
+        const float one = 1.0f, zero = 0.0f;
+        return cublasSgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, m, B, k, &zero, C, m);
+    }
+};
+
+template <typename T>
+static fbim_status precondition(fbim_handle_s* h, const double* in, double* out) {
+    Solver* S = h->solver;
+    const int N = h->N, N2 = 2 * N;
+    T* z = (T*)S->zbuf;
+    T* g = (T*)S->gbuf;
+    k_rot_in<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, h->n_p, h->rot, in, z);
+    const T* Mp = std::is_same<T, float>::value ? (const T*)S->Mpinv32 : (const T*)S->Mpinv64;
+    const T* Hm = std::is_same<T, float>::value ? (const T*)S->H32 : (const T*)S->H64;
+    FBIM_CUBLAS_TRY(h, Gemm<T>::run(S->blas, S->n2, h->n_b, S->n2, Mp, z, g));
+    const double* Nt = S->Nt;
+    k_body_solve<T><<<h->n_b, 128, 0, h->stream>>>(h->n_p, h->ref, h->rot, g, Hm, in + N2, Nt[0], Nt[1], Nt[2],
+                                                   Nt[3], Nt[4], Nt[5], Nt[6], Nt[7], Nt[8], out, out + N2);
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    return FBIM_OK;
+}
+
+// Restarted flexible GMRES for A x = b with the operator and preconditioner in precision T.
+// x holds the initial guess on entry.  Returns the iteration count and the estimated
+// relative residual |b - A x| / |b| of the last cycle.
+template <typename T>
+static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double tol, int max_iter, int& iters,
+                          double& rel_est) {
+    Solver* S = h->solver;
+    const int n = S->n, m = S->restart, ld = S->ld;
+    cublasHandle_t B = S->blas;
+    double bnorm = 0;
+    FBIM_CUBLAS_TRY(h, cublasDnrm2(B, n, b, 1, &bnorm));
+    iters = 0;
+    rel_est = 0;
+    if (bnorm == 0) {
+        FBIM_CUDA_TRY(h, cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
+        return FBIM_OK;
+    }
+    std::vector<double> Hh((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), hc(2 * (m + 1));
+    const double one = 1.0, mone = -1.0, zero = 0.0;
+    const int tb = 256, nb = (n + tb - 1) / tb;
+    while (true) {
+        // r = b - A x
+        FBIM_TRY(saddle_apply<T>(h, x, S->w));
+        k_axpby<<<nb, tb, 0, h->stream>>>(n, 1.0, b, -1.0, S->w);  // w = b - w
+        double beta = 0;
+        FBIM_CUBLAS_TRY(h, cublasDnrm2(B, n, S->w, 1, &beta));
+        rel_est = beta / bnorm;
+        if (!std::isfinite(beta)) {
+            h->fail("GMRES residual is not finite");
+            return FBIM_ERR_NONFINITE;
+        }
+        if (rel_est <= tol || iters >= max_iter) return FBIM_OK;
+        double inv = 1.0 / beta;
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->V, S->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+        FBIM_CUBLAS_TRY(h, cublasDscal(B, n, &inv, S->V, 1));
+        std::fill(gvec.begin(), gvec.end(), 0.0);
+        gvec[0] = beta;
+        int k_used = 0;
+        for (int k = 0; k < m; ++k) {
+            double* vk = S->V + (size_t)k * ld;
+            double* zk = S->Z + (size_t)k * ld;
+            FBIM_TRY(precondition<T>(h, vk, zk));
+            FBIM_TRY(saddle_apply<T>(h, zk, S->w));
+            // classical Gram-Schmidt, twice
+            FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero, S->hcol, 1));
+            FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol, 1, &one, S->w, 1));
+            FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero,
+                                           S->hcol + (m + 1), 1));
+            FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol + (m + 1), 1, &one,
+                                           S->w, 1));
+            double hn = 0;
+            FBIM_CUBLAS_TRY(h, cublasDnrm2(B, n, S->w, 1, &hn));
+            FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->hcol, sizeof(double) * 2 * (m + 1), cudaMemcpyDeviceToHost,
+                                             h->stream));
+            FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            double* col = &Hh[(size_t)k * (m + 1)];
+            for (int i = 0; i <= k; ++i) col[i] = hc[i] + hc[(m + 1) + i];
+            col[k + 1] = hn;
+            if (!std::isfinite(hn)) {
+                h->fail("GMRES iterate is not finite");
+                return FBIM_ERR_NONFINITE;
+            }
+            if (hn > 0) {
+                double ih = 1.0 / hn;
+                double* vn = S->V + (size_t)(k + 1) * ld;
+                FBIM_CUDA_TRY(h, cudaMemcpyAsync(vn, S->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+                FBIM_CUBLAS_TRY(h, cublasDscal(B, n, &ih, vn, 1));
+            }
+            for (int i = 0; i < k; ++i) {
+                double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
+                col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+                col[i] = t0;
+            }
+            double den = std::hypot(col[k], col[k + 1]);
+            cs[k] = den > 0 ? col[k] / den : 1.0;
+            sn[k] = den > 0 ? col[k + 1] / den : 0.0;
+            col[k] = den;
+            col[k + 1] = 0;
+            gvec[k + 1] = -sn[k] * gvec[k];
+            gvec[k] = cs[k] * gvec[k];
+            ++iters;
+            k_used = k + 1;
+            if (std::fabs(gvec[k + 1]) / bnorm <= tol || iters >= max_iter || hn == 0) break;
+        }
+        // y = R^-1 g (upper triangular), x += Z y
+        std::vector<double> y(k_used);
+        for (int i = k_used - 1; i >= 0; --i) {
+            double acc = gvec[i];
+            for (int j = i + 1; j < k_used; ++j) acc -= Hh[(size_t)j * (m + 1) + i] * y[j];
+            y[i] = acc / Hh[(size_t)i * (m + 1) + i];
+        }
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->hcol, y.data(), sizeof(double) * k_used, cudaMemcpyHostToDevice,
+                                         h->stream));
+        FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k_used, &one, S->Z, ld, S->hcol, 1, &one, x, 1));
+    }
+}
+
+// True relative residual |b - A_64 x| / |b| with the FP64 operator.
+static fbim_status true_residual(fbim_handle_s* h, const double* b, const double* x, double* r, double& rel) {
+    Solver* S = h->solver;
+    const int n = S->n;
+    FBIM_TRY(saddle_apply<double>(h, x, r));
+    k_axpby<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0, b, -1.0, r);
+    double rn = 0, bn = 0;
+    FBIM_CUBLAS_TRY(h, cublasDnrm2(S->blas, n, r, 1, &rn));
+    FBIM_CUBLAS_TRY(h, cublasDnrm2(S->blas, n, b, 1, &bn));
+    rel = bn > 0 ? rn / bn : 0.0;
+    return FBIM_OK;
+}
+
+fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip, double tol, int max_iter,
+                           double* U, double* mu_out, int* iters_out, double* res_out) {
+    FBIM_TRY(setup_solver(h));
+    Solver* S = h->solver;
+    const int n = S->n, N2 = 2 * h->N;
+    const int tb = 256, nb = (n + tb - 1) / tb;
+    // b lives in S->t, x in S->d
+    k_neg_rhs<<<nb, tb, 0, h->stream>>>(N2, 3 * h->n_b, slip, F, S->t);
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(S->d, 0, sizeof(double) * n, h->stream));
+    int iters = 0;
+    double rel = 1.0;
+    if (h->precision == FBIM_FP64) {
+        double est = 0;
+        FBIM_TRY(fgmres<double>(h, S->t, S->d, tol, max_iter, iters, est));
+        FBIM_TRY(true_residual(h, S->t, S->d, S->r, rel));
+    } else {
+        // iterative refinement: FP64 residual, FP32 corrections
+        double* corr = nullptr;
+        FBIM_CUDA_TRY(h, cudaMalloc(&corr, sizeof(double) * n));
+        fbim_status st = FBIM_OK;
+        for (int outer = 0; outer < 12; ++outer) {
+            st = true_residual(h, S->t, S->d, S->r, rel);
+            if (st != FBIM_OK || rel <= tol || iters >= max_iter) break;
+            // inner tolerance relative to |r|: aim at tol |b|, but no tighter than the
+            // FP32 operator can deliver
+            double inner = std::max(0.3 * tol / rel, 2e-6);
+            cudaMemsetAsync(corr, 0, sizeof(double) * n, h->stream);
+            int it = 0;
+            double est = 0;
+            st = fgmres<float>(h, S->r, corr, inner, max_iter - iters, it, est);
+            if (st != FBIM_OK) break;
+            iters += it;
+            k_axpby<<<nb, tb, 0, h->stream>>>(n, 1.0, corr, 1.0, S->d);
+        }
+        cudaFree(corr);
+        FBIM_TRY(st);
+    }
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(U, S->d + N2, sizeof(double) * 3 * h->n_b, cudaMemcpyDeviceToDevice,
+                                     h->stream));
+    if (mu_out)
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(mu_out, S->d, sizeof(double) * N2, cudaMemcpyDeviceToDevice, h->stream));
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (iters_out) *iters_out = iters;
+    if (res_out) *res_out = rel;
+    if (!std::isfinite(rel)) {
+        h->fail("mobility solve produced non-finite values");
+        return FBIM_ERR_NONFINITE;
+    }
+    if (rel > tol) {
+        h->fail("GMRES reached the iteration cap before the tolerance");
+        return FBIM_ERR_NOT_CONVERGED;
+    }
+    return FBIM_OK;
+}
+
+// exposed for the Brownian slip
+fbim_status solver_precondition64(fbim_handle_s* h, const double* in, double* out) {
+    return precondition<double>(h, in, out);
+}
+
+}  // namespace fbim
+
+extern "C" fbim_status fbim_mobility_solve(fbim_handle h, const double* F_dev, const double* slip_dev, double tol,
+                                           int max_iter, double* U_dev, double* mu_dev, int* iters,
+                                           double* rel_residual) {
+    if (!h || !F_dev || !U_dev || !(tol > 0) || max_iter <= 0) return FBIM_ERR_INVALID_ARG;
+    try {
+        if (cudaSetDevice(h->device) != cudaSuccess) return FBIM_ERR_CUDA;
+        return fbim::mobility_solve(h, F_dev, slip_dev, tol, max_iter, U_dev, mu_dev, iters, rel_residual);
+    } catch (...) {
+        h->fail("unexpected host exception in fbim_mobility_solve");
+        return FBIM_ERR_SETUP;
+    }
+}

@@ -1,0 +1,32 @@
+// Preconditioner and Krylov workspace of a handle (solver.cu, brownian.cu).
+#pragma once
+#include <cublas_v2.h>
+
+struct Solver {
+    int n2 = 0;                 // 2 n_p
+    int n = 0;                  // 2N + 3 n_b
+    int ld = 0;                 // leading dimension of V and Z: n rounded up to 32 (keeps rows 16-byte aligned)
+    double* Mpinv64 = nullptr;  // [n2][n2] M_ref^+
+    float* Mpinv32 = nullptr;
+    double* H64 = nullptr;      // [3][n2] column-major (n2 x 3): M_ref^+ K_ref
+    float* H32 = nullptr;
+    double Nt[9] = {};          // N~_ref, row-major
+    double* G64 = nullptr;      // [n2][n2] G_ref = M(r)_ref^{-1/2} (principal, spurious modes dropped)
+    double* Gd64 = nullptr;     // [n2][n2] G_ref^+ = M(r)_ref^{1/2}
+    float* G32 = nullptr;
+    float* Gd32 = nullptr;
+    int restart = 0;
+    double* V = nullptr;        // [(m+1)][ld] Krylov basis
+    double* Z = nullptr;        // [m][ld] preconditioned basis
+    double* w = nullptr;        // [n]
+    double* r = nullptr;        // [n]
+    double* d = nullptr;        // [n]
+    double* t = nullptr;        // [n]
+    double* hcol = nullptr;     // [2 (m+1)] dot products
+    void* zbuf = nullptr;       // [N][2] rotated residual (T)
+    void* gbuf = nullptr;       // [N][2] M_ref^+ z (T)
+    cublasHandle_t blas = nullptr;
+    int lanczos_max = 0;        // Lanczos workspace (brownian.cu)
+    double* lz = nullptr;       // [lanczos_max][2N] Lanczos basis
+    double* lh = nullptr;       // [2 lanczos_max] Lanczos dot products / coefficients
+};
