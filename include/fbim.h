@@ -166,6 +166,18 @@ fbim_status fbim_brownian_slip(fbim_handle h, uint64_t seed, uint64_t counter, d
 fbim_status fbim_philox_normals(fbim_handle h, uint64_t seed, uint32_t stream, uint32_t counter, size_t n,
                                 double* out_dev);
 
+/* v = (M(t) + M(a)_sym) mu, the same operator as fbim_apply_real, computed without
+ * allocating any device memory (the paper has no counterpart: this is a library
+ * service).  It is for callers that must not allocate once running, such as a host
+ * that gives all device memory to its own pool at start-up or a time-critical loop.
+ * Works in FP64 on the handle's cell list, with its scratch in a fixed device array
+ * of the library (4 MiB per device, held until exit); the handle may have at most
+ * 131072 nodes, larger handles get FBIM_ERR_INVALID_ARG.  The first call on each
+ * device looks up that array's address (make it before any stream capture).  All
+ * calls share the array: calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  mu_dev, v_dev: double [N][2], 16-byte aligned. */
+fbim_status fbim_apply_real_noalloc(fbim_handle h, const double* mu_dev, double* v_dev);
+
 /* Information about the handle's parameters. */
 fbim_status fbim_get_info(fbim_handle h, fbim_info* info);
 

@@ -35,7 +35,7 @@ EXPORTS = [
     "fbim_apply_stokeslet", "fbim_apply_real", "fbim_apply_wave", "fbim_get_info",
     "fbim_destroy", "fbim_last_error", "fbim_host_expint_e1", "fbim_host_alpert_rule",
     "fbim_set_timing", "fbim_stage_times", "fbim_mobility_solve", "fbim_brownian_slip",
-    "fbim_philox_normals",
+    "fbim_philox_normals", "fbim_apply_real_noalloc",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -83,6 +83,7 @@ _lib.fbim_update_config.argtypes = [_P, _P]
 _lib.fbim_apply_stokeslet.argtypes = [_P, _P, _P]
 _lib.fbim_apply_real.argtypes = [_P, _P, _P]
 _lib.fbim_apply_wave.argtypes = [_P, _P, _P]
+_lib.fbim_apply_real_noalloc.argtypes = [_P, _P, _P]
 _lib.fbim_get_info.argtypes = [_P, ctypes.POINTER(Info)]
 _lib.fbim_destroy.argtypes = [_P]
 _lib.fbim_destroy.restype = None
@@ -195,6 +196,11 @@ class FBIM:
         v = out if out is not None else self._out(mu, (self.n, 2))
         _check(_lib.fbim_apply_real(self._h, _ptr(mu), _ptr(v)), self._h)
         return v
+
+    def apply_real_noalloc(self, mu, out):
+        """Real-space operator into the caller's ``out``; allocates no device memory."""
+        _check(_lib.fbim_apply_real_noalloc(self._h, _ptr(mu), _ptr(out)), self._h)
+        return out
 
     def apply_wave(self, mu, out=None):
         v = out if out is not None else self._out(mu, (self.n, 2))

@@ -83,35 +83,6 @@ template <typename T> struct PairEntry;
 template <> struct __align__(16) PairEntry<float> { float xx, xy, yy; int src; };
 template <> struct __align__(16) PairEntry<double> { double xx, xy, yy; long long src; };
 
-template <typename T, typename F>
-__device__ __forceinline__ void for_each_pair(int t, int n_box, T r_c, T rc2, const int* __restrict__ perm,
-                                              const int* __restrict__ cell, const int* __restrict__ start,
-                                              const typename V2<T>::type* __restrict__ off, F&& f) {
-    int c = cell[perm[t]];
-    int cx = c % n_box, cy = c / n_box;
-    typename V2<T>::type ot = off[t];
-    for (int dy = -1; dy <= 1; ++dy) {
-        int ny = cy + dy;
-        ny += (ny < 0) ? n_box : 0;
-        ny -= (ny >= n_box) ? n_box : 0;
-        T sy = ot.y - T(dy) * r_c;
-        for (int dx = -1; dx <= 1; ++dx) {
-            int nx = cx + dx;
-            nx += (nx < 0) ? n_box : 0;
-            nx -= (nx >= n_box) ? n_box : 0;
-            T sx = ot.x - T(dx) * r_c;
-            int nc = ny * n_box + nx;
-            int lo = start[nc], hi = start[nc + 1];
-            for (int s = lo; s < hi; ++s) {
-                typename V2<T>::type os = off[s];
-                T rx = sx - os.x, ry = sy - os.y;
-                T r2 = rx * rx + ry * ry;
-                if (r2 < rc2 && s != t) f(s, rx, ry, r2);
-            }
-        }
-    }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(128) k_pair_count(int N, int n_box, T r_c, T rc2, const int* __restrict__ perm,
                                                    const int* __restrict__ cell, const int* __restrict__ start,

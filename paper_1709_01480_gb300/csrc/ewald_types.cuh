@@ -68,6 +68,38 @@ __device__ __forceinline__ double2 philox_normals(unsigned long long seed, unsig
     return make_double2(rad * c2, rad * s);
 }
 
+// Visit the sources s != t within r_c of cell-sorted target t over the 9 cells
+// around t's cell; f(s, rx, ry, r2) gets the separation x_t - x_s.  Offsets are
+// measured from each node's cell corner, so the periodic wrap is the cell shift.
+template <typename T, typename F>
+__device__ __forceinline__ void for_each_pair(int t, int n_box, T r_c, T rc2, const int* __restrict__ perm,
+                                              const int* __restrict__ cell, const int* __restrict__ start,
+                                              const typename V2<T>::type* __restrict__ off, F&& f) {
+    int c = cell[perm[t]];
+    int cx = c % n_box, cy = c / n_box;
+    typename V2<T>::type ot = off[t];
+    for (int dy = -1; dy <= 1; ++dy) {
+        int ny = cy + dy;
+        ny += (ny < 0) ? n_box : 0;
+        ny -= (ny >= n_box) ? n_box : 0;
+        T sy = ot.y - T(dy) * r_c;
+        for (int dx = -1; dx <= 1; ++dx) {
+            int nx = cx + dx;
+            nx += (nx < 0) ? n_box : 0;
+            nx -= (nx >= n_box) ? n_box : 0;
+            T sx = ot.x - T(dx) * r_c;
+            int nc = ny * n_box + nx;
+            int lo = start[nc], hi = start[nc + 1];
+            for (int s = lo; s < hi; ++s) {
+                typename V2<T>::type os = off[s];
+                T rx = sx - os.x, ry = sy - os.y;
+                T r2 = rx * rx + ry * ry;
+                if (r2 < rc2 && s != t) f(s, rx, ry, r2);
+            }
+        }
+    }
+}
+
 struct TileGeom {
     int M, TS, n_tile, P, hw;
 };
