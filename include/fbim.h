@@ -160,6 +160,18 @@ fbim_status fbim_brownian_slip(fbim_handle h, uint64_t seed, uint64_t counter, d
                                const double* W_r_dev, const double* Z_w_dev, double tol, int max_iter,
                                double* slip_dev, int* lanczos_iters);
 
+/* One Euler-Maruyama step with a random finite difference (Sec. 4.4, Eq. EM-RFD):
+ *   Q <- Q + dt N F + sqrt(2 kT dt) N^1/2 W + dt kT/delta [N(Q + delta/2 W~) - N(Q - delta/2 W~)] W~,
+ * three saddle solves to tol (the velocity with slip and force, and the two displaced
+ * solves with force W~).  The slip's normals are W_r_dev / Z_w_dev or, when NULL, Philox
+ * (seed, streams 0 and 1, counter 3 step); W~ is W_t_dev (double [n_b][3]) or Philox
+ * (seed, stream 2, counter step).  Q_dev (double [n_b][3], device) is read and
+ * overwritten; the handle is left at the new configuration.  iters: NULL or the GMRES
+ * iterations of the three solves.  Synchronises the stream. */
+fbim_status fbim_rfd_step(fbim_handle h, const double* F_dev, double dt, double kT, double delta, uint64_t seed,
+                          uint64_t step, const double* W_r_dev, const double* Z_w_dev, const double* W_t_dev,
+                          double tol, int max_iter, double* Q_dev, int* iters);
+
 /* n standard normals of (seed, stream, counter) from Philox4x32-10 and Box-Muller:
  * normal i is element i mod 2 of block i / 2, counter block = (i/2 low, i/2 high,
  * stream, counter), key = (seed low, seed high).  out_dev: double [n] (device). */

@@ -35,7 +35,7 @@ EXPORTS = [
     "fbim_apply_stokeslet", "fbim_apply_real", "fbim_apply_wave", "fbim_get_info",
     "fbim_destroy", "fbim_last_error", "fbim_host_expint_e1", "fbim_host_alpert_rule",
     "fbim_set_timing", "fbim_stage_times", "fbim_mobility_solve", "fbim_brownian_slip",
-    "fbim_philox_normals", "fbim_apply_real_noalloc",
+    "fbim_philox_normals", "fbim_apply_real_noalloc", "fbim_rfd_step",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -84,6 +84,7 @@ _lib.fbim_apply_stokeslet.argtypes = [_P, _P, _P]
 _lib.fbim_apply_real.argtypes = [_P, _P, _P]
 _lib.fbim_apply_wave.argtypes = [_P, _P, _P]
 _lib.fbim_apply_real_noalloc.argtypes = [_P, _P, _P]
+_lib.fbim_rfd_step.argtypes = [_P, _P, _D, _D, _D, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P, _D, _I, _P, _IP]
 _lib.fbim_get_info.argtypes = [_P, ctypes.POINTER(Info)]
 _lib.fbim_destroy.argtypes = [_P]
 _lib.fbim_destroy.restype = None
@@ -231,6 +232,16 @@ class FBIM:
                                        None if W_r is None else _ptr(W_r), None if Z_w is None else _ptr(Z_w),
                                        float(tol), int(max_iter), _ptr(out), ctypes.byref(it)), self._h)
         return out, it.value
+
+    def rfd_step(self, F, Q, dt, kT=1.0, delta=1e-3, seed=0, step=0, W_r=None, Z_w=None, W_t=None, tol=1e-6,
+                 max_iter=500):
+        """One EM-RFD step; Q (device [n_b, 3]) is updated in place.  Returns the GMRES iterations."""
+        it = ctypes.c_int(0)
+        opt = lambda t: None if t is None else _ptr(t)
+        _check(_lib.fbim_rfd_step(self._h, _ptr(F), float(dt), float(kT), float(delta), int(seed), int(step),
+                                  opt(W_r), opt(Z_w), opt(W_t), float(tol), int(max_iter), _ptr(Q),
+                                  ctypes.byref(it)), self._h)
+        return it.value
 
     def philox_normals(self, n, seed=0, stream=0, counter=0):
         import torch

@@ -252,9 +252,7 @@ extern "C" fbim_status fbim_update_config(fbim_handle h, const double* Q_dev) {
     if (!h || !Q_dev) return FBIM_ERR_INVALID_ARG;
     return guarded(h, [&]() -> fbim_status {
         FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
-        FBIM_CUDA_TRY(h, cudaMemcpyAsync(h->Q, Q_dev, 3 * h->n_b * sizeof(double), cudaMemcpyDeviceToDevice,
-                                         h->stream));
-        return fbim::build_geometry(h);
+        return fbim::update_positions(h, Q_dev);
     });
 }
 

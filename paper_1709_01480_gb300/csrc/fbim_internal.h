@@ -163,6 +163,8 @@ fbim_status choose_ewald(double L, double r_c, double tol, double xi_in, int& n_
 
 // geometry (geometry.cu)
 fbim_status build_geometry(fbim_handle_s* h);
+// copy body coordinates Q_dev (device, [n_b][3]) into the handle and rebuild the geometry
+fbim_status update_positions(fbim_handle_s* h, const double* Q_dev);
 
 // solvers (solver.cu)
 void free_solver(fbim_handle_s* h);

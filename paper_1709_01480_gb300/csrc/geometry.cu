@@ -153,4 +153,11 @@ fbim_status build_geometry(fbim_handle_s* h) {
     return FBIM_OK;
 }
 
+fbim_status update_positions(fbim_handle_s* h, const double* Q_dev) {
+    if (Q_dev != h->Q)
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(h->Q, Q_dev, 3 * h->n_b * sizeof(double), cudaMemcpyDeviceToDevice,
+                                         h->stream));
+    return build_geometry(h);
+}
+
 }  // namespace fbim

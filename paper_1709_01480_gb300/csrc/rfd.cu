@@ -1,0 +1,117 @@
+// One Euler-Maruyama step with a random finite difference (Sec. 4.4, Eq. EM-RFD):
+//   Q^{n+1} = Q^n + dt N F + sqrt(2 kT dt) N^1/2 W
+//             + dt kT/delta [ N(Q + delta/2 W~) W~ - N(Q - delta/2 W~) W~ ].
+// The first two terms are dt U with U from one saddle solve with right-hand side
+// [slip; F], slip = sqrt(2kT/dt) M^1/2 W (fbim_brownian_slip); the drift needs two
+// solves with force W~ and no slip at the displaced configurations.  Three solves
+// per step, as in the paper.  W~ is drawn from Philox stream 2 (or given).
+#include <cmath>
+
+#include "ewald_types.cuh"
+#include "fbim_internal.h"
+#include "solver.cuh"
+
+namespace fbim {
+
+fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip, double tol, int max_iter,
+                           double* U, double* mu_out, int* iters_out, double* res_out);
+fbim_status brownian_slip(fbim_handle_s* h, unsigned long long seed, unsigned long long counter, double kT, double dt,
+                          const double* W_r, const double* Z_w, double tol, int max_iter, double* slip,
+                          int* lanczos_iters);
+
+fbim_status ensure_solver(fbim_handle_s* h);
+
+namespace {
+
+__global__ void k_wtilde(int n, unsigned long long seed, unsigned counter, double* __restrict__ w) {
+    int blk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * blk >= n) return;
+    double2 z = philox_normals(seed, 2u, counter, (unsigned long long)blk);
+    w[2 * blk] = z.x;
+    if (2 * blk + 1 < n) w[2 * blk + 1] = z.y;
+}
+
+__global__ void k_displace(int n, const double* __restrict__ Q, double a, const double* __restrict__ w,
+                           double* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = Q[i] + a * w[i];
+}
+
+__global__ void k_rfd_update(int n, double* __restrict__ Q, double dt, const double* __restrict__ U, double c,
+                             const double* __restrict__ Up, const double* __restrict__ Um) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) Q[i] += dt * U[i] + c * (Up[i] - Um[i]);
+}
+
+}  // namespace
+
+fbim_status rfd_step(fbim_handle_s* h, const double* F, double dt, double kT, double delta, unsigned long long seed,
+                     unsigned long long step, const double* W_r, const double* Z_w, const double* W_t, double tol,
+                     int max_iter, double* Q, int* iters_total) {
+    const int n3 = 3 * h->n_b, n2 = 2 * h->N, tb = 256;
+    // work: slip [2N], W~, Q+-, U, U+, U- [3 n_b each] (kept in the solver workspace)
+    FBIM_TRY(ensure_solver(h));
+    Solver* S = h->solver;
+    if (!S->rfd) FBIM_CUDA_TRY(h, cudaMalloc(&S->rfd, sizeof(double) * (n2 + 6 * (size_t)n3)));
+    double* work = S->rfd;
+    double* slip = work;
+    double* wt = slip + n2;
+    double* Qd = wt + n3;
+    double* U = Qd + n3;
+    double* Up = U + n3;
+    double* Um = Up + n3;
+    fbim_status st = FBIM_OK;
+    int it = 0, total = 0;
+    auto run = [&]() -> fbim_status {
+        // (1) geometry at Q, slip, and the velocity N F + N^1/2 W
+        FBIM_TRY(update_positions(h, Q));
+        int lz = 0;
+        FBIM_TRY(brownian_slip(h, seed, 3 * step, kT, dt, W_r, Z_w, std::max(tol, 1e-12), 200, slip, &lz));
+        fbim_status s1 = mobility_solve(h, F, slip, tol, max_iter, U, nullptr, &it, nullptr);
+        total += it;
+        if (s1 != FBIM_OK && s1 != FBIM_ERR_NOT_CONVERGED) return s1;
+        // (2) random finite difference of N along W~
+        if (W_t) {
+            FBIM_CUDA_TRY(h, cudaMemcpyAsync(wt, W_t, sizeof(double) * n3, cudaMemcpyDeviceToDevice, h->stream));
+        } else {
+            k_wtilde<<<(n3 / 2 + tb) / tb, tb, 0, h->stream>>>(n3, seed, (unsigned)step, wt);
+        }
+        k_displace<<<(n3 + tb - 1) / tb, tb, 0, h->stream>>>(n3, Q, 0.5 * delta, wt, Qd);
+        FBIM_TRY(update_positions(h, Qd));
+        fbim_status s2 = mobility_solve(h, wt, nullptr, tol, max_iter, Up, nullptr, &it, nullptr);
+        total += it;
+        if (s2 != FBIM_OK && s2 != FBIM_ERR_NOT_CONVERGED) return s2;
+        k_displace<<<(n3 + tb - 1) / tb, tb, 0, h->stream>>>(n3, Q, -0.5 * delta, wt, Qd);
+        FBIM_TRY(update_positions(h, Qd));
+        fbim_status s3 = mobility_solve(h, wt, nullptr, tol, max_iter, Um, nullptr, &it, nullptr);
+        total += it;
+        if (s3 != FBIM_OK && s3 != FBIM_ERR_NOT_CONVERGED) return s3;
+        // (3) update and leave the handle at the new configuration
+        k_rfd_update<<<(n3 + tb - 1) / tb, tb, 0, h->stream>>>(n3, Q, dt, U, dt * kT / delta, Up, Um);
+        FBIM_CUDA_TRY(h, cudaGetLastError());
+        FBIM_TRY(update_positions(h, Q));
+        if (s1 != FBIM_OK || s2 != FBIM_OK || s3 != FBIM_OK) return FBIM_ERR_NOT_CONVERGED;
+        return FBIM_OK;
+    };
+    st = run();
+    cudaStreamSynchronize(h->stream);
+    if (iters_total) *iters_total = total;
+    return st;
+}
+
+}  // namespace fbim
+
+extern "C" fbim_status fbim_rfd_step(fbim_handle h, const double* F_dev, double dt, double kT, double delta,
+                                     uint64_t seed, uint64_t step, const double* W_r_dev, const double* Z_w_dev,
+                                     const double* W_t_dev, double tol, int max_iter, double* Q_dev, int* iters) {
+    if (!h || !F_dev || !Q_dev || !(dt > 0) || !(kT >= 0) || !(delta > 0) || !(tol > 0) || max_iter <= 0)
+        return FBIM_ERR_INVALID_ARG;
+    try {
+        if (cudaSetDevice(h->device) != cudaSuccess) return FBIM_ERR_CUDA;
+        return fbim::rfd_step(h, F_dev, dt, kT, delta, seed, step, W_r_dev, Z_w_dev, W_t_dev, tol, max_iter, Q_dev,
+                              iters);
+    } catch (...) {
+        h->fail("unexpected host exception in fbim_rfd_step");
+        return FBIM_ERR_SETUP;
+    }
+}

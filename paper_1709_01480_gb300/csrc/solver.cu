@@ -370,7 +370,7 @@ void free_solver(fbim_handle_s* h) {
     for (void* p : {(void*)S->Mpinv64, (void*)S->Mpinv32, (void*)S->H64, (void*)S->H32, (void*)S->G64,
                     (void*)S->Gd64, (void*)S->G32, (void*)S->Gd32, (void*)S->V, (void*)S->Z, (void*)S->w,
                     (void*)S->r, (void*)S->d, (void*)S->t, (void*)S->hcol, S->zbuf, S->gbuf, (void*)S->lz,
-                    (void*)S->lh})
+                    (void*)S->lh, (void*)S->rfd})
         cudaFree(p);
     if (S->blas) cublasDestroy(S->blas);
     delete S;

@@ -29,4 +29,5 @@ struct Solver {
     int lanczos_max = 0;        // Lanczos workspace (brownian.cu)
     double* lz = nullptr;       // [lanczos_max][2N] Lanczos basis
     double* lh = nullptr;       // [2 lanczos_max] Lanczos dot products / coefficients
+    double* rfd = nullptr;      // [2N + 6 * 3 n_b] workspace of the random-finite-difference step
 };

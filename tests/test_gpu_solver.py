@@ -168,3 +168,25 @@ def test_brownian_displacement_covariance_is_mobility(torch, fb, tiny):
     print(f"DFDB: max z-score {z.max():.2f}, max rel diag dev {np.max(np.abs(np.diag(C) / d - 1)):.3f}")
     assert z.max() < 4.5
     op.close()
+
+
+def test_fp64_rfd_step_matches_oracle(torch, fb, tiny):
+    """One EM-RFD step (Sec. 4.4, Eq. EM-RFD) with given noise: Q^{n+1} - Q^n against the oracle's."""
+    from oracle import rfd
+    w, xi, grid = tiny["w"], tiny["xi"], tiny["grid"]
+    op = _op(fb, tiny)
+    rng = np.random.default_rng(55)
+    W_r = rng.standard_normal((w.n, 2))
+    Z = rng.standard_normal((grid, grid, 2, 2))
+    Wt = rng.standard_normal((w.n_b, 3))
+    dt, kT, delta = 1e-3, 1.0, 1e-2
+    Q = torch.tensor(w.Q, device="cuda")
+    it = op.rfd_step(torch.tensor(w.F, device="cuda"), Q, dt, kT, delta, W_r=torch.tensor(W_r, device="cuda"),
+                     Z_w=torch.tensor(Z, device="cuda"), W_t=torch.tensor(Wt, device="cuda"), tol=1e-12)
+    dQ = Q.cpu().numpy() - w.Q
+    Q_or = rfd.em_rfd_step(w.Q, w.ref_nodes, w.L, xi, w.F, dt, kT, delta, W_r, Z, Wt)
+    dQ_or = Q_or - w.Q
+    err = _rel(dQ, dQ_or)
+    print(f"rfd step: GMRES iterations {it}, rel err of the displacement {err:.3e}")
+    assert err < 1e-8
+    op.close()
