@@ -83,6 +83,8 @@ typedef struct {
                                 (ordered pairs within r_c plus sliced-ELL padding)     */
     int    wave_variant;     /* spread/interp kernels in use: 0 tile, 1 warp-per-node  */
     double variant_ms[2];    /* autotuner timings (ms) of spread + interp per variant  */
+    long long launches;      /* kernels this library has launched for the handle so far
+                                (library calls such as cuFFT and cuBLAS not included)  */
 } fbim_info;
 
 /* Fill *p with defaults: FP64, order 4, automatic grid and support, eta = 1,

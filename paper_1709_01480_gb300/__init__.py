@@ -60,7 +60,8 @@ class Info(ctypes.Structure):
                 ("alpert_order", ctypes.c_int), ("alpert_nodes", ctypes.c_int),
                 ("alpert_window", ctypes.c_int), ("alpert_band", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tile", ctypes.c_int), ("pair_entries", ctypes.c_longlong),
-                ("wave_variant", ctypes.c_int), ("variant_ms", ctypes.c_double * 2)]
+                ("wave_variant", ctypes.c_int), ("variant_ms", ctypes.c_double * 2),
+                ("launches", ctypes.c_longlong)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -306,6 +306,7 @@ extern "C" fbim_status fbim_get_info(fbim_handle h, fbim_info* info) {
     info->wave_variant = f32 ? h->e32.wave_variant : h->e64.wave_variant;
     info->variant_ms[0] = f32 ? h->e32.variant_ms[0] : h->e64.variant_ms[0];
     info->variant_ms[1] = f32 ? h->e32.variant_ms[1] : h->e64.variant_ms[1];
+    info->launches = h->launches;
     return FBIM_OK;
 }
 

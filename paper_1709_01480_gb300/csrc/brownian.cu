@@ -100,6 +100,7 @@ fbim_status block_apply(fbim_handle_s* h, const T* Bref, const double* in, doubl
         return FBIM_ERR_CUDA;
     }
     k_rot_out<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, h->n_p, h->rot, g, out);
+    h->launches += 2;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;
 }
@@ -258,6 +259,7 @@ fbim_status brownian_slip(fbim_handle_s* h, unsigned long long seed, unsigned lo
         k_philox_normals<<<(unsigned)((n / 2 + 256) / 256), 256, 0, h->stream>>>((size_t)n, seed, 0u,
                                                                                 (unsigned)counter, Wn);
         FBIM_CUDA_TRY(h, cudaGetLastError());
+        h->launches += 1;
         W_r = Wn;
     }
     int it = 0;
@@ -272,6 +274,7 @@ fbim_status brownian_slip(fbim_handle_s* h, unsigned long long seed, unsigned lo
     }
     const double sc = std::sqrt(2.0 * kT / dt);
     k_combine<<<(n + 255) / 256, 256, 0, h->stream>>>(n, sc, near, sc, far, slip);
+    h->launches += 1;
     FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     if (lanczos_iters) *lanczos_iters = it;
     return FBIM_OK;

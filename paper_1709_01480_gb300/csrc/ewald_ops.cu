@@ -307,6 +307,7 @@ static fbim_status build_pairs(fbim_handle_s* h) {
     k_pair_fill<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, (T)(h->xi * h->xi), pref,
                                                            cheb<T>(h), h->perm, h->cell, h->cell_start,
                                                            (const T2*)e.off, e.slice_start, (PairEntry<T>*)e.pairs);
+    h->launches += 3;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     e.n_padded = (long long)total * 32;
     e.pairs_ready = true;
@@ -321,6 +322,7 @@ fbim_status refresh_offsets(fbim_handle_s* h) {
     k_offsets<T><<<(h->N + tb - 1) / tb, tb, 0, h->stream>>>(h->N, h->perm, h->tperm, h->x, h->cell, h->gbase,
                                                              h->n_box, h->r_c, h->h, (T2*)e.off, e.tbase,
                                                              (T2*)e.tfrac);
+    h->launches += 1;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return build_pairs<T>(h);
 }
@@ -464,6 +466,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
                                                          h->tslot, (const T2*)e.v_s, (const T2*)e.v_t, h->Q,
                                                          h->band_dev, (const double2*)mu, (double2*)v);
     h->mark(FBIM_ST_FINISH);
+    h->launches += 2 + (wave ? 3 : 0) + (real ? 1 : 0);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     h->collect();
     return FBIM_OK;
@@ -562,6 +565,7 @@ fbim_status apply_noise(fbim_handle_s* h, const double* Z, unsigned long long se
     k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, 0, 1, h->slot, h->tslot,
                                                          (const T2*)e.v_s, (const T2*)e.v_t, h->Q, h->band_dev,
                                                          (const double2*)out, (double2*)out);
+    h->launches += 3;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;
 }

@@ -144,6 +144,8 @@ struct fbim_handle_s {
     void mark_begin();             // record the opening event of a timed operator call
     void collect();                // synchronise and accumulate the recorded intervals
 
+    long long launches = 0;      // kernels this library has launched on the handle (counted at launch sites)
+
     int n_cell() const { return n_box * n_box; }
     void fail(const std::string& m) { err = m; }
 };

@@ -147,6 +147,7 @@ fbim_status build_geometry(fbim_handle_s* h) {
     k_scatter_slots<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->tile_tmp, h->tile_start, h->tile_fill, h->tperm,
                                                              h->tslot);
     k_rot<<<(h->n_b + tb - 1) / tb, tb, 0, h->stream>>>(h->n_b, h->Q, h->rot);
+    h->launches += 8;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     if (h->e64.ready) FBIM_TRY(refresh_offsets<double>(h));
     if (h->e32.ready) FBIM_TRY(refresh_offsets<float>(h));

@@ -88,6 +88,7 @@ fbim_status rfd_step(fbim_handle_s* h, const double* F, double dt, double kT, do
         if (s3 != FBIM_OK && s3 != FBIM_ERR_NOT_CONVERGED) return s3;
         // (3) update and leave the handle at the new configuration
         k_rfd_update<<<(n3 + tb - 1) / tb, tb, 0, h->stream>>>(n3, Q, dt, U, dt * kT / delta, Up, Um);
+        h->launches += (W_t ? 0 : 1) + 3;
         FBIM_CUDA_TRY(h, cudaGetLastError());
         FBIM_TRY(update_positions(h, Q));
         if (s1 != FBIM_OK || s2 != FBIM_OK || s3 != FBIM_OK) return FBIM_ERR_NOT_CONVERGED;
