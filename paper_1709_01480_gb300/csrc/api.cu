@@ -214,7 +214,7 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         FBIM_CUDA_TRY(h, cudaMalloc(&h->Q, 3 * n_b * sizeof(double)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->x, 2 * N * sizeof(double)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->cell, N * sizeof(int)));
-        FBIM_CUDA_TRY(h, cudaMalloc(&h->cell_start, (nc + 1) * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->cell_start, fbim::scan_storage((int)nc) * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->cell_fill, nc * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->perm, N * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->slot, N * sizeof(int)));
@@ -222,7 +222,7 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         FBIM_CUDA_TRY(h, cudaMalloc(&h->band_dev, bandv.size() * sizeof(double)));
         const size_t ntl = (size_t)h->n_tile * h->n_tile;
         FBIM_CUDA_TRY(h, cudaMalloc(&h->gbase, N * sizeof(int2)));
-        FBIM_CUDA_TRY(h, cudaMalloc(&h->tile_start, (ntl + 1) * sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&h->tile_start, fbim::scan_storage((int)ntl) * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->tile_fill, ntl * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->tperm, N * sizeof(int)));
         FBIM_CUDA_TRY(h, cudaMalloc(&h->tslot, N * sizeof(int)));

@@ -183,7 +183,7 @@ fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_it
     const T* Gd = std::is_same<T, float>::value ? (const T*)S->Gd32 : (const T*)S->Gd64;
     cublasHandle_t B = S->blas;
     double wn = 0;
-    FBIM_CUBLAS_TRY2(h, cublasDnrm2(B, n, W, 1, &wn));
+    FBIM_CUBLAS_TRY2(h, fbim_norm2(B, n, W, &wn));
     iters = 0;
     if (wn == 0) {
         FBIM_CUDA_TRY(h, cudaMemsetAsync(y, 0, sizeof(double) * n, h->stream));
@@ -214,7 +214,7 @@ fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_it
         FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->lh, sizeof(double) * 2 * (max_iter + 1),
                                          cudaMemcpyDeviceToHost, h->stream));
         double bn = 0;
-        FBIM_CUBLAS_TRY2(h, cublasDnrm2(B, n, tmp, 1, &bn));
+        FBIM_CUBLAS_TRY2(h, fbim_norm2(B, n, tmp, &bn));
         FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         alpha.push_back(hc[k] + hc[(max_iter + 1) + k]);
         beta.push_back(bn);

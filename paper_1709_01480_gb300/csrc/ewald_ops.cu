@@ -100,42 +100,21 @@ __global__ void __launch_bounds__(128) k_pair_count(int N, int n_box, T r_c, T r
     row_count[t] = n;
 }
 
-// slice_start[s] = sum over earlier slices of the longest row in the slice (one block)
-__global__ void k_slice_scan(int n_slice, int N, const int* __restrict__ row_count, int* __restrict__ slice_start) {
-    __shared__ int part[1024];
-    int tid = threadIdx.x;
-    int per = (n_slice + blockDim.x - 1) / blockDim.x;
-    int lo = min(n_slice, tid * per), hi = min(n_slice, lo + per);
-    auto len = [&](int sl) {
-        int mx = 0;
-        for (int l = 0; l < 32; ++l) {
-            int t = sl * 32 + l;
-            if (t < N) mx = max(mx, row_count[t]);
-        }
-        return mx;
-    };
-    int s = 0;
-    for (int i = lo; i < hi; ++i) s += len(i);
-    part[tid] = s;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        int v = tid >= o ? part[tid - o] : 0;
-        __syncthreads();
-        part[tid] += v;
-        __syncthreads();
-    }
-    int run = tid > 0 ? part[tid - 1] : 0;
-    for (int i = lo; i < hi; ++i) {
-        slice_start[i] = run;
-        run += len(i);
-    }
-    if (tid == blockDim.x - 1) slice_start[n_slice] = part[tid];
+// slice_len[s] = longest row of the 32 targets in slice s (one warp per slice).
+__global__ void k_slice_len(int n_slice, int N, const int* __restrict__ row_count, int* __restrict__ slice_len) {
+    const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (sl >= n_slice) return;
+    const int t = sl * 32 + lane;
+    int v = t < N ? row_count[t] : 0;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) slice_len[sl] = v;
 }
 
+// Pass 2 of the list build: write each pair's separation (rx, ry in the xx, xy
+// slots) and source; padding entries get a zero separation and the target itself.
 template <typename T>
-__global__ void __launch_bounds__(128) k_pair_fill(int N, int n_box, T r_c, T rc2, T xi2, T pref, ChebE1<T> ce,
-                                                  const int* __restrict__ perm, const int* __restrict__ cell,
-                                                  const int* __restrict__ start,
+__global__ void __launch_bounds__(128) k_pair_fill(int N, int n_box, T r_c, T rc2, const int* __restrict__ perm,
+                                                  const int* __restrict__ cell, const int* __restrict__ start,
                                                   const typename V2<T>::type* __restrict__ off,
                                                   const int* __restrict__ slice_start,
                                                   PairEntry<T>* __restrict__ pairs) {
@@ -147,13 +126,10 @@ __global__ void __launch_bounds__(128) k_pair_fill(int N, int n_box, T r_c, T rc
     int k = 0;
     for_each_pair<T>(t, n_box, r_c, rc2, perm, cell, start, off, [&](int s, T rx, T ry, T r2) {
         if (r2 == T(0)) return;
-        T z = xi2 * r2;
-        T a = kernel_a<T>(ce, z);
-        T b = dev_div(dev_exp(-z), r2);
         PairEntry<T> e;
-        e.xx = pref * (a + b * rx * rx);
-        e.xy = pref * (b * rx * ry);
-        e.yy = pref * (a + b * ry * ry);
+        e.xx = rx;
+        e.xy = ry;
+        e.yy = T(0);
         e.src = s;
         row[(size_t)k * 32] = e;
         ++k;
@@ -164,6 +140,27 @@ __global__ void __launch_bounds__(128) k_pair_fill(int N, int n_box, T r_c, T rc
         e.src = t;
         row[(size_t)k * 32] = e;
     }
+}
+
+// Pass 3: turn every stored separation into the kernel G^(r)(r) / (4 pi eta) in
+// place.  One thread per entry, so the transcendental work runs without the
+// divergence of the neighbour search (which matters most for FP64).
+template <typename T>
+__global__ void __launch_bounds__(256) k_pair_eval(size_t n_entries, T xi2, T pref, ChebE1<T> ce,
+                                                  PairEntry<T>* __restrict__ pairs) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_entries) return;
+    PairEntry<T> e = pairs[i];
+    const T rx = e.xx, ry = e.xy;
+    const T r2 = rx * rx + ry * ry;
+    if (r2 == T(0)) return;  // padding
+    const T z = xi2 * r2;
+    const T a = kernel_a<T>(ce, z);
+    const T b = dev_div(dev_exp(-z), r2);
+    e.xx = pref * (a + b * rx * rx);
+    e.xy = pref * (b * rx * ry);
+    e.yy = pref * (a + b * ry * ry);
+    pairs[i] = e;
 }
 
 template <typename T>
@@ -292,7 +289,10 @@ static fbim_status build_pairs(fbim_handle_s* h) {
     const T rc = (T)h->r_c, rc2 = (T)(h->r_c * h->r_c);
     k_pair_count<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, h->perm, h->cell, h->cell_start,
                                                             (const T2*)e.off, e.row_count, h->flags);
-    k_slice_scan<<<1, 1024, 0, h->stream>>>(n_slice, N, e.row_count, e.slice_start);
+    // slice lengths (one warp per slice) into slice_start, then an exclusive scan in place
+    k_slice_len<<<(unsigned)(((size_t)n_slice * 32 + 255) / 256), 256, 0, h->stream>>>(n_slice, N, e.row_count,
+                                                                                        e.row_count + N);
+    scan_exclusive(h->stream, e.row_count + N, n_slice, e.slice_start);
     int total = 0;
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(&total, e.slice_start + n_slice, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -304,10 +304,12 @@ static fbim_status build_pairs(fbim_handle_s* h) {
         e.pair_cap = cap;
     }
     const T pref = (T)(1.0 / (4.0 * M_PI * h->eta));
-    k_pair_fill<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, (T)(h->xi * h->xi), pref,
-                                                           cheb<T>(h), h->perm, h->cell, h->cell_start,
+    k_pair_fill<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, h->perm, h->cell, h->cell_start,
                                                            (const T2*)e.off, e.slice_start, (PairEntry<T>*)e.pairs);
-    h->launches += 3;
+    const size_t n_entries = (size_t)total * 32;
+    k_pair_eval<T><<<(unsigned)((n_entries + 255) / 256), 256, 0, h->stream>>>(
+        n_entries, (T)(h->xi * h->xi), pref, cheb<T>(h), (PairEntry<T>*)e.pairs);
+    h->launches += 4;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     e.n_padded = (long long)total * 32;
     e.pairs_ready = true;
@@ -392,8 +394,8 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&e.v_t, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.grid, 2 * M * M * sizeof(T)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.spec, 2 * M * Mh * sizeof(C)));
-    FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, (n_slice + 1) * sizeof(int)));
-    FBIM_CUDA_TRY(h, cudaMalloc(&e.row_count, n_slice * 32 * sizeof(int)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, scan_storage((int)n_slice) * sizeof(int)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.row_count, (n_slice * 33 + 1) * sizeof(int)));
     int n[2] = {(int)M, (int)M};
     int inembed[2] = {(int)M, (int)M};
     int onembed[2] = {(int)M, (int)Mh};

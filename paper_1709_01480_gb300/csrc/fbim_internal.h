@@ -165,6 +165,9 @@ fbim_status choose_ewald(double L, double r_c, double tol, double xi_in, int& n_
 
 // geometry (geometry.cu)
 fbim_status build_geometry(fbim_handle_s* h);
+// exclusive scan of n ints into out[0..n] (out[n] = total); out needs scan_storage(n) ints
+void scan_exclusive(cudaStream_t st, const int* in, int n, int* out);
+size_t scan_storage(int n);
 // copy body coordinates Q_dev (device, [n_b][3]) into the handle and rebuild the geometry
 fbim_status update_positions(fbim_handle_s* h, const double* Q_dev);
 

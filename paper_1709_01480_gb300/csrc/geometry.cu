@@ -123,7 +123,60 @@ __global__ void k_rot(int n_b, const double* __restrict__ Q, double* __restrict_
     rot[2 * b + 1] = s;
 }
 
+// Block-local exclusive scan of 1024 elements per block (256 threads x 4); the
+// block total goes to totals[block].
+__global__ void k_scan_local(int n, const int* __restrict__ in, int* __restrict__ out, int* __restrict__ totals) {
+    __shared__ int warp_sum[8];
+    const int base = blockIdx.x * 1024 + threadIdx.x * 4;
+    int v[4], s = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        s += v[i];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < 8; ++w) {
+        before += (w < warp) ? warp_sum[w] : 0;
+        tot += warp_sum[w];
+    }
+    int run = before + incl - s;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += v[i];
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(int n, int* __restrict__ out, const int* __restrict__ offs) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += offs[i / 1024];
+}
+
 }  // namespace
+
+// out[0..n] = exclusive prefix sums of in[0..n) with out[n] the total.  Uses
+// out[n + 1 ..] as scratch: out must hold n + 2 + 2 ceil(n / 1024) ints.
+void scan_exclusive(cudaStream_t st, const int* in, int n, int* out) {
+    const int nb = (n + 1023) / 1024;
+    int* totals = out + n + 1;
+    int* offs = totals + nb;
+    k_scan_local<<<nb, 256, 0, st>>>(n, in, out, totals);
+    k_scan<<<1, 1024, 0, st>>>(nb, totals, offs);  // offs[0..nb], offs[nb] = grand total
+    k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(n, out, offs);
+    // out[n] = grand total
+    cudaMemcpyAsync(out + n, offs + nb, sizeof(int), cudaMemcpyDeviceToDevice, st);
+}
+
+size_t scan_storage(int n) { return (size_t)n + 2 + 2 * (size_t)((n + 1023) / 1024); }
 
 fbim_status build_geometry(fbim_handle_s* h) {
     const int N = h->N, nc = h->n_cell(), nt = h->n_tile * h->n_tile;
@@ -134,12 +187,12 @@ fbim_status build_geometry(fbim_handle_s* h) {
                                                      h->TS, h->n_tile, h->x, h->cell, h->cell_fill, h->gbase,
                                                      h->tile_fill, h->flags);
     // cell list (real space)
-    k_scan<<<1, 1024, 0, h->stream>>>(nc, h->cell_fill, h->cell_start);
+    scan_exclusive(h->stream, h->cell_fill, nc, h->cell_start);
     FBIM_CUDA_TRY(h, cudaMemsetAsync(h->cell_fill, 0, sizeof(int) * nc, h->stream));
     k_scatter<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->cell, h->cell_start, h->cell_fill, h->perm);
     k_sort_cells<<<(nc + tb - 1) / tb, tb, 0, h->stream>>>(nc, h->cell_start, h->perm, h->slot);
     // grid tiles (wave space): nodes sorted by the TS x TS tile holding their nearest grid point
-    k_scan<<<1, 1024, 0, h->stream>>>(nt, h->tile_fill, h->tile_start);
+    scan_exclusive(h->stream, h->tile_fill, nt, h->tile_start);
     FBIM_CUDA_TRY(h, cudaMemsetAsync(h->tile_fill, 0, sizeof(int) * nt, h->stream));
     k_tile_of<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->gbase, h->TS, h->n_tile, h->tile_tmp);
     // (order inside a tile is left as scattered: wave-space sums do not depend on it

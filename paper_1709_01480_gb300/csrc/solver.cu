@@ -434,7 +434,7 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
     const int n = S->n, m = S->restart, ld = S->ld;
     cublasHandle_t B = S->blas;
     double bnorm = 0;
-    FBIM_CUBLAS_TRY(h, cublasDnrm2(B, n, b, 1, &bnorm));
+    FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, b, &bnorm));
     iters = 0;
     rel_est = 0;
     if (bnorm == 0) {
@@ -456,7 +456,7 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
         }
         first = false;
         double beta = 0;
-        FBIM_CUBLAS_TRY(h, cublasDnrm2(B, n, S->w, 1, &beta));
+        FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, S->w, &beta));
         rel_est = beta / bnorm;
         if (!std::isfinite(beta)) {
             h->fail("GMRES residual is not finite");
@@ -482,7 +482,7 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
             FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol + (m + 1), 1, &one,
                                            S->w, 1));
             double hn = 0;
-            FBIM_CUBLAS_TRY(h, cublasDnrm2(B, n, S->w, 1, &hn));
+            FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, S->w, &hn));
             FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->hcol, sizeof(double) * 2 * (m + 1), cudaMemcpyDeviceToHost,
                                              h->stream));
             FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -536,8 +536,8 @@ static fbim_status true_residual(fbim_handle_s* h, const double* b, const double
     k_axpby<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0, b, -1.0, r);
     h->launches += 1;
     double rn = 0, bn = 0;
-    FBIM_CUBLAS_TRY(h, cublasDnrm2(S->blas, n, r, 1, &rn));
-    FBIM_CUBLAS_TRY(h, cublasDnrm2(S->blas, n, b, 1, &bn));
+    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, r, &rn));
+    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, b, &bn));
     rel = bn > 0 ? rn / bn : 0.0;
     return FBIM_OK;
 }

@@ -2,6 +2,17 @@
 #pragma once
 #include <cublas_v2.h>
 
+#include <cmath>
+
+// Euclidean norm through a dot product (one reduction kernel; the library's nrm2
+// routine uses a slower overflow-safe scaling that these vectors do not need).
+inline cublasStatus_t fbim_norm2(cublasHandle_t b, int n, const double* x, double* out) {
+    double d = 0.0;
+    cublasStatus_t st = cublasDdot(b, n, x, 1, x, 1, &d);
+    *out = std::sqrt(d);
+    return st;
+}
+
 struct Solver {
     int n2 = 0;                 // 2 n_p
     int n = 0;                  // 2N + 3 n_b
