@@ -23,6 +23,7 @@ import numpy as np
 __all__ = [
     "starfish_ref_nodes", "starfish_area", "disk_ref_nodes", "place_bodies",
     "random_forces", "Workload", "WORKLOADS", "make_workload", "box_for_fraction",
+    "BATCHES", "suspension_batch", "batch",
 ]
 
 
@@ -77,6 +78,16 @@ def place_bodies(n_b: int, L: float, ref_nodes: np.ndarray, min_gap: float, seed
     rng = np.random.default_rng(seed)
     outline = _dense_outline(ref_nodes)
     r_env = float(np.max(np.linalg.norm(outline, axis=1)))
+    # Outline subsets (every 8th, 4th, 2nd point) decide most pairs exactly before
+    # the full test.  With delta_s the largest distance from an outline point to the
+    # nearest point of subset s, the full minimum distance D and the subset one D_s
+    # obey D <= D_s <= D + 2 delta_s: D_s < gap rejects, D_s >= gap + 2 delta_s accepts.
+    gap2 = min_gap * min_gap
+    levels = []
+    for stride in (8, 4, 2):
+        sub = outline[::stride]
+        delta = float(np.max(np.min(np.linalg.norm(outline[:, None, :] - sub[None, :, :], axis=2), axis=1)))
+        levels.append((stride, (min_gap + 2.0 * delta) ** 2))
     reach = 2.0 * r_env + min_gap
     n_cell = max(1, int(L // reach))
     cell = L / n_cell
@@ -101,8 +112,24 @@ def place_bodies(n_b: int, L: float, ref_nodes: np.ndarray, min_gap: float, seed
                     d -= L * np.round(d / L)
                     if np.hypot(*d) >= reach:
                         continue
-                    diff = (placed_outlines[other] + d)[:, None, :] - cand[None, :, :]
-                    if np.min(np.einsum("ijk,ijk->ij", diff, diff)) < min_gap * min_gap:
+                    other_outline = placed_outlines[other] + d
+                    decided = False
+                    for stride, sure2 in levels:
+                        dc = other_outline[::stride, None, :] - cand[None, ::stride, :]
+                        dc2 = np.min(np.einsum("ijk,ijk->ij", dc, dc))
+                        if dc2 < gap2:
+                            ok = False
+                            decided = True
+                            break
+                        if dc2 >= sure2:
+                            decided = True
+                            break
+                    if not ok:
+                        break
+                    if decided:
+                        continue
+                    diff = other_outline[:, None, :] - cand[None, :, :]
+                    if np.min(np.einsum("ijk,ijk->ij", diff, diff)) < gap2:
                         ok = False
                         break
                 if not ok:
@@ -176,3 +203,34 @@ WORKLOADS = {
 def workload(name: str) -> Workload:
     kw = dict(WORKLOADS[name])
     return make_workload(name, **kw)
+
+
+def suspension_batch(name: str, n_sys: int, n_min: int, n_max: int, n_p: int, phi_lo: float, phi_hi: float,
+                     tol: float = 1e-8, min_gap: float = 0.1, seed: int = 0) -> list:
+    """Independent starfish suspensions of uneven size.
+
+    Body counts are log-uniform on [n_min, n_max] (rounded down), area
+    fractions uniform on [phi_lo, phi_hi]; suspension i is placed with seed
+    1000 seed + i + 1.  Returns a list of Workload.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_sys):
+        n_b = int(np.floor(np.exp(rng.uniform(np.log(n_min), np.log(n_max + 1)))))
+        n_b = min(max(n_b, n_min), n_max)
+        phi = float(rng.uniform(phi_lo, phi_hi))
+        out.append(make_workload(f"{name}[{i}]", n_b, n_p, phi=phi, tol=tol, min_gap=min_gap,
+                                 seed=1000 * seed + i + 1))
+    return out
+
+
+# Named batches of independent suspensions: 64 starfish suspensions with
+# 16..512 bodies (log-uniform), 96 nodes per body and area fractions 0.1..0.35.
+BATCHES = {
+    "batch64_starfish_np96": dict(n_sys=64, n_min=16, n_max=512, n_p=96, phi_lo=0.1, phi_hi=0.35, tol=1e-8,
+                                  min_gap=0.1, seed=2),
+}
+
+
+def batch(name: str) -> list:
+    return suspension_batch(name, **BATCHES[name])

@@ -180,6 +180,59 @@ fbim_status fbim_rfd_step(fbim_handle h, const double* F_dev, double dt, double 
 fbim_status fbim_philox_normals(fbim_handle h, uint64_t seed, uint32_t stream, uint32_t counter, size_t n,
                                 double* out_dev);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves: many independent suspensions (handles), each with one or more
+ * right-hand sides, through one captured CUDA graph per operator application.
+ * The batched form of fbim_mobility_solve (Sec. 3.1, Eq. discreteSaddlePoint with
+ * the Sec. 3.4 block-diagonal preconditioner): every system (handle k, right-hand
+ * side r) is solved to the same relative residual as a single solve would be.
+ * ------------------------------------------------------------------------- */
+typedef struct fbim_batch_s* fbim_batch;
+
+typedef struct {
+    int       n_handles, n_systems;  /* suspensions, systems (handle, right-hand side)          */
+    long long n_unknowns;            /* length of the stacked Krylov vectors                    */
+    int       restart;               /* GMRES restart of the batch (smallest of the handles')   */
+    int       branches;              /* concurrent branches of the captured graphs              */
+    long long graph_kernels[4];      /* this library's kernels in each graph: precondition +
+                                        saddle FP32, the same FP64, saddle FP32, saddle FP64
+                                        (0 until the graph is first captured)                   */
+    long long launches;              /* this library's kernels run by the batch so far,
+                                        graph nodes included (cuFFT, cuBLAS not counted)        */
+    long long graph_launches;        /* graph replays so far                                    */
+} fbim_batch_info;
+
+/* Group n_handles distinct handles into a batch; handle k gets n_rhs[k] >= 1
+ * right-hand sides (n_rhs NULL: one each).  All handles must share device, stream
+ * and precision.  Systems are ordered handle-major: system i = (k, r) for k in
+ * order and r < n_rhs[k].  The handles stay owned by the caller and must outlive
+ * the batch; they may be moved (fbim_update_config, fbim_rfd_step) between batched
+ * solves, and the batch recaptures its graphs when a move reallocated a buffer.
+ * Allocates the stacked Krylov workspace ((2 restart + 9) doubles per unknown). */
+fbim_status fbim_batch_create(fbim_batch* out, int n_handles, const fbim_handle* handles, const int* n_rhs);
+
+/* Solve every system of the batch.
+ *   F_dev:    double, the systems' [n_b][3] force blocks stacked in system order (device).
+ *   slip_dev: NULL or double, the systems' [N][2] slip blocks stacked the same way.
+ *   tol:      relative residual each system must reach, measured with its FP64 operator
+ *             (FP32 handles refine: FP64 residuals, FP32-operator corrections).
+ *   max_iter: cap on each system's GMRES iterations (all refinement steps together).
+ *   U_dev:    double output, the systems' [n_b][3] velocity blocks stacked like F_dev.
+ *   iters, rel_residual: NULL or host arrays [n_systems] (iterations and the final FP64
+ *             relative residual of every system).
+ * Synchronises the stream.  FBIM_ERR_NOT_CONVERGED (results written) when a system
+ * misses tol within max_iter. */
+fbim_status fbim_batch_solve(fbim_batch b, const double* F_dev, const double* slip_dev, double tol, int max_iter,
+                             double* U_dev, int* iters, double* rel_residual);
+
+fbim_status fbim_batch_get_info(fbim_batch b, fbim_batch_info* info);
+
+/* Release the batch's workspace and graphs (not the handles).  NULL is accepted. */
+void fbim_batch_destroy(fbim_batch b);
+
+/* Text of the last error of the batch (of the last failed fbim_batch_create when NULL). */
+const char* fbim_batch_last_error(fbim_batch b);
+
 /* v = (M(t) + M(a)_sym) mu, the same operator as fbim_apply_real, computed without
  * allocating any device memory (the paper has no counterpart: this is a library
  * service).  It is for callers that must not allocate once running, such as a host

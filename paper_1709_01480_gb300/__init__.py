@@ -36,6 +36,8 @@ EXPORTS = [
     "fbim_destroy", "fbim_last_error", "fbim_host_expint_e1", "fbim_host_alpert_rule",
     "fbim_set_timing", "fbim_stage_times", "fbim_mobility_solve", "fbim_brownian_slip",
     "fbim_philox_normals", "fbim_apply_real_noalloc", "fbim_rfd_step",
+    "fbim_batch_create", "fbim_batch_solve", "fbim_batch_get_info", "fbim_batch_destroy",
+    "fbim_batch_last_error",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -69,6 +71,17 @@ class Info(ctypes.Structure):
         return d
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_handles", ctypes.c_int), ("n_systems", ctypes.c_int), ("n_unknowns", ctypes.c_longlong),
+                ("restart", ctypes.c_int), ("branches", ctypes.c_int), ("graph_kernels", ctypes.c_longlong * 4),
+                ("launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["graph_kernels"] = list(self.graph_kernels)
+        return d
+
+
 
 
 _P = ctypes.c_void_p
@@ -99,6 +112,13 @@ _lib.fbim_mobility_solve.argtypes = [_P, _P, _P, _D, _I, _P, _P, _IP, _DP]
 _lib.fbim_brownian_slip.argtypes = [_P, ctypes.c_uint64, ctypes.c_uint64, _D, _D, _P, _P, _D, _I, _P, _IP]
 _lib.fbim_philox_normals.argtypes = [_P, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_size_t, _P]
 _lib.fbim_stage_times.argtypes = [_P, _DP, ctypes.POINTER(ctypes.c_longlong), _I]
+_lib.fbim_batch_create.argtypes = [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _IP]
+_lib.fbim_batch_solve.argtypes = [_P, _P, _P, _D, _I, _P, _IP, _DP]
+_lib.fbim_batch_get_info.argtypes = [_P, ctypes.POINTER(BatchInfo)]
+_lib.fbim_batch_destroy.argtypes = [_P]
+_lib.fbim_batch_destroy.restype = None
+_lib.fbim_batch_last_error.argtypes = [_P]
+_lib.fbim_batch_last_error.restype = ctypes.c_char_p
 
 
 def lib():
@@ -266,6 +286,69 @@ class FBIM:
         if getattr(self, "_h", None):
             _lib.fbim_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Batched mobility solves over several handles (``FBIM`` objects).
+
+    ``n_rhs[k]`` right-hand sides go with handle k; systems are ordered
+    handle-major.  ``solve`` takes the systems' forces (and slips) as lists of
+    tensors, or as stacked flat tensors, and returns the velocities as a list of
+    [n_b, 3] tensors with the per-system iterations and FP64 relative residuals.
+    """
+
+    def __init__(self, ops, n_rhs=None):
+        self.ops = list(ops)  # keeps the handles alive
+        n = len(self.ops)
+        self.n_rhs = [1] * n if n_rhs is None else [int(r) for r in n_rhs]
+        hs = (_P * n)(*[o.handle.value if isinstance(o.handle, _P) else o.handle for o in self.ops])
+        rr = (ctypes.c_int * n)(*self.n_rhs)
+        b = _P()
+        st = _lib.fbim_batch_create(ctypes.byref(b), n, hs, rr)
+        if st != 0:
+            msg = _lib.fbim_batch_last_error(None)
+            raise FbimError(st, msg.decode() if msg else "")
+        self._b = b
+        self.systems = [(k, r) for k in range(n) for r in range(self.n_rhs[k])]
+
+    def _check(self, st):
+        if st != 0:
+            msg = _lib.fbim_batch_last_error(self._b)
+            raise FbimError(st, msg.decode() if msg else "")
+
+    def info(self):
+        i = BatchInfo()
+        self._check(_lib.fbim_batch_get_info(self._b, ctypes.byref(i)))
+        return i.as_dict()
+
+    def solve(self, F, slip=None, tol=1e-6, max_iter=500, check=True):
+        import torch
+        Fs = torch.cat([f.reshape(-1) for f in F]) if isinstance(F, (list, tuple)) else F
+        Ss = None
+        if slip is not None:
+            Ss = torch.cat([s.reshape(-1) for s in slip]) if isinstance(slip, (list, tuple)) else slip
+        n_sys = len(self.systems)
+        sizes = [3 * self.ops[k].n_b for k, _ in self.systems]
+        U = torch.empty(sum(sizes), dtype=torch.float64, device=Fs.device)
+        it = (ctypes.c_int * n_sys)()
+        res = (ctypes.c_double * n_sys)()
+        st = _lib.fbim_batch_solve(self._b, _ptr(Fs), None if Ss is None else _ptr(Ss), float(tol), int(max_iter),
+                                   _ptr(U), it, res)
+        if check or st not in (0, 6):
+            self._check(st)
+        Us = list(torch.split(U, sizes))
+        return [u.view(-1, 3) for u in Us], list(it), list(res)
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _lib.fbim_batch_destroy(self._b)
+            self._b = None
 
     def __del__(self):
         try:

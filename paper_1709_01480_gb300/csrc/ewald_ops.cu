@@ -302,6 +302,7 @@ static fbim_status build_pairs(fbim_handle_s* h) {
         size_t cap = (size_t)total + total / 4 + 32;
         FBIM_CUDA_TRY(h, cudaMalloc(&e.pairs, cap * 32 * sizeof(PairEntry<T>)));
         e.pair_cap = cap;
+        ++h->layout_version;
     }
     const T pref = (T)(1.0 / (4.0 * M_PI * h->eta));
     k_pair_fill<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, h->perm, h->cell, h->cell_start,

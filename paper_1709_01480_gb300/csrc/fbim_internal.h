@@ -145,6 +145,7 @@ struct fbim_handle_s {
     void collect();                // synchronise and accumulate the recorded intervals
 
     long long launches = 0;      // kernels this library has launched on the handle (counted at launch sites)
+    unsigned long long layout_version = 0;  // bumped when a buffer that launches take by pointer is reallocated
 
     int n_cell() const { return n_box * n_box; }
     void fail(const std::string& m) { err = m; }
@@ -173,6 +174,12 @@ fbim_status update_positions(fbim_handle_s* h, const double* Q_dev);
 
 // solvers (solver.cu)
 void free_solver(fbim_handle_s* h);
+fbim_status ensure_solver(fbim_handle_s* h);
+// block preconditioner and saddle operator on x = [mu; U] (stream-ordered, no host sync)
+fbim_status solver_precondition(fbim_handle_s* h, const double* in, double* out, bool fp32);
+fbim_status solver_saddle(fbim_handle_s* h, const double* x, double* y, bool fp32);
+// point every launch of the handle (kernels, cuFFT plans, cuBLAS) at stream s
+void bind_stream(fbim_handle_s* h, cudaStream_t s);
 
 // operators (ewald_ops.cu)
 template <typename T> fbim_status ensure_ewald(fbim_handle_s* h);

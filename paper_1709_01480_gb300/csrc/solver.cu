@@ -359,6 +359,12 @@ fbim_status setup_solver(fbim_handle_s* h) {
         return FBIM_ERR_CUDA;
     }
     cublasSetStream(S->blas, h->stream);
+    const size_t ws = 4u << 20;
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->blas_ws, ws));
+    if (cublasSetWorkspace(S->blas, S->blas_ws, ws) != CUBLAS_STATUS_SUCCESS) {
+        h->fail("cublasSetWorkspace failed");
+        return FBIM_ERR_CUDA;
+    }
     return FBIM_OK;
 }
 
@@ -370,7 +376,7 @@ void free_solver(fbim_handle_s* h) {
     for (void* p : {(void*)S->Mpinv64, (void*)S->Mpinv32, (void*)S->H64, (void*)S->H32, (void*)S->G64,
                     (void*)S->Gd64, (void*)S->G32, (void*)S->Gd32, (void*)S->V, (void*)S->Z, (void*)S->w,
                     (void*)S->r, (void*)S->d, (void*)S->t, (void*)S->hcol, S->zbuf, S->gbuf, (void*)S->lz,
-                    (void*)S->lh, (void*)S->rfd})
+                    (void*)S->lh, (void*)S->rfd, S->blas_ws})
         cudaFree(p);
     if (S->blas) cublasDestroy(S->blas);
     delete S;
@@ -607,9 +613,26 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
     return FBIM_OK;
 }
 
-// exposed for the Brownian slip
-fbim_status solver_precondition64(fbim_handle_s* h, const double* in, double* out) {
-    return precondition<double>(h, in, out);
+// exposed for the batched solver (batch.cu)
+fbim_status solver_precondition(fbim_handle_s* h, const double* in, double* out, bool fp32) {
+    return fp32 ? precondition<float>(h, in, out) : precondition<double>(h, in, out);
+}
+
+fbim_status solver_saddle(fbim_handle_s* h, const double* x, double* y, bool fp32) {
+    return fp32 ? saddle_apply<float>(h, x, y) : saddle_apply<double>(h, x, y);
+}
+
+void bind_stream(fbim_handle_s* h, cudaStream_t s) {
+    h->stream = s;
+    if (h->e64.ready) {
+        cufftSetStream(h->e64.plan_f, s);
+        cufftSetStream(h->e64.plan_i, s);
+    }
+    if (h->e32.ready) {
+        cufftSetStream(h->e32.plan_f, s);
+        cufftSetStream(h->e32.plan_i, s);
+    }
+    if (h->solver && h->solver->blas) cublasSetStream(h->solver->blas, s);
 }
 
 }  // namespace fbim

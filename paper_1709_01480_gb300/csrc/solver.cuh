@@ -40,5 +40,6 @@ struct Solver {
     int lanczos_max = 0;        // Lanczos workspace (brownian.cu)
     double* lz = nullptr;       // [lanczos_max][2N] Lanczos basis
     double* lh = nullptr;       // [2 lanczos_max] Lanczos dot products / coefficients
+    void* blas_ws = nullptr;    // fixed cuBLAS workspace (so captured graphs never allocate)
     double* rfd = nullptr;      // [2N + 6 * 3 n_b] workspace of the random-finite-difference step
 };
