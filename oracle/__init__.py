@@ -20,6 +20,9 @@ in float64, written so that each step can be checked against the paper by eye:
                   Eqs. sqrtM-split, sqrtMwave, preconditioned-real-part, Gprecond-precompute)
 * ``philox``      Philox4x32-10 counter-based generator (Salmon et al., SC'11)
 * ``rfd``         Euler-Maruyama step with random finite differences (Sec. 4.4, Eq. EM-RFD)
+* ``mlp``         pair-correction network, its loss gradient and Adam (learned coarse level)
+* ``coarse``      close body pairs, their features, two-body mobility corrections and the
+                  coarse-level body velocities (learned coarse level on top of Sec. 3.4)
 
 Parity status of each function is stated in its module header.  The wave
 space is evaluated as a direct non-uniform Fourier sum: no grid, no Gaussian
