@@ -233,6 +233,80 @@ void fbim_batch_destroy(fbim_batch b);
 /* Text of the last error of the batch (of the last failed fbim_batch_create when NULL). */
 const char* fbim_batch_last_error(fbim_batch b);
 
+/* ---------------------------------------------------------------------------
+ * Learned coarse level (an option on top of the Sec. 3.4 block-diagonal
+ * preconditioner; the paper has no network).  A multilayer perceptron
+ * 6 -> 128 -> 128 -> 128 -> 36 (tanh hidden layers, linear output) maps the
+ * geometry of a close body pair to a 6x6 pair-mobility correction C, which the
+ * preconditioner adds to the block-diagonal body mobilities.  Matrix products
+ * run on the tensor cores with bfloat16 operands and FP32 accumulation; the
+ * parameters, activations, gradients and Adam moments are FP32.
+ *
+ * Parameter vector (float, fbim_mlp_param_count() = 38564 entries): for layers
+ * l = 1..4, W_l [n_l][n_(l-1)] row-major then b_l [n_l], widths 6, 128, 128, 128, 36.
+ * Network inputs are normalised features x_n = (x - in_shift) / in_scale; outputs y
+ * are the normalised 6x6 correction, C = sym(reshape(y * out_scale, 6, 6)).
+ * ------------------------------------------------------------------------- */
+typedef struct fbim_mlp_s* fbim_mlp;
+
+int fbim_mlp_param_count(void);
+
+/* Create a network for batches of up to max_batch samples on `stream` (cudaStream_t,
+ * NULL = legacy default) of `device`.  Parameters start at zero. */
+fbim_status fbim_mlp_create(fbim_mlp* out, int max_batch, void* stream, int device);
+void fbim_mlp_destroy(fbim_mlp m);
+const char* fbim_mlp_last_error(fbim_mlp m);
+
+/* Copy the parameter vector from / to host memory (float [38564]).  Setting the
+ * parameters resets the Adam moments and step count.  Synchronises the stream. */
+fbim_status fbim_mlp_set_params(fbim_mlp m, const float* theta_host);
+fbim_status fbim_mlp_get_params(fbim_mlp m, float* theta_host);
+
+/* Feature normalisation used by the coarse level (host arrays float [6], [6], [36];
+ * in_scale > 0). */
+fbim_status fbim_mlp_set_normalization(fbim_mlp m, const float* in_shift, const float* in_scale,
+                                       const float* out_scale);
+
+/* Y [n][36] = network(X [n][6]) for n <= max_batch (device, float). */
+fbim_status fbim_mlp_forward(fbim_mlp m, int n, const float* X_dev, float* Y_dev);
+
+/* Loss (1 / (36 n)) sum (Y - T)^2 of the batch X [n][6], T [n][36] (device, float) and
+ * its gradient with respect to the parameter vector into grad_dev (float [38564],
+ * device; NULL to skip the copy).  *loss (host, NULL allowed).  Synchronises. */
+fbim_status fbim_mlp_gradient(fbim_mlp m, int n, const float* X_dev, const float* T_dev, float* grad_dev,
+                              double* loss);
+
+/* One Adam step (Kingma & Ba, Algorithm 1) on the batch's loss gradient: moments
+ * m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2, theta <- theta - lr m^ / (sqrt(v^) + eps)
+ * with m^ = m / (1 - b1^t), v^ = v / (1 - b2^t).  *loss: the loss before the step. */
+fbim_status fbim_mlp_adam_step(fbim_mlp m, int n, const float* X_dev, const float* T_dev, float lr, float beta1,
+                               float beta2, float eps, double* loss);
+
+/* Kernels the network has launched so far. */
+long long fbim_mlp_launches(fbim_mlp m);
+
+/* Close pairs of the handle's current configuration: pairs (a < b, alpha-major) whose
+ * smallest node-to-node distance (minimum image) is below g_c, and their features
+ * (dx, dy, |d|, cos phi, sin phi, gap): d = q_b - q_a (minimum image) rotated into
+ * body a's frame, phi = theta_b - theta_a.  pairs_dev int [max][2], feat_dev double
+ * [max][6] (device, either may be NULL); *n_pairs = the number found (all of them
+ * even when more than max_pairs; only the first max_pairs are written).  Synchronises. */
+fbim_status fbim_coarse_pairs(fbim_handle h, double g_c, int max_pairs, int* pairs_dev, double* feat_dev,
+                              int* n_pairs);
+
+/* Turn the learned coarse level on (model non-NULL) or off (NULL).  With it on, every
+ * preconditioner application replaces each body's velocity U_b = N~_b a_b by
+ * U_b = N~_b a_b + sum over close pairs (p, q) containing b of (C_pq [a_p; a_q])_b and
+ * recomputes the body's traction from that U (the body solve of Sec. 3.4 with the
+ * mobility N~ + sum C).  C comes from the network at every new configuration; a
+ * pair's correction is dropped when blockdiag(N~_p, N~_q) + C_pq is not positive
+ * definite or not finite.  The model must outlive its use by the handle and is
+ * evaluated on the handle's stream. */
+fbim_status fbim_coarse_enable(fbim_handle h, fbim_mlp model, double g_c);
+
+/* Pairs in use and pairs dropped at the last coarse-level setup (NULL allowed). */
+fbim_status fbim_coarse_stats(fbim_handle h, int* n_pairs, int* n_rejected);
+
 /* v = (M(t) + M(a)_sym) mu, the same operator as fbim_apply_real, computed without
  * allocating any device memory (the paper has no counterpart: this is a library
  * service).  It is for callers that must not allocate once running, such as a host

@@ -38,6 +38,10 @@ EXPORTS = [
     "fbim_philox_normals", "fbim_apply_real_noalloc", "fbim_rfd_step",
     "fbim_batch_create", "fbim_batch_solve", "fbim_batch_get_info", "fbim_batch_destroy",
     "fbim_batch_last_error",
+    "fbim_mlp_param_count", "fbim_mlp_create", "fbim_mlp_destroy", "fbim_mlp_last_error",
+    "fbim_mlp_set_params", "fbim_mlp_get_params", "fbim_mlp_set_normalization", "fbim_mlp_forward",
+    "fbim_mlp_gradient", "fbim_mlp_adam_step", "fbim_mlp_launches", "fbim_coarse_pairs",
+    "fbim_coarse_enable", "fbim_coarse_stats",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -119,6 +123,25 @@ _lib.fbim_batch_destroy.argtypes = [_P]
 _lib.fbim_batch_destroy.restype = None
 _lib.fbim_batch_last_error.argtypes = [_P]
 _lib.fbim_batch_last_error.restype = ctypes.c_char_p
+_FP = ctypes.POINTER(ctypes.c_float)
+_lib.fbim_mlp_param_count.restype = _I
+_lib.fbim_mlp_create.argtypes = [ctypes.POINTER(_P), _I, _P, _I]
+_lib.fbim_mlp_destroy.argtypes = [_P]
+_lib.fbim_mlp_destroy.restype = None
+_lib.fbim_mlp_last_error.argtypes = [_P]
+_lib.fbim_mlp_last_error.restype = ctypes.c_char_p
+_lib.fbim_mlp_set_params.argtypes = [_P, _FP]
+_lib.fbim_mlp_get_params.argtypes = [_P, _FP]
+_lib.fbim_mlp_set_normalization.argtypes = [_P, _FP, _FP, _FP]
+_lib.fbim_mlp_forward.argtypes = [_P, _I, _P, _P]
+_lib.fbim_mlp_gradient.argtypes = [_P, _I, _P, _P, _P, _DP]
+_lib.fbim_mlp_adam_step.argtypes = [_P, _I, _P, _P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, _DP]
+_lib.fbim_mlp_launches.argtypes = [_P]
+_lib.fbim_mlp_launches.restype = ctypes.c_longlong
+_lib.fbim_coarse_pairs.argtypes = [_P, _D, _I, _P, _P, _IP]
+_lib.fbim_coarse_enable.argtypes = [_P, _P, _D]
+_lib.fbim_coarse_stats.argtypes = [_P, _IP, _IP]
 
 
 def lib():
@@ -279,6 +302,28 @@ class FBIM:
         _check(_lib.fbim_stage_times(self._h, _dptr(ms), calls, len(STAGES)), self._h)
         return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(STAGES)}
 
+    def coarse_pairs(self, g_c, max_pairs=None):
+        """Close pairs (gap < g_c) of the current configuration: (pairs int32 [n, 2], features float64 [n, 6])."""
+        import torch
+        n = ctypes.c_int(0)
+        _check(_lib.fbim_coarse_pairs(self._h, float(g_c), 0, None, None, ctypes.byref(n)), self._h)
+        cap = n.value if max_pairs is None else min(int(max_pairs), n.value)
+        dev = torch.device("cuda", self.device)
+        pairs = torch.empty((max(cap, 1), 2), dtype=torch.int32, device=dev)
+        feats = torch.empty((max(cap, 1), 6), dtype=torch.float64, device=dev)
+        _check(_lib.fbim_coarse_pairs(self._h, float(g_c), cap, _ptr(pairs), _ptr(feats), ctypes.byref(n)), self._h)
+        return pairs[:cap], feats[:cap]
+
+    def coarse_enable(self, model, g_c):
+        """Turn the learned coarse level on with ``model`` (an MLP), or off with None."""
+        self._coarse_model = model  # keeps the network alive while the handle uses it
+        _check(_lib.fbim_coarse_enable(self._h, None if model is None else model._m, float(g_c)), self._h)
+
+    def coarse_stats(self):
+        n, r = ctypes.c_int(0), ctypes.c_int(0)
+        _check(_lib.fbim_coarse_stats(self._h, ctypes.byref(n), ctypes.byref(r)), self._h)
+        return n.value, r.value
+
     def update_config(self, Q_dev):
         _check(_lib.fbim_update_config(self._h, _ptr(Q_dev)), self._h)
 
@@ -349,6 +394,79 @@ class Batch:
         if getattr(self, "_b", None):
             _lib.fbim_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mlp_param_count() -> int:
+    return _lib.fbim_mlp_param_count()
+
+
+class MLP:
+    """Pair-correction network 6-128-128-128-36 (bf16 tensor-core products, FP32 state)."""
+
+    def __init__(self, max_batch=1024, device=0, stream=None):
+        m = _P()
+        st = _lib.fbim_mlp_create(ctypes.byref(m), int(max_batch), stream, int(device))
+        if st != 0:
+            msg = _lib.fbim_mlp_last_error(None)
+            raise FbimError(st, msg.decode() if msg else "")
+        self._m = m
+        self.max_batch = int(max_batch)
+        self.device = int(device)
+        self.n_params = mlp_param_count()
+
+    def _check(self, st):
+        if st != 0:
+            msg = _lib.fbim_mlp_last_error(self._m)
+            raise FbimError(st, msg.decode() if msg else "")
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.n_params
+        self._check(_lib.fbim_mlp_set_params(self._m, t.ctypes.data_as(_FP)))
+
+    def get_params(self):
+        t = np.empty(self.n_params, dtype=np.float32)
+        self._check(_lib.fbim_mlp_get_params(self._m, t.ctypes.data_as(_FP)))
+        return t
+
+    def set_normalization(self, in_shift, in_scale, out_scale):
+        a = [np.ascontiguousarray(x, dtype=np.float32) for x in (in_shift, in_scale, out_scale)]
+        self._check(_lib.fbim_mlp_set_normalization(self._m, *[x.ctypes.data_as(_FP) for x in a]))
+        self.normalization = a
+
+    def forward(self, X):
+        import torch
+        Y = torch.empty((X.shape[0], 36), dtype=torch.float32, device=X.device)
+        self._check(_lib.fbim_mlp_forward(self._m, int(X.shape[0]), _ptr(X), _ptr(Y)))
+        return Y
+
+    def gradient(self, X, T):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_double(0.0)
+        self._check(_lib.fbim_mlp_gradient(self._m, int(X.shape[0]), _ptr(X), _ptr(T), _ptr(g), ctypes.byref(loss)))
+        return loss.value, g
+
+    def adam_step(self, X, T, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        loss = ctypes.c_double(0.0)
+        self._check(_lib.fbim_mlp_adam_step(self._m, int(X.shape[0]), _ptr(X), _ptr(T), float(lr), float(beta1),
+                                            float(beta2), float(eps), ctypes.byref(loss)))
+        return loss.value
+
+    @property
+    def launches(self):
+        return _lib.fbim_mlp_launches(self._m)
+
+    def close(self):
+        if getattr(self, "_m", None):
+            _lib.fbim_mlp_destroy(self._m)
+            self._m = None
 
     def __del__(self):
         try:

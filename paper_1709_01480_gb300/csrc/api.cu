@@ -28,6 +28,7 @@ void release(fbim_handle h) {
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
     fbim::free_ewald(h);
+    fbim::free_coarse(h);
     cudaFree(h->ref);
     cudaFree(h->Q);
     cudaFree(h->x);

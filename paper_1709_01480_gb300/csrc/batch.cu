@@ -447,6 +447,11 @@ fbim_status batch_solve(fbim_batch B, const double* F, const double* slip, doubl
     const long long N = B->n_all;
     cudaStream_t st = B->stream;
     const bool fp32 = B->hs[0]->precision == FBIM_FP32;
+    // coarse-level pair data of moved handles (host-synchronising: before any capture)
+    for (fbim_handle h : B->hs) {
+        const fbim_status cs = fbim::coarse_refresh(h);
+        if (cs != FBIM_OK) return fail(B, std::string("coarse level: ") + h->err, cs);
+    }
     if (fp32) {
         BSTATUS(capture(B, 0));
         BSTATUS(capture(B, 2));

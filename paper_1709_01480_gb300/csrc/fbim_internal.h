@@ -146,6 +146,8 @@ struct fbim_handle_s {
 
     long long launches = 0;      // kernels this library has launched on the handle (counted at launch sites)
     unsigned long long layout_version = 0;  // bumped when a buffer that launches take by pointer is reallocated
+    unsigned long long geom_version = 0;    // bumped by every geometry rebuild
+    struct Coarse* coarse = nullptr;        // learned coarse level (coarse.cu), NULL when off
 
     int n_cell() const { return n_box * n_box; }
     void fail(const std::string& m) { err = m; }
@@ -180,6 +182,18 @@ fbim_status solver_precondition(fbim_handle_s* h, const double* in, double* out,
 fbim_status solver_saddle(fbim_handle_s* h, const double* x, double* y, bool fp32);
 // point every launch of the handle (kernels, cuFFT plans, cuBLAS) at stream s
 void bind_stream(fbim_handle_s* h, cudaStream_t s);
+
+// learned coarse level (coarse.cu)
+void free_coarse(fbim_handle_s* h);
+// true when the coarse level is on; refreshes its pair data if the geometry changed
+// (host-synchronising: call it outside stream capture first)
+bool coarse_active(fbim_handle_s* h, fbim_status* st);
+fbim_status coarse_refresh(fbim_handle_s* h);
+// body solve of the preconditioner with the coarse level: g = M_ref^+ R^T r_mu (per body,
+// precision T), H = M_ref^+ K_ref, rU = residual of the force rows; writes mu and U
+template <typename T>
+fbim_status coarse_body_solve(fbim_handle_s* h, const T* g, const T* H, const double* rU, double* out_mu,
+                              double* out_U);
 
 // operators (ewald_ops.cu)
 template <typename T> fbim_status ensure_ewald(fbim_handle_s* h);

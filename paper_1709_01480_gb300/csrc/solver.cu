@@ -422,6 +422,14 @@ static fbim_status precondition(fbim_handle_s* h, const double* in, double* out)
     const T* Mp = std::is_same<T, float>::value ? (const T*)S->Mpinv32 : (const T*)S->Mpinv64;
     const T* Hm = std::is_same<T, float>::value ? (const T*)S->H32 : (const T*)S->H64;
     FBIM_CUBLAS_TRY(h, Gemm<T>::run(S->blas, S->n2, h->n_b, S->n2, Mp, z, g));
+    fbim_status cst = FBIM_OK;
+    if (coarse_active(h, &cst)) {
+        FBIM_TRY(coarse_body_solve<T>(h, g, Hm, in + N2, out, out + N2));
+        h->launches += 1;  // k_rot_in
+        FBIM_CUDA_TRY(h, cudaGetLastError());
+        return FBIM_OK;
+    }
+    FBIM_TRY(cst);
     const double* Nt = S->Nt;
     k_body_solve<T><<<h->n_b, 128, 0, h->stream>>>(h->n_p, h->ref, h->rot, g, Hm, in + N2, Nt[0], Nt[1], Nt[2],
                                                    Nt[3], Nt[4], Nt[5], Nt[6], Nt[7], Nt[8], out, out + N2);
