@@ -16,6 +16,12 @@ with FP64 refinement; the plain form runs everything in FP64.  L2 is flushed
 The matvec alone (node-matvecs/s) and its per-stage times are measured too; the
 roofline object refers to the dominant stage of the FP32 matvec.
 
+Two further measurements ride along (``--legs``): ``batched`` solves 64
+independent suspensions (16-512 bodies, 96 nodes each, area fractions
+0.1-0.35) with 10 right-hand sides each through the graph-captured batch, and
+``learned`` times the mobility solve of a dense 4096-body suspension (area
+fraction 0.40) with and without the learned coarse level.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
 instead, on a bounded sample of the same workload.
 """
@@ -42,6 +48,9 @@ N_BOX = 115
 SOLVE_TOL = 1e-6
 DT, KT = 1e-3, 1.0
 SOLVES_PER_STEP = 3
+BATCH_WORKLOAD = "batch64_starfish_np96"
+BATCH_RHS = 10          # per suspension: 8 random slips + the RFD pair
+BATCH_RC = 0.504
 # GMRES iterations per solve of the chosen form on this workload (measured); the
 # CPU baseline prices a solve as this many oracle matvecs plus one residual check
 ITERS_PER_SOLVE_REF = 16
@@ -207,6 +216,86 @@ def timed(torch, stream, flush, fn, n):
     return out
 
 
+def batched_leg(torch, fb, fbim_synth, stream, flush, reps):
+    """Independent suspensions with several right-hand sides through the graph-captured batch."""
+    ws = fbim_synth.batch(BATCH_WORKLOAD)
+    R = BATCH_RHS
+    ops = [fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=BATCH_RC, precision="fp32") for w in ws]
+    g = np.random.default_rng(5)
+    # per suspension: random forces, R - 2 random slips, and the two unit-scale RFD solves (force only)
+    F, S = [], []
+    for w in ws:
+        for r in range(R):
+            F.append(torch.tensor(g.standard_normal((w.n_b, 3)), device="cuda"))
+            S.append(torch.tensor(g.standard_normal((w.n, 2)) if r < R - 2 else np.zeros((w.n, 2)), device="cuda"))
+    batch = fb.Batch(ops, [R] * len(ops))
+    U, it, res = batch.solve(F, S, tol=SOLVE_TOL, max_iter=400)     # warm-up: captures the graphs
+    k0 = batch.info()["launches"]
+    ms = timed(torch, stream, flush, lambda i: batch.solve(F, S, tol=SOLVE_TOL, max_iter=400), reps)
+    info = batch.info()
+    n_sys = len(it)
+    # sequential single solves of the same systems on a sample, for comparison
+    n_seq = min(n_sys, 40)
+    idx = np.linspace(0, n_sys - 1, n_seq).astype(int)
+    t0 = time.time()
+    seq_it = []
+    for i in idx:
+        k = i // R
+        _, _, its, _ = ops[k].mobility_solve(F[i], S[i], tol=SOLVE_TOL, max_iter=400)
+        seq_it.append(its)
+    torch.cuda.synchronize()
+    seq_rate = n_seq / (time.time() - t0)
+    out = {"workload": BATCH_WORKLOAD, "suspensions": len(ws), "rhs_per_suspension": R,
+           "systems": n_sys, "nodes": int(sum(w.n for w in ws)),
+           "node_rhs": int(sum(w.n for w in ws) * R), "value": n_sys / (float(np.mean(ms)) * 1e-3),
+           "unit": "mobility solves/s", "ms_per_batch_solve": float(np.mean(ms)), "reps": reps,
+           "gmres_iters_mean": float(np.mean(it)), "gmres_iters_max": int(np.max(it)),
+           "worst_residual": float(np.max(res)), "graph_kernels": info["graph_kernels"],
+           "kernels_per_batch_solve": (info["launches"] - k0) / max(reps, 1),
+           "graph_launches": info["graph_launches"], "branches": info["branches"],
+           "sequential_single_solves_per_s": seq_rate, "sequential_iters_mean": float(np.mean(seq_it)),
+           "precision": "FP32 operators, FP64 residuals and Krylov vectors"}
+    batch.close()
+    for o in ops:
+        o.close()
+    return out
+
+
+def learned_leg(torch, fb, fbim_synth, stream, flush, reps):
+    """GMRES with and without the learned coarse level on the dense suspension."""
+    from paper_1709_01480_gb300 import coarse_train
+    w = fbim_synth.dense_workload("dense4096_np128_phi0.40", **fbim_synth.DENSE)
+    model, meta = coarse_train.load(os.path.join(ROOT, "paper_1709_01480_gb300", "coarse_pair_mlp.npz"))
+    op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=0.5, precision="fp32")
+    F = torch.tensor(w.F, device="cuda")
+    slip = torch.tensor(np.random.default_rng(6).standard_normal((w.n, 2)), device="cuda")
+    res = {}
+    for mode in ("block_diagonal", "learned_coarse"):
+        if mode == "learned_coarse":
+            t0 = time.time()
+            op.coarse_enable(model, float(meta["g_c"]))
+            torch.cuda.synchronize()
+            setup_s = time.time() - t0
+        its = []
+
+        def solve(i):
+            _, _, it, r = op.mobility_solve(F, slip, tol=SOLVE_TOL, max_iter=800, check=False)
+            its.append((it, r))
+        solve(0)
+        ms = timed(torch, stream, flush, solve, reps)
+        res[mode] = {"ms_per_solve": float(np.mean(ms)), "gmres_iters": its[-1][0], "residual": its[-1][1],
+                     "solves_per_s": 1e3 / float(np.mean(ms))}
+    n_pairs, n_rej = op.coarse_stats()
+    res["learned_coarse"].update({"pairs": n_pairs, "pairs_dropped": n_rej, "setup_s": setup_s})
+    op.coarse_enable(None, 1.0)
+    op.close()
+    model.close()
+    return {"workload": "dense4096_np128_phi0.40 (jittered lattice, gaps >= 0.05 R)", "n_nodes": w.n,
+            "rhs": "random forces + random slip", "model": {"pairs": int(meta["pairs"]),
+                                                            "validation_mse": float(meta["final_val"])},
+            **res}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -340,6 +429,12 @@ def run_gpu(args):
     e2e = {"value": world * SOLVES_PER_STEP / (e2e_ms * 1e-3), "unit": UNIT,
            "h2d_bytes_per_step": F_h.numel() * 8 + Q_h.numel() * 8, "d2h_bytes_per_step": Q_out.numel() * 8}
 
+    legs = {}
+    if "batched" in args.legs:
+        legs["batched"] = batched_leg(torch, fb, fbim_synth, stream, flush, 2)
+    if "learned" in args.legs:
+        legs["learned_coarse"] = learned_leg(torch, fb, fbim_synth, stream, flush, 2)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         val, t_solve, sample = oracle_solve_rate(w, xi, 48, 4096, 0)
@@ -370,6 +465,7 @@ def run_gpu(args):
             "e2e": e2e,
             "gpu_launches": int(launches),
             "cpu_baseline": cpu,
+            **legs,
         }
         print(json.dumps(line), flush=True)
     for op in ops.values():
@@ -385,6 +481,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="batched,learned",
+                    help="extra measurements: batched (independent suspensions), learned (coarse level); '' for none")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

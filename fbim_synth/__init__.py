@@ -23,7 +23,7 @@ import numpy as np
 __all__ = [
     "starfish_ref_nodes", "starfish_area", "disk_ref_nodes", "place_bodies",
     "random_forces", "Workload", "WORKLOADS", "make_workload", "box_for_fraction",
-    "BATCHES", "suspension_batch", "batch",
+    "BATCHES", "suspension_batch", "batch", "place_lattice", "dense_workload",
 ]
 
 
@@ -234,3 +234,43 @@ BATCHES = {
 
 def batch(name: str) -> list:
     return suspension_batch(name, **BATCHES[name])
+
+
+def place_lattice(n_b: int, L: float, ref_nodes: np.ndarray, min_gap: float, seed: int) -> np.ndarray:
+    """Jittered square lattice for dense suspensions (random sequential placement jams there).
+
+    Sites of a k x k lattice (k = ceil(sqrt(n_b)), spacing a = L / k; n_b of them
+    drawn at random when n_b < k^2), each centre moved uniformly by at most
+    j = (a - 2 r_env - min_gap) / 2 per axis, orientations uniform on [0, 2 pi).
+    Any two bodies then stay at least min_gap apart whatever their orientation
+    (r_env = the outline's largest radius).  Returns Q [n_b, 3].
+    """
+    rng = np.random.default_rng(seed)
+    k = int(math.ceil(math.sqrt(n_b)))
+    a = L / k
+    r_env = float(np.max(np.linalg.norm(_dense_outline(ref_nodes), axis=1)))
+    j = 0.5 * (a - 2.0 * r_env - min_gap)
+    if j < 0:
+        raise ValueError(f"lattice spacing {a:.4f} too small for envelope {2 * r_env:.4f} + gap {min_gap}")
+    sites = rng.permutation(k * k)[:n_b] if n_b < k * k else np.arange(k * k)
+    ix, iy = sites % k, sites // k
+    Q = np.zeros((n_b, 3))
+    Q[:, 0] = ((ix + 0.5) * a + rng.uniform(-j, j, n_b)) % L
+    Q[:, 1] = ((iy + 0.5) * a + rng.uniform(-j, j, n_b)) % L
+    Q[:, 2] = rng.uniform(0.0, 2.0 * np.pi, n_b)
+    return Q
+
+
+def dense_workload(name: str, n_b: int, n_p: int, phi: float, min_gap: float, tol: float = 1e-8,
+                   seed: int = 0) -> Workload:
+    """Workload placed on a jittered lattice (``place_lattice``), forces as ``make_workload``."""
+    ref = starfish_ref_nodes(n_p)
+    L = box_for_fraction(n_b, starfish_area(), phi)
+    Q = place_lattice(n_b, L, ref, min_gap, seed)
+    F = random_forces(n_b, seed + 1000)
+    return Workload(name, n_b, n_p, float(L), tol, Q, ref, F, seed, min_gap, n_b * starfish_area() / (L * L))
+
+
+# The dense suspension of the learned coarse level: 4096 starfish, 128 nodes each, area
+# fraction 0.40, gaps down to 0.05 R (R = 0.65, the largest radius).
+DENSE = dict(n_b=4096, n_p=128, phi=0.40, min_gap=0.05 * 0.65, tol=1e-8, seed=0)

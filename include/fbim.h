@@ -65,6 +65,9 @@ typedef struct {
     int    restart;       /* GMRES restart length, default 60                                   */
     int    autotune;      /* wave-space kernels: 1 (default) time both variants at setup and keep
                              the faster; 0 shared-memory tile kernels; 2 warp-per-node kernels */
+    int    grid_tune;     /* 1 (default): when grid <= 0, time the FFT of a few admissible sides in
+                             [M_min, 1.3 M_min] and keep the cheapest (any side >= the rule's M_min
+                             meets tol); 0: use M_min                                          */
 } fbim_params;
 
 /* Ewald parameters the library settled on (fbim_get_info). */
@@ -85,6 +88,8 @@ typedef struct {
     double variant_ms[2];    /* autotuner timings (ms) of spread + interp per variant  */
     long long launches;      /* kernels this library has launched for the handle so far
                                 (library calls such as cuFFT and cuBLAS not included)  */
+    int    grid_min;         /* the grid rule's smallest admissible side M_min          */
+    double grid_tune_ms;     /* tuned cost (ms) of the chosen side's FFT pair, 0 if untuned */
 } fbim_info;
 
 /* Fill *p with defaults: FP64, order 4, automatic grid and support, eta = 1,

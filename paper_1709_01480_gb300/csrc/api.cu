@@ -79,6 +79,7 @@ extern "C" fbim_status fbim_default_params(fbim_params* p) {
     p->device = 0;
     p->restart = 60;
     p->autotune = 1;
+    p->grid_tune = 1;
     return FBIM_OK;
 }
 
@@ -152,8 +153,15 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
             h->fail(err);
             return FBIM_ERR_INVALID_ARG;
         }
-        if (p.grid > 0) M = p.grid + (p.grid & 1);
         if (p.support > 0) P = p.support | 1;
+        h->M_min = M;
+        if (p.grid > 0) {
+            M = p.grid + (p.grid & 1);
+        } else if (p.grid_tune) {
+            FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
+            h->precision = p.precision;
+            FBIM_TRY(fbim::tune_grid(h, M, P, M, h->grid_tune_ms));
+        }
         // wave-space tiles: TS divides M, TS <= 64, and a node's window (P - 1)/2 points
         // to each side never reaches past the neighbouring tile
         auto tile_side = [](int m) {
@@ -308,6 +316,8 @@ extern "C" fbim_status fbim_get_info(fbim_handle h, fbim_info* info) {
     info->variant_ms[0] = f32 ? h->e32.variant_ms[0] : h->e64.variant_ms[0];
     info->variant_ms[1] = f32 ? h->e32.variant_ms[1] : h->e64.variant_ms[1];
     info->launches = h->launches;
+    info->grid_min = h->M_min;
+    info->grid_tune_ms = h->grid_tune_ms;
     return FBIM_OK;
 }
 

@@ -57,15 +57,21 @@ __global__ void k_offsets(int N, const int* __restrict__ perm, const int* __rest
 }
 
 template <typename T>
-__global__ void k_gather(int N, const int* __restrict__ perm, const int* __restrict__ tperm, int want_s, int want_t,
-                         const double2* __restrict__ mu, typename V2<T>::type* __restrict__ mu_s,
-                         typename V2<T>::type* __restrict__ mu_t) {
+__global__ void k_gather(int N, int n_p, const int* __restrict__ perm, const int* __restrict__ tperm, int want_s,
+                         int want_t, const double* __restrict__ rot, const double2* __restrict__ mu,
+                         typename V2<T>::type* __restrict__ mu_s, typename V2<T>::type* __restrict__ mu_t,
+                         double2* __restrict__ mu_r) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     if (want_s) {
         double2 v = mu[perm[s]];
         mu_s[s].x = (T)v.x;
         mu_s[s].y = (T)v.y;
+        // node s in body order, rotated into its body's frame for the Alpert band
+        const int b = s / n_p;
+        const double c = rot[2 * b], sn = rot[2 * b + 1];
+        const double2 u = mu[s];
+        mu_r[s] = make_double2(c * u.x + sn * u.y, -sn * u.x + c * u.y);
     }
     if (want_t) {
         double2 v = mu[tperm[s]];
@@ -222,11 +228,13 @@ __global__ void k_scale(int M, T twopi_L, T inv4xi2, T one_minus_eta, T pref,
 }
 
 // Back to body order: v_m = v_s[slot[m]] + v_t[tslot[m]] + R_b A_ref[j] R_b^T mu (FP64 band).
+// mu_r: the forces already rotated into their body's frame (k_gather), so the band
+// costs four FP64 FMAs per entry.
 template <typename T>
 __global__ void k_finish(int N, int n_p, int band, int with_real, int with_wave, const int* __restrict__ slot,
                          const int* __restrict__ tslot, const typename V2<T>::type* __restrict__ v_s,
-                         const typename V2<T>::type* __restrict__ v_t, const double* __restrict__ Q,
-                         const double* __restrict__ A, const double2* __restrict__ mu, double2* __restrict__ v) {
+                         const typename V2<T>::type* __restrict__ v_t, const double* __restrict__ rot,
+                         const double* __restrict__ A, const double2* __restrict__ mu_r, double2* __restrict__ v) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= N) return;
     double vx = 0, vy = 0;
@@ -235,20 +243,19 @@ __global__ void k_finish(int N, int n_p, int band, int with_real, int with_wave,
         vx = (double)w.x;
         vy = (double)w.y;
         int b = m / n_p, j = m - b * n_p;
-        double c, s;
-        sincos(Q[3 * b + 2], &s, &c);
+        const double c = rot[2 * b], s = rot[2 * b + 1];
         double ax = 0, ay = 0;
         const int B = 2 * band + 1;
+        const double2* ub = mu_r + (size_t)b * n_p;
+        const double4_32a* a4 = reinterpret_cast<const double4_32a*>(A) + (size_t)j * B;
         for (int o = -band; o <= band; ++o) {
             int jj = j + o;
             jj += (jj < 0) ? n_p : 0;
             jj -= (jj >= n_p) ? n_p : 0;
-            double2 u = mu[b * n_p + jj];
-            // rotate into the reference frame: R^T u
-            double rx = c * u.x + s * u.y, ry = -s * u.x + c * u.y;
-            const double* a = A + ((size_t)j * B + (o + band)) * 4;
-            ax += a[0] * rx + a[1] * ry;
-            ay += a[2] * rx + a[3] * ry;
+            const double2 u = ub[jj];
+            const double4_32a a = a4[o + band];
+            ax += a.x * u.x + a.y * u.y;
+            ay += a.z * u.x + a.w * u.y;
         }
         vx += c * ax - s * ay;
         vy += s * ax + c * ay;
@@ -393,6 +400,7 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&e.tfrac, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_t, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.v_t, N * sizeof(T2)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_r, N * sizeof(double2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.grid, 2 * M * M * sizeof(T)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.spec, 2 * M * Mh * sizeof(C)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, scan_storage((int)n_slice) * sizeof(int)));
@@ -425,8 +433,8 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     const int N = h->N, tb = 256;
     const bool real = which & 1, wave = which & 2;
     h->mark_begin();
-    k_gather<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->perm, h->tperm, real, wave, (const double2*)mu,
-                                                         (T2*)e.mu_s, (T2*)e.mu_t);
+    k_gather<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->perm, h->tperm, real, wave, h->rot,
+                                                         (const double2*)mu, (T2*)e.mu_s, (T2*)e.mu_t, e.mu_r);
     h->mark(FBIM_ST_GATHER);
     const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
     const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
@@ -466,8 +474,8 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         h->mark(FBIM_ST_INTERP);
     }
     k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, real ? 1 : 0, wave ? 1 : 0, h->slot,
-                                                         h->tslot, (const T2*)e.v_s, (const T2*)e.v_t, h->Q,
-                                                         h->band_dev, (const double2*)mu, (double2*)v);
+                                                         h->tslot, (const T2*)e.v_s, (const T2*)e.v_t, h->rot,
+                                                         h->band_dev, e.mu_r, (double2*)v);
     h->mark(FBIM_ST_FINISH);
     h->launches += 2 + (wave ? 3 : 0) + (real ? 1 : 0);
     FBIM_CUDA_TRY(h, cudaGetLastError());
@@ -582,6 +590,7 @@ static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.tfrac);
     cudaFree(e.mu_t);
     cudaFree(e.v_t);
+    cudaFree(e.mu_r);
     cudaFree(e.grid);
     cudaFree(e.spec);
     cudaFree(e.pairs);

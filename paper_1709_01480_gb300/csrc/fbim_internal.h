@@ -60,6 +60,7 @@ struct EwaldBuffers {
     void* tfrac = nullptr;   // [N] T2: x / h - base in [-1/2, 1/2], tile-sorted
     void* mu_t = nullptr;    // [N] T2: forces in tile-sorted order (wave space)
     void* v_t = nullptr;     // [N] T2: wave-space velocities, tile-sorted
+    double2* mu_r = nullptr; // [N] forces rotated into their body's frame (body order, FP64)
     T* grid = nullptr;       // [2][M][M] real grid (component-major)
     void* spec = nullptr;    // [2][M][M/2+1] complex half spectrum
     cufftHandle plan_f = 0;  // R2C / D2Z, batch 2
@@ -121,6 +122,8 @@ struct fbim_handle_s {
     int* tile_tmp = nullptr;     // [N] tile id of each node (scratch of the sort)
     int TS = 0, n_tile = 0;      // tile side (divides M) and tiles per side
     int autotune = 1;            // time the wave-space kernel variants at setup
+    int M_min = 0;               // the grid rule's smallest side
+    double grid_tune_ms = 0;     // cost of the tuned FFT pair (0: not tuned)
     double zmax = 0;             // xi^2 r_c^2 (upper end of the E1 expansion)
     fbim::ChebE1<double> cheb64{};
     fbim::ChebE1<float> cheb32{};
@@ -165,6 +168,8 @@ void reference_blocks(fbim_handle_s* h, const std::vector<double>& band_sym, std
                       std::vector<double>& Mfull);
 fbim_status choose_ewald(double L, double r_c, double tol, double xi_in, int& n_box, double& r_c_out,
                          double& xi, int& M, int& P, double& eta_s, std::string& err);
+// grid autotuner (tune.cu): cheapest admissible FFT side in [M_min, 1.3 M_min]
+fbim_status tune_grid(fbim_handle_s* h, int M_min, int P, int& M_out, double& best_ms);
 
 // geometry (geometry.cu)
 fbim_status build_geometry(fbim_handle_s* h);

@@ -443,7 +443,7 @@ static fbim_status precondition(fbim_handle_s* h, const double* in, double* out)
 // relative residual |b - A x| / |b| of the last cycle.
 template <typename T>
 static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double tol, int max_iter, int& iters,
-                          double& rel_est, bool x_is_zero = false) {
+                          double& rel_est, bool x_is_zero = false, bool trust_estimate = false) {
     Solver* S = h->solver;
     const int n = S->n, m = S->restart, ld = S->ld;
     cublasHandle_t B = S->blas;
@@ -539,6 +539,13 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
         FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->hcol, y.data(), sizeof(double) * k_used, cudaMemcpyHostToDevice,
                                          h->stream));
         FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k_used, &one, S->Z, ld, S->hcol, 1, &one, x, 1));
+        // A correction of iterative refinement stops on the cycle's own estimate: the
+        // outer loop measures the true FP64 residual anyway, and a restart started only
+        // because the FP32 residual lands just above the inner tolerance costs a cycle.
+        if (trust_estimate && k_used > 0) {
+            rel_est = std::fabs(gvec[k_used]) / bnorm;
+            if (rel_est <= tol || iters >= max_iter) return FBIM_OK;
+        }
     }
 }
 
@@ -594,7 +601,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
             cudaMemsetAsync(corr, 0, sizeof(double) * n, h->stream);
             int it = 0;
             double est = 0;
-            st = fgmres<float>(h, S->r, corr, inner, std::min(max_iter - iters, S->restart), it, est, true);
+            st = fgmres<float>(h, S->r, corr, inner, std::min(max_iter - iters, S->restart), it, est, true, true);
             if (st != FBIM_OK) break;
             iters += it;
             k_axpby<<<nb, tb, 0, h->stream>>>(n, 1.0, corr, 1.0, S->d);
