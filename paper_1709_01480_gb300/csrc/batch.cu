@@ -125,6 +125,12 @@ __global__ void k_sub(long long n, const double* __restrict__ b, double* __restr
     if (t < n) w[t] = b[t] - w[t];
 }
 
+// r -= w
+__global__ void k_dec(long long n, const double* __restrict__ w, double* __restrict__ r) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) r[t] -= w[t];
+}
+
 __global__ void k_add(long long n, const double* __restrict__ d, double* __restrict__ x) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) x[t] += d[t];
@@ -471,37 +477,57 @@ fbim_status batch_solve(fbim_batch B, const double* F, const double* slip, doubl
         BSTATUS(batched_fgmres(B, 1, 3, B->b, B->x, std::vector<double>(n, tol), max_iter, it, est));
         it_tot = it;
     } else {
-        // iterative refinement: FP64 residual, FP32-operator correction
+        // iterative refinement (as in the single solve): FP32-operator corrections; the
+        // residual is recomputed with the FP64 operators after a correction taken from a
+        // residual above 1e-3, else advanced by the inner GMRES's estimate (and, when
+        // another correction follows, by r - A_32 d)
         BTRY(cudaMemsetAsync(B->x, 0, sizeof(double) * N, st));
         BTRY(cudaMemcpyAsync(B->r, B->b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        for (int i = 0; i < n; ++i) rel[i] = bn[i] > 0 ? 1.0 : 0.0;
         std::vector<double> inner(n, 1e-4), keep(n, 1.0);
         int used = 0;
         for (int outer = 0; outer < 40; ++outer) {
-            if (outer > 0) {
-                BSTATUS(final_residual(B, bn, rel));
-                have_rel = true;
-                double worst = 0;
-                for (int i = 0; i < n; ++i) {
-                    worst = std::max(worst, rel[i]);
-                    // a converged system gets no further correction; the others
-                    // aim a little below the outer tolerance
-                    keep[i] = rel[i] <= tol ? 0.0 : 1.0;
-                    inner[i] = rel[i] > 0 ? std::max(0.3 * tol / rel[i], 1e-4) : 1e-4;
-                }
-                if (worst <= tol || used >= max_iter) break;
-                BSTATUS(seg_scale(B, keep, B->r, B->r));
-                have_rel = false;
+            double worst = 0;
+            for (int i = 0; i < n; ++i) worst = std::max(worst, rel[i]);
+            if (worst <= tol || used >= max_iter) break;
+            for (int i = 0; i < n; ++i) {
+                // a converged system gets no further correction; the others aim a
+                // little below the outer tolerance
+                keep[i] = rel[i] <= tol ? 0.0 : 1.0;
+                inner[i] = rel[i] > 0 ? std::max(0.3 * tol / rel[i], 1e-4) : 1e-4;
             }
+            if (outer > 0) BSTATUS(seg_scale(B, keep, B->r, B->r));
             BSTATUS(batched_fgmres(B, 0, 2, B->r, B->d, inner, std::min(max_iter - used, B->m), it, est));
             int mx = 0;
+            double big = 0;
             for (int i = 0; i < n; ++i) {
                 it_tot[i] += it[i];
                 mx = std::max(mx, it[i]);
+                if (keep[i] > 0) big = std::max(big, rel[i]);
             }
             used += std::max(mx, 1);
             k_add<<<blocks(N, tb), tb, 0, st>>>(N, B->d, B->x);
             B->launches += 1;
+            if (big > 1e-3) {
+                BSTATUS(final_residual(B, bn, rel));
+            } else {
+                bool more = false;
+                for (int i = 0; i < n; ++i) {
+                    if (keep[i] > 0) rel[i] *= est[i];
+                    more = more || rel[i] > tol;
+                }
+                if (more && used < max_iter) {
+                    BSTATUS(run_graph(B, 2, B->d, nullptr, B->w));
+                    k_dec<<<blocks(N, tb), tb, 0, st>>>(N, B->w, B->r);
+                    B->launches += 1;
+                    std::vector<double> rr;
+                    BSTATUS(seg_norms2(B, B->r, rr));
+                    for (int i = 0; i < n; ++i)
+                        if (keep[i] > 0) rel[i] = bn[i] > 0 ? std::sqrt(rr[i]) / bn[i] : 0.0;
+                }
+            }
         }
+        have_rel = true;
     }
     if (!have_rel) BSTATUS(final_residual(B, bn, rel));
     k_batch_u<<<blocks(N, tb), tb, 0, st>>>(N, B->d_off, n, B->d_two_n, B->d_f_off, B->x, U);

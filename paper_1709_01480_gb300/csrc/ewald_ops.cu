@@ -364,7 +364,7 @@ static fbim_status autotune_wave(fbim_handle_s* h) {
                 warp_spread<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.mu_t, e.grid);
                 warp_interp<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.grid, e.v_t);
             } else {
-                tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid);
+                tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
                 tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
             }
             cudaEventRecord(ev[1], h->stream);
@@ -401,6 +401,10 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_t, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.v_t, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_r, N * sizeof(double2)));
+    {
+        const size_t W = h->TS + h->P - 1;
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.ring, (size_t)h->n_tile * h->n_tile * 2 * W * W * sizeof(T)));
+    }
     FBIM_CUDA_TRY(h, cudaMalloc(&e.grid, 2 * M * M * sizeof(T)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.spec, 2 * M * Mh * sizeof(C)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, scan_storage((int)n_slice) * sizeof(int)));
@@ -446,7 +450,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
             FBIM_CUDA_TRY(h, cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream));
             warp_spread<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.mu_t, e.grid);
         } else {
-            tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid);
+            tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
         }
         h->mark(FBIM_ST_SPREAD);
         FBIM_CUFFT_TRY(h, FftType<T>::f(e.plan_f, e.grid, (C*)e.spec));
@@ -477,7 +481,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
                                                          h->tslot, (const T2*)e.v_s, (const T2*)e.v_t, h->rot,
                                                          h->band_dev, e.mu_r, (double2*)v);
     h->mark(FBIM_ST_FINISH);
-    h->launches += 2 + (wave ? 3 : 0) + (real ? 1 : 0);
+    h->launches += 2 + (wave ? (e.wave_variant == 1 ? 3 : 4) : 0) + (real ? 1 : 0);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     h->collect();
     return FBIM_OK;
@@ -591,6 +595,7 @@ static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.mu_t);
     cudaFree(e.v_t);
     cudaFree(e.mu_r);
+    cudaFree(e.ring);
     cudaFree(e.grid);
     cudaFree(e.spec);
     cudaFree(e.pairs);

@@ -108,9 +108,11 @@ struct TileGeom {
 // wave_tiles_f64.cu).  Return cudaSuccess or the attribute error.
 template <typename T>
 cudaError_t tile_set_smem(const TileGeom& tg);
+// tile_spread writes every grid point (no zeroing needed); ring: the per-tile halo
+// buffer of spread_ring_elems(TS, P, n_tile) elements.  Two launches.
 template <typename T>
 void tile_spread(cudaStream_t st, const TileGeom& tg, T a, T g0, const int* tstart, const int2* tbase,
-                 const void* tfrac, const void* mu_t, T* grid);
+                 const void* tfrac, const void* mu_t, T* grid, T* ring);
 template <typename T>
 void tile_interp(cudaStream_t st, const TileGeom& tg, T a, T g0, const int* tstart, const int2* tbase,
                  const void* tfrac, const T* grid, void* v_t);

@@ -351,7 +351,12 @@ fbim_status setup_solver(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&S->r, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->d, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->t, sizeof(double) * n));
-    FBIM_CUDA_TRY(h, cudaMalloc(&S->hcol, sizeof(double) * 2 * (m + 1)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->corr, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->hcol, sizeof(double) * (2 * (m + 1) + 1)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->gin, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->gz, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->gw, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(S->gin, 0, sizeof(double) * n, h->stream));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->zbuf, sizeof(double) * 2 * h->N));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gbuf, sizeof(double) * 2 * h->N));
     if (cublasCreate(&S->blas) != CUBLAS_STATUS_SUCCESS) {
@@ -376,8 +381,12 @@ void free_solver(fbim_handle_s* h) {
     for (void* p : {(void*)S->Mpinv64, (void*)S->Mpinv32, (void*)S->H64, (void*)S->H32, (void*)S->G64,
                     (void*)S->Gd64, (void*)S->G32, (void*)S->Gd32, (void*)S->V, (void*)S->Z, (void*)S->w,
                     (void*)S->r, (void*)S->d, (void*)S->t, (void*)S->hcol, S->zbuf, S->gbuf, (void*)S->lz,
-                    (void*)S->lh, (void*)S->rfd, S->blas_ws})
+                    (void*)S->lh, (void*)S->rfd, S->blas_ws, (void*)S->corr, (void*)S->gin, (void*)S->gz,
+                    (void*)S->gw})
         cudaFree(p);
+    for (cudaGraphExec_t g : S->op_graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (S->cap) cudaStreamDestroy(S->cap);
     if (S->blas) cublasDestroy(S->blas);
     delete S;
     h->solver = nullptr;
@@ -438,6 +447,56 @@ static fbim_status precondition(fbim_handle_s* h, const double* in, double* out)
     return FBIM_OK;
 }
 
+// The Krylov step's operator, z = P v and w = A z, captured once as a CUDA graph on
+// fixed buffers (gin -> gz, gw) so that each step costs one graph launch instead of
+// some twenty kernel, cuFFT and cuBLAS launches.  Recaptured when a buffer the
+// launches hold by pointer was reallocated (layout_version).
+template <typename T>
+static fbim_status op_graph(fbim_handle_s* h) {
+    Solver* S = h->solver;
+    const int k = std::is_same<T, float>::value ? 0 : 1;
+    if (S->op_graph[k] && S->op_version[k] == h->layout_version) return FBIM_OK;
+    if (S->op_graph[k]) {
+        cudaGraphExecDestroy(S->op_graph[k]);
+        S->op_graph[k] = nullptr;
+    }
+    // warm-up outside the capture: first use allocates, plans and refreshes
+    FBIM_TRY(precondition<T>(h, S->gin, S->gz));
+    FBIM_TRY(saddle_apply<T>(h, S->gz, S->gw));
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (!S->cap) FBIM_CUDA_TRY(h, cudaStreamCreateWithFlags(&S->cap, cudaStreamNonBlocking));
+    const cudaStream_t orig = h->stream;
+    const bool timing = h->timing;
+    const long long l0 = h->launches;
+    h->timing = false;
+    FBIM_CUDA_TRY(h, cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal));
+    bind_stream(h, S->cap);
+    fbim_status st = precondition<T>(h, S->gin, S->gz);
+    if (st == FBIM_OK) st = saddle_apply<T>(h, S->gz, S->gw);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(S->cap, &graph);
+    bind_stream(h, orig);
+    h->timing = timing;
+    S->op_kernels[k] = h->launches - l0;
+    h->launches = l0;  // captured, not run
+    if (st != FBIM_OK || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (st != FBIM_OK) return st;
+        h->fail(std::string("operator capture: ") + cudaGetErrorString(ee));
+        return FBIM_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&S->op_graph[k], graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        S->op_graph[k] = nullptr;
+        h->fail(std::string("operator graph instantiate: ") + cudaGetErrorString(ie));
+        return FBIM_ERR_CUDA;
+    }
+    S->op_version[k] = h->layout_version;
+    return FBIM_OK;
+}
+
 // Restarted flexible GMRES for A x = b with the operator and preconditioner in precision T.
 // x holds the initial guess on entry.  Returns the iteration count and the estimated
 // relative residual |b - A x| / |b| of the last cycle.
@@ -455,7 +514,12 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
         FBIM_CUDA_TRY(h, cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
         return FBIM_OK;
     }
-    std::vector<double> Hh((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), hc(2 * (m + 1));
+    std::vector<double> Hh((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), hc(2 * (m + 1) + 1);
+    const bool use_graph = !h->timing;
+    if (use_graph) {
+        FBIM_TRY(coarse_refresh(h));  // host-synchronising, and may reallocate: before the graph check
+        FBIM_TRY(op_graph<T>(h));
+    }
     const double one = 1.0, mone = -1.0, zero = 0.0;
     const int tb = 256, nb = (n + tb - 1) / tb;
     bool first = true;
@@ -486,8 +550,17 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
         for (int k = 0; k < m; ++k) {
             double* vk = S->V + (size_t)k * ld;
             double* zk = S->Z + (size_t)k * ld;
-            FBIM_TRY(precondition<T>(h, vk, zk));
-            FBIM_TRY(saddle_apply<T>(h, zk, S->w));
+            if (use_graph) {
+                const int gk = std::is_same<T, float>::value ? 0 : 1;
+                FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->gin, vk, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+                FBIM_CUDA_TRY(h, cudaGraphLaunch(S->op_graph[gk], h->stream));
+                FBIM_CUDA_TRY(h, cudaMemcpyAsync(zk, S->gz, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+                FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->w, S->gw, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+                h->launches += S->op_kernels[gk];
+            } else {
+                FBIM_TRY(precondition<T>(h, vk, zk));
+                FBIM_TRY(saddle_apply<T>(h, zk, S->w));
+            }
             // classical Gram-Schmidt, twice
             FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero, S->hcol, 1));
             FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol, 1, &one, S->w, 1));
@@ -495,11 +568,15 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
                                            S->hcol + (m + 1), 1));
             FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol + (m + 1), 1, &one,
                                            S->w, 1));
-            double hn = 0;
-            FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, S->w, &hn));
-            FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->hcol, sizeof(double) * 2 * (m + 1), cudaMemcpyDeviceToHost,
-                                             h->stream));
+            // |w|^2 on the device next to the dot products: one read-back, one sync per step
+            cublasSetPointerMode(B, CUBLAS_POINTER_MODE_DEVICE);
+            const cublasStatus_t ds = cublasDdot(B, n, S->w, 1, S->w, 1, S->hcol + 2 * (m + 1));
+            cublasSetPointerMode(B, CUBLAS_POINTER_MODE_HOST);
+            FBIM_CUBLAS_TRY(h, ds);
+            FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->hcol, sizeof(double) * (2 * (m + 1) + 1),
+                                             cudaMemcpyDeviceToHost, h->stream));
             FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            const double hn = std::sqrt(std::max(hc[2 * (m + 1)], 0.0));
             double* col = &Hh[(size_t)k * (m + 1)];
             for (int i = 0; i <= k; ++i) col[i] = hc[i] + hc[(m + 1) + i];
             col[k + 1] = hn;
@@ -580,24 +657,23 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
         FBIM_TRY(fgmres<double>(h, S->t, S->d, tol, max_iter, iters, est, true));
         FBIM_TRY(true_residual(h, S->t, S->d, S->r, rel));
     } else {
-        // iterative refinement: FP64 residual, FP32 corrections
-        double* corr = nullptr;
-        FBIM_CUDA_TRY(h, cudaMalloc(&corr, sizeof(double) * n));
+        // Iterative refinement: FP32-operator corrections, FP64 residuals.  r holds the
+        // residual b - A x and rel = |r| / |b|.  After a correction d computed from a
+        // residual that is not yet small (rel > 1e-3), x has changed by O(|x|) and r is
+        // recomputed from scratch with the FP64 operator.  After a later correction,
+        // |d| ~ rel |x|, so the inner GMRES's own residual estimate gives the new rel and
+        // r - A_32 d the new residual to within ~3e-7 rel |b| (the FP32 operator's
+        // error on d): one FP64 matvec per solve instead of one per correction.
+        double* corr = S->corr;
         fbim_status st = FBIM_OK;
-        for (int outer = 0; outer < 40; ++outer) {
-            if (outer == 0) {
-                // x = 0: the residual is b itself
-                cudaMemcpyAsync(S->r, S->t, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);
-                rel = 1.0;
-            } else {
-                st = true_residual(h, S->t, S->d, S->r, rel);
-                if (st != FBIM_OK || rel <= tol || iters >= max_iter) break;
-            }
+        cudaMemcpyAsync(S->r, S->t, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);  // x = 0
+        rel = 1.0;
+        for (int outer = 0; outer < 40 && rel > tol && iters < max_iter; ++outer) {
             // Each correction solves A d = r with the FP32 operator to a relative 1e-4
             // (or tighter when that already meets tol), within one restart cycle: the
             // FP32 operator cannot resolve residuals much below ~1e-5 of a right-hand
             // side like the random slip, and refinement gains its factor per step.
-            double inner = std::max(0.3 * tol / rel, 1e-4);
+            const double inner = std::max(0.3 * tol / rel, 1e-4);
             cudaMemsetAsync(corr, 0, sizeof(double) * n, h->stream);
             int it = 0;
             double est = 0;
@@ -606,8 +682,24 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
             iters += it;
             k_axpby<<<nb, tb, 0, h->stream>>>(n, 1.0, corr, 1.0, S->d);
             h->launches += 1;
+            if (rel > 1e-3) {
+                st = true_residual(h, S->t, S->d, S->r, rel);
+                if (st != FBIM_OK) break;
+            } else {
+                const double rel_prev = rel;
+                rel = est * rel_prev;
+                if (rel > tol && iters < max_iter) {
+                    // another correction follows: r <- r - A_32 d
+                    FBIM_TRY(saddle_apply<float>(h, corr, S->w));
+                    k_axpby<<<nb, tb, 0, h->stream>>>(n, -1.0, S->w, 1.0, S->r);
+                    h->launches += 1;
+                    double rn = 0, bn = 0;
+                    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->r, &rn));
+                    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->t, &bn));
+                    rel = bn > 0 ? rn / bn : 0.0;
+                }
+            }
         }
-        cudaFree(corr);
         FBIM_TRY(st);
     }
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(U, S->d + N2, sizeof(double) * 3 * h->n_b, cudaMemcpyDeviceToDevice,

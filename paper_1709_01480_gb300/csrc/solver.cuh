@@ -33,7 +33,7 @@ struct Solver {
     double* r = nullptr;        // [n]
     double* d = nullptr;        // [n]
     double* t = nullptr;        // [n]
-    double* hcol = nullptr;     // [2 (m+1)] dot products
+    double* hcol = nullptr;     // [2 (m+1) + 1] dot products and the squared norm
     void* zbuf = nullptr;       // [N][2] rotated residual (T)
     void* gbuf = nullptr;       // [N][2] M_ref^+ z (T)
     cublasHandle_t blas = nullptr;
@@ -41,5 +41,13 @@ struct Solver {
     double* lz = nullptr;       // [lanczos_max][2N] Lanczos basis
     double* lh = nullptr;       // [2 lanczos_max] Lanczos dot products / coefficients
     void* blas_ws = nullptr;    // fixed cuBLAS workspace (so captured graphs never allocate)
+    double* corr = nullptr;     // [n] refinement correction
+    // captured operator (precondition then saddle) per precision, [0] FP32 / [1] FP64:
+    // reads gin, writes gz = P gin and gw = A gz; recaptured when the handle's layout changes
+    double *gin = nullptr, *gz = nullptr, *gw = nullptr;
+    cudaGraphExec_t op_graph[2] = {nullptr, nullptr};
+    unsigned long long op_version[2] = {0, 0};
+    long long op_kernels[2] = {0, 0};
+    cudaStream_t cap = nullptr;  // capture origin (the handle's stream may be the legacy default)
     double* rfd = nullptr;      // [2N + 6 * 3 n_b] workspace of the random-finite-difference step
 };

@@ -27,173 +27,157 @@ __device__ __forceinline__ void window_weights(int P, int hw, T f, T a, T scale,
     }
 }
 
-// ---------------------------------------------------------------------------
-// Spread.  One CTA per tile, 8 warps.  Candidates (nodes of the 3 x 3 tile
-// neighbourhood whose window meets this tile) are compacted in chunks into
-// shared memory with their window weights (wy already multiplied by mu).  Warp
-// w owns the rows [w RB, (w+1) RB) of the tile and lane l the columns l and
-// l + 32; each warp accumulates its rows in registers over all candidates and
-// writes them once.  No atomics: the sum over candidates runs in the compacted
-// order, which is deterministic for a given node order.
-// ---------------------------------------------------------------------------
-template <typename T, int PMAX>
-struct SpreadSmem {
-    static constexpr int KMAX = 256;   // one raw chunk of 256 candidates at most
-    int rx[KMAX], ry[KMAX];
-    T wx[KMAX][PMAX];
-    T wmx[KMAX][PMAX];   // wy * mu_x
-    T wmy[KMAX][PMAX];   // wy * mu_y
-    int warp_tot[8];
-    int n_cand;
-};
+__device__ __forceinline__ float acc_exp(float x) { return expf(x); }
+__device__ __forceinline__ double acc_exp(double x) { return exp(x); }
 
+// The PMAX weights e^{-a (j - HW - f)^2}, j = 0..PMAX-1, HW = (PMAX-1)/2, by a
+// two-sided recurrence from the centre: the ratio of neighbours is
+// e^{-a (2 d + 1)} going up and e^{-a (1 - 2 d)} going down (d = j - HW - f), and
+// each ratio is the previous one times q2 = e^{-2a}.  Three exponentials instead
+// of PMAX; the tail weights, which carry the longest product chains, are the
+// smallest.  A window of P < PMAX points uses j in [HW - hw, HW + hw].
 template <typename T, int PMAX>
-__global__ void __launch_bounds__(256) k_spread_tiles(TileGeom tg, T a, T g0, const int* __restrict__ tstart,
+__device__ __forceinline__ void window_recur(T f, T a, T q2, T scale, T* __restrict__ w) {
+    constexpr int HW = (PMAX - 1) / 2;
+    w[HW] = scale * acc_exp(-a * f * f);
+    T r = acc_exp(-a * (T(1) - T(2) * f));
+#pragma unroll
+    for (int j = HW; j < PMAX - 1; ++j) {
+        w[j + 1] = w[j] * r;
+        r *= q2;
+    }
+    r = acc_exp(-a * (T(1) + T(2) * f));
+#pragma unroll
+    for (int j = HW; j > 0; --j) {
+        w[j - 1] = w[j] * r;
+        r *= q2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Spread.  One CTA per tile accumulates the windows of the tile's own nodes
+// (nodes whose nearest grid point lies in the tile) into its extended region of
+// W = TS + 2 hw points per side in shared memory, with shared-memory atomics:
+// a half-warp (a warp when P > 16) takes a node, lane q < P its window row q.
+// The core TS x TS points are then stored straight to the grid (plain stores: no
+// zeroing, no global atomics) and the halo ring to a per-tile buffer; k_spread_fold adds the
+// neighbours' rings to the border bands in a fixed order, so the result does
+// not depend on scheduling.
+// ---------------------------------------------------------------------------
+template <typename T, int PMAX>
+__global__ void __launch_bounds__(256) k_spread_tiles(TileGeom tg, T a, T q2, T g0, const int* __restrict__ tstart,
                                                      const int2* __restrict__ tbase,
                                                      const typename V2<T>::type* __restrict__ tfrac,
                                                      const typename V2<T>::type* __restrict__ mu_t,
-                                                     T* __restrict__ grid) {
+                                                     T* __restrict__ grid, T* __restrict__ ring) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using S = SpreadSmem<T, PMAX>;
-    S& sm = *reinterpret_cast<S*>(smem_raw);
-    constexpr int KMAX = S::KMAX;
-    const int P = tg.P, hw = tg.hw, TS = tg.TS, nt = tg.n_tile;
-    const int tx = blockIdx.x, ty = blockIdx.y;
+    constexpr int HW = (PMAX - 1) / 2;
+    const int P = tg.P, hw = tg.hw, TS = tg.TS, M = tg.M;
+    const int W = TS + 2 * hw, pitch = W | 1, plane = W * pitch;
+    T* acc = reinterpret_cast<T*>(smem_raw);  // [2][W][pitch]
+    const int tx = blockIdx.x, ty = blockIdx.y, tile = ty * tg.n_tile + tx;
+    for (int e = threadIdx.x; e < 2 * plane; e += blockDim.x) acc[e] = T(0);
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int RB = (TS + 7) / 8;
-    const int r0 = warp * RB;
-
-    // the nine neighbour lists, concatenated in a fixed order
-    int lo[9], len[9], total = 0;
+    // a half-warp per node when the window has at most 16 rows, else a warp
+    const bool half = P <= 16;
+    const int per_warp = half ? 2 : 1;
+    const int sub = half ? (lane >> 4) : 0;
+    const int q = half ? (lane & 15) : lane;
+    const int lo = tstart[tile], hi = tstart[tile + 1];
+    const int shift = HW - hw;
+    for (int i = lo + per_warp * warp + sub; i < hi; i += 8 * per_warp) {
+        if (q >= P) continue;
+        const int2 b = tbase[i];
+        const typename V2<T>::type f = tfrac[i];
+        const typename V2<T>::type mu = mu_t[i];
+        T wx[PMAX];
+        window_recur<T, PMAX>(f.x, a, q2, T(1), wx);
+        const T dy = T(q - hw) - f.y;
+        const T wyq = g0 * acc_exp(-a * dy * dy);
+        const T cx = wyq * mu.x, cy = wyq * mu.y;
+        // window origin (b - hw) relative to the extended region's origin (tile - hw)
+        const int base = (b.y - ty * TS + q) * pitch + (b.x - tx * TS) - shift;
 #pragma unroll
-    for (int d = 0; d < 9; ++d) {
-        int nty = ty + d / 3 - 1, ntx = tx + d % 3 - 1;
-        nty += (nty < 0) ? nt : 0;
-        nty -= (nty >= nt) ? nt : 0;
-        ntx += (ntx < 0) ? nt : 0;
-        ntx -= (ntx >= nt) ? nt : 0;
-        int t = nty * nt + ntx;
-        lo[d] = tstart[t];
-        len[d] = tstart[t + 1] - lo[d];
-        total += len[d];
+        for (int j = 0; j < PMAX; ++j) {
+            if (j >= shift && j < shift + P) {
+                atomicAdd(acc + base + j, wx[j] * cx);
+                atomicAdd(acc + plane + base + j, wx[j] * cy);
+            }
+        }
     }
-
-    T acc[2][8][2];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int i = 0; i < 8; ++i) acc[c][i][0] = acc[c][i][1] = T(0);
-
-    for (int base = 0; base < total; base += 256) {
-        // ---- phase 1: test one raw candidate per thread, compact by a block scan ----
-        const int j = base + threadIdx.x;
-        int d = 0, off = j;
-        bool valid = false;
-        int rx = 0, ry = 0, idx = -1;
-        if (j < total) {
-            while (off >= len[d]) {
-                off -= len[d];
-                ++d;
-            }
-            idx = lo[d] + off;
-            const int2 b = tbase[idx];
-            const int dy = d / 3 - 1, dx = d % 3 - 1;
-            int nty = ty + dy, ntx = tx + dx;
-            nty += (nty < 0) ? nt : 0;
-            nty -= (nty >= nt) ? nt : 0;
-            ntx += (ntx < 0) ? nt : 0;
-            ntx -= (ntx >= nt) ? nt : 0;
-            // window origin relative to this tile, in the unwrapped frame of the neighbour
-            rx = b.x - ntx * TS + dx * TS - hw;
-            ry = b.y - nty * TS + dy * TS - hw;
-            valid = !(rx + P <= 0 || rx >= TS || ry + P <= 0 || ry >= TS);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, valid);
-        if (lane == 0) sm.warp_tot[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, n_chunk = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            before += (w < warp) ? sm.warp_tot[w] : 0;
-            n_chunk += sm.warp_tot[w];
-        }
-        if (valid) {
-            const int k = before + __popc(bal & ((1u << lane) - 1u));
-            sm.rx[k] = rx;
-            sm.ry[k] = ry;
-            const typename V2<T>::type f = tfrac[idx];
-            const typename V2<T>::type mu = mu_t[idx];
-            T w[PMAX];
-            window_weights<T, PMAX>(P, hw, f.x, a, T(1), w);
-#pragma unroll
-            for (int p = 0; p < PMAX; ++p) sm.wx[k][p] = w[p];
-            window_weights<T, PMAX>(P, hw, f.y, a, g0, w);
-#pragma unroll
-            for (int p = 0; p < PMAX; ++p) {
-                sm.wmx[k][p] = w[p] * mu.x;
-                sm.wmy[k][p] = w[p] * mu.y;
-            }
-        }
-        __syncthreads();
-        // ---- phase 2: every warp accumulates its rows over the chunk ----
-        for (int k = 0; k < n_chunk; ++k) {
-            const int cy = sm.ry[k];
-            if (cy >= r0 + RB || cy + P <= r0) continue;  // warp-uniform
-            const int cx = sm.rx[k];
-            const int p0 = lane - cx, p1 = lane + 32 - cx;
-            const T wx0 = (p0 >= 0 && p0 < P) ? sm.wx[k][p0] : T(0);
-            const T wx1 = (p1 >= 0 && p1 < P) ? sm.wx[k][p1] : T(0);
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int q = r0 + i - cy;
-                if (i < RB && q >= 0 && q < P) {
-                    const T fx = sm.wmx[k][q], fy = sm.wmy[k][q];
-                    acc[0][i][0] = fma(wx0, fx, acc[0][i][0]);
-                    acc[0][i][1] = fma(wx1, fx, acc[0][i][1]);
-                    acc[1][i][0] = fma(wx0, fy, acc[1][i][0]);
-                    acc[1][i][1] = fma(wx1, fy, acc[1][i][1]);
-                }
-            }
-        }
-        __syncthreads();
+    __syncthreads();
+    const size_t MM = (size_t)M * M;
+    for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+        const int ly = e / TS, lx = e - ly * TS;
+        const size_t g = (size_t)(ty * TS + ly) * M + tx * TS + lx;
+        const int s = (ly + hw) * pitch + lx + hw;
+        grid[g] = acc[s];
+        grid[MM + g] = acc[plane + s];
     }
-    const size_t MM = (size_t)tg.M * tg.M;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int r = r0 + i;
-        if (i >= RB || r >= TS) continue;
-        const size_t row = (size_t)(ty * TS + r) * tg.M + tx * TS;
-        if (lane < TS) {
-            grid[row + lane] = acc[0][i][0];
-            grid[MM + row + lane] = acc[1][i][0];
-        }
-        if (lane + 32 < TS) {
-            grid[row + lane + 32] = acc[0][i][1];
-            grid[MM + row + lane + 32] = acc[1][i][1];
-        }
+    T* rt = ring + (size_t)tile * 2 * W * W;
+    for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
+        const int ey = e / W, ex = e - ey * W;
+        if (ey >= hw && ey < TS + hw && ex >= hw && ex < TS + hw) continue;
+        rt[e] = acc[ey * pitch + ex];
+        rt[W * W + e] = acc[plane + ey * pitch + ex];
+    }
+}
+
+// Border bands of each tile: add the neighbours' halo rings (fixed neighbour order).
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_fold(TileGeom tg, const T* __restrict__ ring, T* __restrict__ grid) {
+    const int hw = tg.hw, TS = tg.TS, M = tg.M, nt = tg.n_tile;
+    const int W = TS + 2 * hw;
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    const size_t MM = (size_t)M * M;
+    for (int e = threadIdx.x; e < TS * TS; e += blockDim.x) {
+        const int ly = e / TS, lx = e - ly * TS;
+        if (ly >= hw && ly < TS - hw && lx >= hw && lx < TS - hw) continue;
+        T sx = T(0), sy = T(0);
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                const int ex = lx - dx * TS + hw, ey = ly - dy * TS + hw;
+                if (ex < 0 || ex >= W || ey < 0 || ey >= W) continue;
+                int ntx = tx + dx, nty = ty + dy;
+                ntx += (ntx < 0) ? nt : 0;
+                ntx -= (ntx >= nt) ? nt : 0;
+                nty += (nty < 0) ? nt : 0;
+                nty -= (nty >= nt) ? nt : 0;
+                const T* rt = ring + (size_t)(nty * nt + ntx) * 2 * W * W;
+                sx += rt[ey * W + ex];
+                sy += rt[W * W + ey * W + ex];
+            }
+        const size_t g = (size_t)(ty * TS + ly) * M + tx * TS + lx;
+        grid[g] += sx;
+        grid[MM + g] += sy;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Interpolation: v_t = sum_{P x P} g(x_t - y) U(y) (the h^2 weight is in k_scale).
 // One CTA per tile loads the tile and a halo of hw points (periodic) into shared
-// memory with an odd row pitch; then each half-warp handles one node (lane q =
-// window row q; P <= 16), or each warp one node when P > 16.  Rows are reduced
-// across the lanes with shuffles.
+// memory as interleaved (x, y) pairs with an odd row pitch; then each half-warp
+// handles one node (lane q = window row q, one 8-byte load per point; P <= 16),
+// or each warp one node when P > 16.  Rows are reduced across the lanes with
+// shuffles.
 // ---------------------------------------------------------------------------
 template <typename T>
 __host__ __device__ inline int interp_pitch(int W) { return W | 1; }
 
 template <typename T, int PMAX>
-__global__ void __launch_bounds__(256) k_interp_tiles(TileGeom tg, T a, T g0, const int* __restrict__ tstart,
+__global__ void __launch_bounds__(256) k_interp_tiles(TileGeom tg, T a, T q2, T g0, const int* __restrict__ tstart,
                                                      const int2* __restrict__ tbase,
                                                      const typename V2<T>::type* __restrict__ tfrac,
                                                      const T* __restrict__ grid,
                                                      typename V2<T>::type* __restrict__ v_t) {
+    using T2 = typename V2<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int HW = (PMAX - 1) / 2;
     const int P = tg.P, hw = tg.hw, TS = tg.TS, M = tg.M;
-    const int W = TS + 2 * hw, pitch = interp_pitch<T>(W), plane = W * pitch;
-    T* sg = reinterpret_cast<T*>(smem_raw);  // [2][W][pitch]
+    const int W = TS + 2 * hw, pitch = interp_pitch<T>(W);
+    T2* sg = reinterpret_cast<T2*>(smem_raw);  // [W][pitch] of (x, y)
     const int tx = blockIdx.x, ty = blockIdx.y;
     const int x0 = tx * TS - hw, y0 = ty * TS - hw;
     const size_t MM = (size_t)M * M;
@@ -208,8 +192,10 @@ __global__ void __launch_bounds__(256) k_interp_tiles(TileGeom tg, T a, T g0, co
             int gx = x0 + ix;
             gx += (gx < 0) ? M : 0;
             gx -= (gx >= M) ? M : 0;
-            sg[iy * pitch + ix] = srcx[gx];
-            sg[plane + iy * pitch + ix] = srcy[gx];
+            T2 u;
+            u.x = srcx[gx];
+            u.y = srcy[gx];
+            sg[iy * pitch + ix] = u;
         }
     }
     __syncthreads();
@@ -219,27 +205,26 @@ __global__ void __launch_bounds__(256) k_interp_tiles(TileGeom tg, T a, T g0, co
     const int per_warp = half ? 2 : 1;
     const int sub = half ? (lane >> 4) : 0;
     const int q = half ? (lane & 15) : lane;
-    const unsigned group = half ? (0xffffu << (16 * sub)) : 0xffffffffu;
+    const int shift = HW - hw;
     for (int i0 = lo + warp * per_warp; i0 < hi; i0 += 8 * per_warp) {
         const int i = i0 + sub;
         const bool have = i < hi;
         T ax = 0, ay = 0;
         if (have && q < P) {
             const int2 b = tbase[i];
-            const int rx = b.x - tx * TS, ry = b.y - ty * TS;  // window origin (rx, ry) in sg
             const typename V2<T>::type f = tfrac[i];
             T wx[PMAX];
-            window_weights<T, PMAX>(P, hw, f.x, a, T(1), wx);
+            window_recur<T, PMAX>(f.x, a, q2, T(1), wx);
             const T dyq = T(q - hw) - f.y;
-            const T wyq = g0 * dev_exp(-a * dyq * dyq);
-            const T* rowx = sg + (ry + q) * pitch + rx;
-            const T* rowy = rowx + plane;
+            const T wyq = g0 * acc_exp(-a * dyq * dyq);
+            const int base = (b.y - ty * TS + q) * pitch + (b.x - tx * TS) - shift;
             T sx = 0, sy = 0;
 #pragma unroll
-            for (int p = 0; p < PMAX; ++p) {
-                if (p < P) {
-                    sx = fma(wx[p], rowx[p], sx);
-                    sy = fma(wx[p], rowy[p], sy);
+            for (int j = 0; j < PMAX; ++j) {
+                if (j >= shift && j < shift + P) {
+                    const T2 u = sg[base + j];
+                    sx = fma(wx[j], u.x, sx);
+                    sy = fma(wx[j], u.y, sy);
                 }
             }
             ax = wyq * sx;
@@ -250,7 +235,6 @@ __global__ void __launch_bounds__(256) k_interp_tiles(TileGeom tg, T a, T g0, co
             ax += __shfl_xor_sync(0xffffffffu, ax, o, width);
             ay += __shfl_xor_sync(0xffffffffu, ay, o, width);
         }
-        (void)group;
         if (have && q == 0) {
             v_t[i].x = ax;
             v_t[i].y = ay;
@@ -260,98 +244,119 @@ __global__ void __launch_bounds__(256) k_interp_tiles(TileGeom tg, T a, T g0, co
 
 
 // ---------------------------------------------------------------------------
-// Warp-per-node variants.  A warp takes one node (tile-sorted order keeps
-// consecutive warps on neighbouring grid regions); lane p < P computes the p-th
-// weight of each dimension, and the P x P window is walked row-major, 32 points
-// per step, so that each step touches a few short contiguous row segments.
+// Warp variants.  Lane p of a node's lane group owns window column p; the window
+// rows are walked in a loop, so every step touches one contiguous row segment of
+// P points per node (coalesced), and the row weights come from the lane that owns
+// them by a shuffle.  Two nodes share a warp when P <= 16 (lanes 0-15, 16-31).
 // Spreading reduces into the grid with fire-and-forget global atomic adds (the
-// grid stays in L2); interpolation gathers the same segments and reduces over
-// the warp.
+// grid stays in L2); interpolation accumulates column sums, weights them by the
+// column weights and reduces over the lane group.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread_warp(int N, int M, int P, int hw, float invP, T a, T g0,
+__global__ void __launch_bounds__(256) k_spread_warp(int N, int M, int P, int hw, T a, T g0,
                                                     const int2* __restrict__ tbase,
                                                     const typename V2<T>::type* __restrict__ tfrac,
                                                     const typename V2<T>::type* __restrict__ mu_t,
                                                     T* __restrict__ grid) {
     const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= N) return;  // warp-uniform
-    const int2 b = tbase[i];
-    const typename V2<T>::type f = tfrac[i];
-    const typename V2<T>::type mu = mu_t[i];
-    const T dx = T(lane - hw) - f.x, dy = T(lane - hw) - f.y;
-    const T wx = dev_exp(-a * dx * dx);
-    const T wy = g0 * dev_exp(-a * dy * dy);
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const bool two = P <= 16;
+    const int sub = two ? (lane >> 4) : 0, p = two ? (lane & 15) : lane;
+    const int i = w * (two ? 2 : 1) + sub;
+    if (w * (two ? 2 : 1) >= N) return;  // warp-uniform
+    const bool active = i < N && p < P;
+    int2 b = make_int2(0, 0);
+    typename V2<T>::type f = {T(0), T(0)}, mu = {T(0), T(0)};
+    if (active) {
+        b = tbase[i];
+        f = tfrac[i];
+        mu = mu_t[i];
+    }
+    const T dx = T(p - hw) - f.x, dy = T(p - hw) - f.y;
+    const T wx = active ? acc_exp(-a * dx * dx) : T(0);
+    const T wy = active ? g0 * acc_exp(-a * dy * dy) : T(0);  // row weight of row p
+    const T cx = wx * mu.x, cy = wx * mu.y;
+    int gx = b.x - hw + p;
+    gx += (gx < 0) ? M : 0;
+    gx -= (gx >= M) ? M : 0;
+    int gy = b.y - hw;
+    gy += (gy < 0) ? M : 0;
     const size_t MM = (size_t)M * M;
-    const int PP = P * P;
-    for (int k0 = 0; k0 < PP; k0 += 32) {
-        const int k = k0 + lane;
-        int q = (int)(((float)k + 0.5f) * invP);
-        int p = k - q * P;
-        const bool ok = k < PP;
-        if (!ok) p = q = 0;
-        const T w = __shfl_sync(0xffffffffu, wx, p) * __shfl_sync(0xffffffffu, wy, q);
-        if (ok) {
-            int gx = b.x + p - hw, gy = b.y + q - hw;
-            gx += (gx < 0) ? M : 0;
-            gx -= (gx >= M) ? M : 0;
-            gy += (gy < 0) ? M : 0;
-            gy -= (gy >= M) ? M : 0;
+    const int src = two ? (sub << 4) : 0;
+    for (int q = 0; q < P; ++q) {
+        const T wq = __shfl_sync(0xffffffffu, wy, src + q);
+        if (active) {
             const size_t g = (size_t)gy * M + gx;
-            atomicAdd(grid + g, w * mu.x);
-            atomicAdd(grid + MM + g, w * mu.y);
+            atomicAdd(grid + g, wq * cx);
+            atomicAdd(grid + MM + g, wq * cy);
         }
+        gy = (gy + 1 == M) ? 0 : gy + 1;
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_interp_warp(int N, int M, int P, int hw, float invP, T a, T g0,
+__global__ void __launch_bounds__(256) k_interp_warp(int N, int M, int P, int hw, T a, T g0,
                                                     const int2* __restrict__ tbase,
                                                     const typename V2<T>::type* __restrict__ tfrac,
                                                     const T* __restrict__ grid,
                                                     typename V2<T>::type* __restrict__ v_t) {
     const int lane = threadIdx.x & 31;
-    const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= N) return;  // warp-uniform
-    const int2 b = tbase[i];
-    const typename V2<T>::type f = tfrac[i];
-    const T dx = T(lane - hw) - f.x, dy = T(lane - hw) - f.y;
-    const T wx = dev_exp(-a * dx * dx);
-    const T wy = g0 * dev_exp(-a * dy * dy);
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const bool two = P <= 16;
+    const int sub = two ? (lane >> 4) : 0, p = two ? (lane & 15) : lane;
+    const int i = w * (two ? 2 : 1) + sub;
+    if (w * (two ? 2 : 1) >= N) return;  // warp-uniform
+    const bool active = i < N && p < P;
+    int2 b = make_int2(0, 0);
+    typename V2<T>::type f = {T(0), T(0)};
+    if (active) {
+        b = tbase[i];
+        f = tfrac[i];
+    }
+    const T dx = T(p - hw) - f.x, dy = T(p - hw) - f.y;
+    const T wx = active ? acc_exp(-a * dx * dx) : T(0);
+    const T wy = active ? g0 * acc_exp(-a * dy * dy) : T(0);
+    int gx = b.x - hw + p;
+    gx += (gx < 0) ? M : 0;
+    gx -= (gx >= M) ? M : 0;
+    int gy = b.y - hw;
+    gy += (gy < 0) ? M : 0;
     const size_t MM = (size_t)M * M;
-    const int PP = P * P;
-    T ax = 0, ay = 0;
-    for (int k0 = 0; k0 < PP; k0 += 32) {
-        const int k = k0 + lane;
-        int q = (int)(((float)k + 0.5f) * invP);
-        int p = k - q * P;
-        const bool ok = k < PP;
-        if (!ok) p = q = 0;
-        const T w = __shfl_sync(0xffffffffu, wx, p) * __shfl_sync(0xffffffffu, wy, q);
-        if (ok) {
-            int gx = b.x + p - hw, gy = b.y + q - hw;
-            gx += (gx < 0) ? M : 0;
-            gx -= (gx >= M) ? M : 0;
-            gy += (gy < 0) ? M : 0;
-            gy -= (gy >= M) ? M : 0;
+    const int src = two ? (sub << 4) : 0;
+    T sx = 0, sy = 0;
+    for (int q = 0; q < P; ++q) {
+        const T wq = __shfl_sync(0xffffffffu, wy, src + q);
+        if (active) {
             const size_t g = (size_t)gy * M + gx;
-            ax = fma(w, __ldg(grid + g), ax);
-            ay = fma(w, __ldg(grid + MM + g), ay);
+            sx = fma(wq, __ldg(grid + g), sx);
+            sy = fma(wq, __ldg(grid + MM + g), sy);
         }
+        gy = (gy + 1 == M) ? 0 : gy + 1;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        ax += __shfl_xor_sync(0xffffffffu, ax, o);
-        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    sx *= wx;
+    sy *= wx;
+    const int width = two ? 16 : 32;
+    for (int o = width / 2; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o, width);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o, width);
     }
-    if (lane == 0) {
-        v_t[i].x = ax;
-        v_t[i].y = ay;
+    if (p == 0 && i < N) {
+        v_t[i].x = sx;
+        v_t[i].y = sy;
     }
 }
 
-template <typename T, int PMAX>
-inline size_t spread_smem_bytes() { return sizeof(SpreadSmem<T, PMAX>); }
+template <typename T>
+inline size_t spread_smem_bytes(int TS, int P) {
+    const int W = TS + (P - 1), pitch = W | 1;
+    return 2 * (size_t)W * pitch * sizeof(T);
+}
+
+// per-tile halo rings of the spread: [n_tile^2][2][W][W]
+inline size_t spread_ring_elems(int TS, int P, int n_tile) {
+    const size_t W = TS + (P - 1);
+    return (size_t)n_tile * n_tile * 2 * W * W;
+}
 
 template <typename T>
 inline size_t interp_smem_bytes(int TS, int P) {

@@ -1,4 +1,6 @@
 // Wave-space tile kernels instantiated for float.
+#include <cmath>
+
 #include "wave_tiles.cuh"
 
 namespace fbim {
@@ -11,12 +13,12 @@ static int pmax_for(int P) { return P <= 9 ? 9 : P <= 13 ? 13 : P <= 17 ? 17 : P
 template <>
 cudaError_t tile_set_smem<float>(const TileGeom& tg) {
     cudaError_t err = cudaErrorInvalidValue;
+    const int ss = (int)spread_smem_bytes<float>(tg.TS, tg.P);
     const int si = (int)interp_smem_bytes<float>(tg.TS, tg.P);
     switch (pmax_for(tg.P)) {
 #define FBIM_SET(PM)                                                                                        \
     case PM:                                                                                                \
-        err = cudaFuncSetAttribute(k_spread_tiles<float, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                   (int)spread_smem_bytes<float, PM>());                                      \
+        err = cudaFuncSetAttribute(k_spread_tiles<float, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss); \
         if (err == cudaSuccess)                                                                             \
             err = cudaFuncSetAttribute(k_interp_tiles<float, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, si); \
         break;
@@ -28,18 +30,21 @@ cudaError_t tile_set_smem<float>(const TileGeom& tg) {
 
 template <>
 void tile_spread<float>(cudaStream_t st, const TileGeom& tg, float a, float g0, const int* tstart, const int2* tbase,
-                      const void* tfrac, const void* mu_t, float* grid) {
+                      const void* tfrac, const void* mu_t, float* grid, float* ring) {
     using T2 = typename V2<float>::type;
     const dim3 tiles(tg.n_tile, tg.n_tile);
+    const size_t ss = spread_smem_bytes<float>(tg.TS, tg.P);
+    const float q2 = (float)std::exp(-2.0 * (double)a);
     switch (pmax_for(tg.P)) {
 #define FBIM_LAUNCH(PM)                                                                                   \
     case PM:                                                                                              \
-        k_spread_tiles<float, PM><<<tiles, 256, spread_smem_bytes<float, PM>(), st>>>(                        \
-            tg, a, g0, tstart, tbase, (const T2*)tfrac, (const T2*)mu_t, grid);                           \
+        k_spread_tiles<float, PM><<<tiles, 256, ss, st>>>(tg, a, q2, g0, tstart, tbase, (const T2*)tfrac,      \
+                                                        (const T2*)mu_t, grid, ring);                     \
         break;
         FBIM_PMAX_CASES(FBIM_LAUNCH)
 #undef FBIM_LAUNCH
     }
+    k_spread_fold<float><<<tiles, 256, 0, st>>>(tg, ring, grid);
 }
 
 template <>
@@ -48,10 +53,11 @@ void tile_interp<float>(cudaStream_t st, const TileGeom& tg, float a, float g0, 
     using T2 = typename V2<float>::type;
     const dim3 tiles(tg.n_tile, tg.n_tile);
     const size_t si = interp_smem_bytes<float>(tg.TS, tg.P);
+    const float q2 = (float)std::exp(-2.0 * (double)a);
     switch (pmax_for(tg.P)) {
 #define FBIM_LAUNCH(PM)                                                                                   \
     case PM:                                                                                              \
-        k_interp_tiles<float, PM><<<tiles, 256, si, st>>>(tg, a, g0, tstart, tbase, (const T2*)tfrac, grid,   \
+        k_interp_tiles<float, PM><<<tiles, 256, si, st>>>(tg, a, q2, g0, tstart, tbase, (const T2*)tfrac, grid,  \
                                                         (T2*)v_t);                                        \
         break;
         FBIM_PMAX_CASES(FBIM_LAUNCH)
@@ -59,22 +65,25 @@ void tile_interp<float>(cudaStream_t st, const TileGeom& tg, float a, float g0, 
     }
 }
 
+static int warp_blocks(int N, int P) {
+    const long long warps = P <= 16 ? (N + 1) / 2 : N;
+    return (int)((warps * 32 + 255) / 256);
+}
+
 template <>
 void warp_spread<float>(cudaStream_t st, int N, const TileGeom& tg, float a, float g0, const int2* tbase,
                       const void* tfrac, const void* mu_t, float* grid) {
     using T2 = typename V2<float>::type;
-    const int blocks = (int)(((long long)N * 32 + 255) / 256);
-    k_spread_warp<float><<<blocks, 256, 0, st>>>(N, tg.M, tg.P, tg.hw, 1.0f / (float)tg.P, a, g0, tbase,
-                                               (const T2*)tfrac, (const T2*)mu_t, grid);
+    k_spread_warp<float><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
+                                                            (const T2*)mu_t, grid);
 }
 
 template <>
 void warp_interp<float>(cudaStream_t st, int N, const TileGeom& tg, float a, float g0, const int2* tbase,
                       const void* tfrac, const float* grid, void* v_t) {
     using T2 = typename V2<float>::type;
-    const int blocks = (int)(((long long)N * 32 + 255) / 256);
-    k_interp_warp<float><<<blocks, 256, 0, st>>>(N, tg.M, tg.P, tg.hw, 1.0f / (float)tg.P, a, g0, tbase,
-                                               (const T2*)tfrac, grid, (T2*)v_t);
+    k_interp_warp<float><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
+                                                            grid, (T2*)v_t);
 }
 
 }  // namespace fbim

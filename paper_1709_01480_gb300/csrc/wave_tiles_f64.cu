@@ -1,4 +1,6 @@
 // Wave-space tile kernels instantiated for double.
+#include <cmath>
+
 #include "wave_tiles.cuh"
 
 namespace fbim {
@@ -11,12 +13,12 @@ static int pmax_for(int P) { return P <= 9 ? 9 : P <= 13 ? 13 : P <= 17 ? 17 : P
 template <>
 cudaError_t tile_set_smem<double>(const TileGeom& tg) {
     cudaError_t err = cudaErrorInvalidValue;
+    const int ss = (int)spread_smem_bytes<double>(tg.TS, tg.P);
     const int si = (int)interp_smem_bytes<double>(tg.TS, tg.P);
     switch (pmax_for(tg.P)) {
 #define FBIM_SET(PM)                                                                                        \
     case PM:                                                                                                \
-        err = cudaFuncSetAttribute(k_spread_tiles<double, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                   (int)spread_smem_bytes<double, PM>());                                      \
+        err = cudaFuncSetAttribute(k_spread_tiles<double, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss); \
         if (err == cudaSuccess)                                                                             \
             err = cudaFuncSetAttribute(k_interp_tiles<double, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, si); \
         break;
@@ -28,18 +30,21 @@ cudaError_t tile_set_smem<double>(const TileGeom& tg) {
 
 template <>
 void tile_spread<double>(cudaStream_t st, const TileGeom& tg, double a, double g0, const int* tstart, const int2* tbase,
-                      const void* tfrac, const void* mu_t, double* grid) {
+                      const void* tfrac, const void* mu_t, double* grid, double* ring) {
     using T2 = typename V2<double>::type;
     const dim3 tiles(tg.n_tile, tg.n_tile);
+    const size_t ss = spread_smem_bytes<double>(tg.TS, tg.P);
+    const double q2 = (double)std::exp(-2.0 * (double)a);
     switch (pmax_for(tg.P)) {
 #define FBIM_LAUNCH(PM)                                                                                   \
     case PM:                                                                                              \
-        k_spread_tiles<double, PM><<<tiles, 256, spread_smem_bytes<double, PM>(), st>>>(                        \
-            tg, a, g0, tstart, tbase, (const T2*)tfrac, (const T2*)mu_t, grid);                           \
+        k_spread_tiles<double, PM><<<tiles, 256, ss, st>>>(tg, a, q2, g0, tstart, tbase, (const T2*)tfrac,      \
+                                                        (const T2*)mu_t, grid, ring);                     \
         break;
         FBIM_PMAX_CASES(FBIM_LAUNCH)
 #undef FBIM_LAUNCH
     }
+    k_spread_fold<double><<<tiles, 256, 0, st>>>(tg, ring, grid);
 }
 
 template <>
@@ -48,10 +53,11 @@ void tile_interp<double>(cudaStream_t st, const TileGeom& tg, double a, double g
     using T2 = typename V2<double>::type;
     const dim3 tiles(tg.n_tile, tg.n_tile);
     const size_t si = interp_smem_bytes<double>(tg.TS, tg.P);
+    const double q2 = (double)std::exp(-2.0 * (double)a);
     switch (pmax_for(tg.P)) {
 #define FBIM_LAUNCH(PM)                                                                                   \
     case PM:                                                                                              \
-        k_interp_tiles<double, PM><<<tiles, 256, si, st>>>(tg, a, g0, tstart, tbase, (const T2*)tfrac, grid,   \
+        k_interp_tiles<double, PM><<<tiles, 256, si, st>>>(tg, a, q2, g0, tstart, tbase, (const T2*)tfrac, grid,  \
                                                         (T2*)v_t);                                        \
         break;
         FBIM_PMAX_CASES(FBIM_LAUNCH)
@@ -59,22 +65,25 @@ void tile_interp<double>(cudaStream_t st, const TileGeom& tg, double a, double g
     }
 }
 
+static int warp_blocks(int N, int P) {
+    const long long warps = P <= 16 ? (N + 1) / 2 : N;
+    return (int)((warps * 32 + 255) / 256);
+}
+
 template <>
 void warp_spread<double>(cudaStream_t st, int N, const TileGeom& tg, double a, double g0, const int2* tbase,
                       const void* tfrac, const void* mu_t, double* grid) {
     using T2 = typename V2<double>::type;
-    const int blocks = (int)(((long long)N * 32 + 255) / 256);
-    k_spread_warp<double><<<blocks, 256, 0, st>>>(N, tg.M, tg.P, tg.hw, 1.0f / (float)tg.P, a, g0, tbase,
-                                               (const T2*)tfrac, (const T2*)mu_t, grid);
+    k_spread_warp<double><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
+                                                            (const T2*)mu_t, grid);
 }
 
 template <>
 void warp_interp<double>(cudaStream_t st, int N, const TileGeom& tg, double a, double g0, const int2* tbase,
                       const void* tfrac, const double* grid, void* v_t) {
     using T2 = typename V2<double>::type;
-    const int blocks = (int)(((long long)N * 32 + 255) / 256);
-    k_interp_warp<double><<<blocks, 256, 0, st>>>(N, tg.M, tg.P, tg.hw, 1.0f / (float)tg.P, a, g0, tbase,
-                                               (const T2*)tfrac, grid, (T2*)v_t);
+    k_interp_warp<double><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
+                                                            grid, (T2*)v_t);
 }
 
 }  // namespace fbim
