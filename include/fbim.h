@@ -324,6 +324,13 @@ fbim_status fbim_coarse_stats(fbim_handle h, int* n_pairs, int* n_rejected);
  * serialised by the caller.  mu_dev, v_dev: double [N][2], 16-byte aligned. */
 fbim_status fbim_apply_real_noalloc(fbim_handle h, const double* mu_dev, double* v_dev);
 
+/* v = M mu with the handle's FP64 operator whatever its precision: the operator of the
+ * FP64 refinement residuals (Sec. 3.2 as fbim_apply_stokeslet).  On an FBIM_FP32 handle
+ * its real-space kernel values come from the FP32 pair list's pairs, evaluated in
+ * float-float arithmetic (about 1e-13 relative); on an FBIM_FP64 handle this is
+ * fbim_apply_stokeslet. */
+fbim_status fbim_apply_stokeslet_fp64(fbim_handle h, const double* mu_dev, double* v_dev);
+
 /* Information about the handle's parameters. */
 fbim_status fbim_get_info(fbim_handle h, fbim_info* info);
 

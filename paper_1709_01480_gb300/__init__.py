@@ -41,7 +41,7 @@ EXPORTS = [
     "fbim_mlp_param_count", "fbim_mlp_create", "fbim_mlp_destroy", "fbim_mlp_last_error",
     "fbim_mlp_set_params", "fbim_mlp_get_params", "fbim_mlp_set_normalization", "fbim_mlp_forward",
     "fbim_mlp_gradient", "fbim_mlp_adam_step", "fbim_mlp_launches", "fbim_coarse_pairs",
-    "fbim_coarse_enable", "fbim_coarse_stats",
+    "fbim_coarse_enable", "fbim_coarse_stats", "fbim_apply_stokeslet_fp64",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -103,6 +103,7 @@ _lib.fbim_apply_stokeslet.argtypes = [_P, _P, _P]
 _lib.fbim_apply_real.argtypes = [_P, _P, _P]
 _lib.fbim_apply_wave.argtypes = [_P, _P, _P]
 _lib.fbim_apply_real_noalloc.argtypes = [_P, _P, _P]
+_lib.fbim_apply_stokeslet_fp64.argtypes = [_P, _P, _P]
 _lib.fbim_rfd_step.argtypes = [_P, _P, _D, _D, _D, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P, _D, _I, _P, _IP]
 _lib.fbim_get_info.argtypes = [_P, ctypes.POINTER(Info)]
 _lib.fbim_destroy.argtypes = [_P]
@@ -237,6 +238,12 @@ class FBIM:
     def apply_stokeslet(self, mu, out=None):
         v = out if out is not None else self._out(mu, (self.n, 2))
         _check(_lib.fbim_apply_stokeslet(self._h, _ptr(mu), _ptr(v)), self._h)
+        return v
+
+    def apply_stokeslet_fp64(self, mu, out=None):
+        """The FP64 operator of the refinement residuals (FP64 whatever the handle's precision)."""
+        v = out if out is not None else self._out(mu, (self.n, 2))
+        _check(_lib.fbim_apply_stokeslet_fp64(self._h, _ptr(mu), _ptr(v)), self._h)
         return v
 
     def apply_real(self, mu, out=None):

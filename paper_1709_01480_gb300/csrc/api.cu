@@ -1,4 +1,5 @@
 // C ABI entry points: handle life cycle and the Ewald operators.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -208,15 +209,26 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         // Chebyshev series of the smooth part of E1 on [0, xi^2 r_c^2]
         h->zmax = h->xi * h->xi * h->r_c * h->r_c * (1.0 + 1e-6);
         {
-            std::vector<double> c64, c32;
-            fbim::e1_chebyshev(h->zmax, 44, c64);
-            fbim::e1_chebyshev(h->zmax, 30, c32);
-            h->cheb64.deg = 44;
+            // one interpolant of degree kChebMax - 1, truncated per precision where its
+            // coefficients fall below 1e-15 (FP64) or 1e-8 (FP32) of the largest: the
+            // truncation error then sits below each precision's rounding
+            std::vector<double> c;
+            const int dmax = fbim::kChebMax - 1;
+            fbim::e1_chebyshev(h->zmax, dmax, c);
+            double cmax = 0;
+            for (double v : c) cmax = std::max(cmax, std::fabs(v));
+            auto degree = [&](double rel) {
+                int d = dmax;
+                while (d > 4 && std::fabs(c[d]) < rel * cmax) --d;
+                return std::min(dmax, d + 1);
+            };
+            const int d64 = degree(1e-15), d32 = degree(1e-8);
+            h->cheb64.deg = d64;
             h->cheb64.scale = 2.0 / h->zmax;
-            for (int k = 0; k <= 44; ++k) h->cheb64.c[k] = c64[k];
-            h->cheb32.deg = 30;
+            for (int k = 0; k <= d64; ++k) h->cheb64.c[k] = c[k];
+            h->cheb32.deg = d32;
             h->cheb32.scale = (float)(2.0 / h->zmax);
-            for (int k = 0; k <= 30; ++k) h->cheb32.c[k] = (float)c32[k];
+            for (int k = 0; k <= d32; ++k) h->cheb32.c[k] = (float)c[k];
         }
         const size_t N = h->N, nc = (size_t)h->n_cell();
         FBIM_CUDA_TRY(h, cudaMalloc(&h->ref, 2 * n_p * sizeof(double)));
@@ -265,7 +277,7 @@ extern "C" fbim_status fbim_update_config(fbim_handle h, const double* Q_dev) {
     });
 }
 
-static fbim_status apply_which(fbim_handle h, const double* mu, double* v, int which) {
+static fbim_status apply_which(fbim_handle h, const double* mu, double* v, int which, bool fp64 = false) {
     if (!h || !mu || !v) return FBIM_ERR_INVALID_ARG;
     if ((((uintptr_t)mu) | ((uintptr_t)v)) & 15) {
         h->fail("mu and v must be 16-byte aligned");
@@ -273,9 +285,13 @@ static fbim_status apply_which(fbim_handle h, const double* mu, double* v, int w
     }
     return guarded(h, [&]() -> fbim_status {
         FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
-        if (h->precision == FBIM_FP32) return fbim::apply_operator<float>(h, mu, v, which);
+        if (h->precision == FBIM_FP32 && !fp64) return fbim::apply_operator<float>(h, mu, v, which);
         return fbim::apply_operator<double>(h, mu, v, which);
     });
+}
+
+extern "C" fbim_status fbim_apply_stokeslet_fp64(fbim_handle h, const double* mu_dev, double* v_dev) {
+    return apply_which(h, mu_dev, v_dev, 3, true);
 }
 
 extern "C" fbim_status fbim_apply_stokeslet(fbim_handle h, const double* mu_dev, double* v_dev) {

@@ -27,6 +27,9 @@
 // Templated on the operator precision T (double: parity path; float: fast path).
 #include <cmath>
 
+#include <type_traits>
+
+#include "dfloat.cuh"
 #include "fbim_internal.h"
 #include "ewald_types.cuh"
 
@@ -148,25 +151,81 @@ __global__ void __launch_bounds__(128) k_pair_fill(int N, int n_box, T r_c, T rc
     }
 }
 
-// Pass 3: turn every stored separation into the kernel G^(r)(r) / (4 pi eta) in
-// place.  One thread per entry, so the transcendental work runs without the
-// divergence of the neighbour search (which matters most for FP64).
+// The kernel G^(r)(r) / (4 pi eta) for separation (rx, ry): (a + b r r^T) with
+// a = E1(z)/2 - e^{-z} (Chebyshev series of its entire part minus ln(z)/2) and
+// b = e^{-z} / r^2, z = xi^2 r^2.
 template <typename T>
-__global__ void __launch_bounds__(256) k_pair_eval(size_t n_entries, T xi2, T pref, ChebE1<T> ce,
-                                                  PairEntry<T>* __restrict__ pairs) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_entries) return;
-    PairEntry<T> e = pairs[i];
-    const T rx = e.xx, ry = e.xy;
+__device__ __forceinline__ void pair_value(T rx, T ry, T xi2, T pref, const ChebE1<T>& ce, T& xx, T& xy, T& yy) {
     const T r2 = rx * rx + ry * ry;
-    if (r2 == T(0)) return;  // padding
     const T z = xi2 * r2;
     const T a = kernel_a<T>(ce, z);
     const T b = dev_div(dev_exp(-z), r2);
-    e.xx = pref * (a + b * rx * rx);
-    e.xy = pref * (b * rx * ry);
-    e.yy = pref * (a + b * ry * ry);
-    pairs[i] = e;
+    xx = pref * (a + b * rx * rx);
+    xy = pref * (b * rx * ry);
+    yy = pref * (a + b * ry * ry);
+}
+
+// Pass 3: turn every stored separation into the kernel value in place.  One warp
+// per target row, lane k on the row's k-th pair: only real pairs are evaluated, so
+// the sliced-ELL padding idles no lane of the transcendental work.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pair_eval_rows(int N, const int* __restrict__ slice_start,
+                                                       const int* __restrict__ row_count, T xi2, T pref,
+                                                       ChebE1<T> ce, PairEntry<T>* __restrict__ pairs) {
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (t >= N) return;
+    const int n = row_count[t];
+    PairEntry<T>* row = pairs + (size_t)slice_start[t >> 5] * 32 + (t & 31);
+    for (int k = lane; k < n; k += 32) {
+        PairEntry<T> e = row[(size_t)k * 32];
+        T xx, xy, yy;
+        pair_value<T>(e.xx, e.xy, xi2, pref, ce, xx, xy, yy);
+        e.xx = xx;
+        e.xy = xy;
+        e.yy = yy;
+        row[(size_t)k * 32] = e;
+    }
+}
+
+// FP64 list of a handle whose FP32 list is current: the same pairs in the same
+// layout (so no FP64 neighbour search), each separation recomputed from the FP64
+// cell offsets with the cell shift of its source (as the neighbour search forms it),
+// then the kernel in float-float arithmetic (about 48 bits, ~1e-13 relative; the FP32
+// pipes run it far faster than the FP64 pipe would).  Pairs within rounding of r_c
+// may differ from an FP64 search; their kernel value is at the Ewald tolerance.
+__global__ void __launch_bounds__(256) k_pair_from32(int N, int n_box, double r_c, const int* __restrict__ perm,
+                                                    const int* __restrict__ cell, const double2* __restrict__ off,
+                                                    const int* __restrict__ slice_start,
+                                                    const int* __restrict__ row_count,
+                                                    const PairEntry<float>* __restrict__ p32, dfl::df xi2,
+                                                    dfl::df pref, dfl::ChebDF ce,
+                                                    PairEntry<double>* __restrict__ p64) {
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (t >= N) return;
+    const int sl = t >> 5, base = slice_start[sl], len = slice_start[sl + 1] - base, n = row_count[t];
+    const int ct = cell[perm[t]], cxt = ct % n_box, cyt = ct / n_box;
+    const double2 ot = off[t];
+    const size_t r0 = (size_t)base * 32 + (t & 31);
+    for (int k = lane; k < len; k += 32) {
+        PairEntry<double> e;
+        if (k < n) {
+            const int s = p32[r0 + (size_t)k * 32].src;
+            const int cs = cell[perm[s]];
+            int dx = cs % n_box - cxt, dy = cs / n_box - cyt;
+            dx += (dx < -1) ? n_box : 0;
+            dx -= (dx > 1) ? n_box : 0;
+            dy += (dy < -1) ? n_box : 0;
+            dy -= (dy > 1) ? n_box : 0;
+            const double2 os = off[s];
+            const double rx = (ot.x - dx * r_c) - os.x, ry = (ot.y - dy * r_c) - os.y;
+            dfl::pair_value(rx, ry, xi2, pref, ce, e.xx, e.xy, e.yy);
+            e.src = s;
+        } else {
+            e.xx = e.xy = e.yy = 0.0;
+            e.src = t;
+        }
+        p64[r0 + (size_t)k * 32] = e;
+    }
 }
 
 template <typename T>
@@ -287,9 +346,49 @@ template <typename T> static const ChebE1<T>& cheb(fbim_handle_s* h);
 template <> const ChebE1<double>& cheb<double>(fbim_handle_s* h) { return h->cheb64; }
 template <> const ChebE1<float>& cheb<float>(fbim_handle_s* h) { return h->cheb32; }
 
+// FP64 pair list from the current FP32 list (see k_pair_from32): no host sync.
+static fbim_status build_pairs_from32(fbim_handle_s* h) {
+    auto& e = h->e64;
+    const auto& f = h->e32;
+    const int N = h->N, n_slice = (N + 31) / 32;
+    const size_t total = (size_t)(f.n_padded / 32);
+    if (total > e.pair_cap) {
+        cudaFree(e.pairs);
+        e.pairs = nullptr;
+        const size_t cap = total + total / 4 + 32;
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.pairs, cap * 32 * sizeof(PairEntry<double>)));
+        e.pair_cap = cap;
+        ++h->layout_version;
+    }
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.slice_start, f.slice_start, sizeof(int) * (n_slice + 1),
+                                     cudaMemcpyDeviceToDevice, h->stream));
+    dfl::ChebDF cdf;
+    cdf.deg = h->cheb64.deg;
+    for (int k = 0; k <= cdf.deg; ++k) {
+        const dfl::df c = dfl::from_double(h->cheb64.c[k]);
+        cdf.hi[k] = c.hi;
+        cdf.lo[k] = c.lo;
+    }
+    const dfl::df sc = dfl::from_double(h->cheb64.scale);
+    cdf.s_hi = sc.hi;
+    cdf.s_lo = sc.lo;
+    k_pair_from32<<<(unsigned)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(
+        N, h->n_box, h->r_c, h->perm, h->cell, (const double2*)e.off, f.slice_start, f.row_count,
+        (const PairEntry<float>*)f.pairs, dfl::from_double(h->xi * h->xi),
+        dfl::from_double(1.0 / (4.0 * M_PI * h->eta)), cdf, (PairEntry<double>*)e.pairs);
+    h->launches += 1;
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    e.n_padded = f.n_padded;
+    e.pairs_ready = true;
+    e.pairs_geom = h->geom_version;
+    return FBIM_OK;
+}
+
 // Real-space pair list for the current geometry: count, slice lengths, fill.
 template <typename T>
 static fbim_status build_pairs(fbim_handle_s* h) {
+    if (std::is_same<T, double>::value && h->e32.ready && h->e32.pairs_ready && h->e32.pairs_geom == h->geom_version)
+        return build_pairs_from32(h);
     auto& e = bufs<T>(h);
     using T2 = typename V2<T>::type;
     const int N = h->N, n_slice = (N + 31) / 32;
@@ -314,13 +413,13 @@ static fbim_status build_pairs(fbim_handle_s* h) {
     const T pref = (T)(1.0 / (4.0 * M_PI * h->eta));
     k_pair_fill<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, h->perm, h->cell, h->cell_start,
                                                            (const T2*)e.off, e.slice_start, (PairEntry<T>*)e.pairs);
-    const size_t n_entries = (size_t)total * 32;
-    k_pair_eval<T><<<(unsigned)((n_entries + 255) / 256), 256, 0, h->stream>>>(
-        n_entries, (T)(h->xi * h->xi), pref, cheb<T>(h), (PairEntry<T>*)e.pairs);
+    k_pair_eval_rows<T><<<(unsigned)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(
+        N, e.slice_start, e.row_count, (T)(h->xi * h->xi), pref, cheb<T>(h), (PairEntry<T>*)e.pairs);
     h->launches += 4;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     e.n_padded = (long long)total * 32;
     e.pairs_ready = true;
+    e.pairs_geom = h->geom_version;
     return FBIM_OK;
 }
 

@@ -74,6 +74,7 @@ struct EwaldBuffers {
     long long n_pairs = 0;       // ordered pairs within r_c (without padding)
     long long n_padded = 0;      // stored entries including padding
     bool pairs_ready = false;
+    unsigned long long pairs_geom = ~0ull;  // geometry version the pair list was built for
     int wave_variant = 1;        // 0: tile kernels (shared memory), 1: warp-per-node kernels
     float variant_ms[2] = {0, 0};  // autotuner timings of spread + interp per variant
     bool ready = false;

@@ -203,8 +203,9 @@ fbim_status build_geometry(fbim_handle_s* h) {
     k_rot<<<(h->n_b + tb - 1) / tb, tb, 0, h->stream>>>(h->n_b, h->Q, h->rot);
     h->launches += 8;
     FBIM_CUDA_TRY(h, cudaGetLastError());
-    if (h->e64.ready) FBIM_TRY(refresh_offsets<double>(h));
+    // FP32 first: an FP32 handle's FP64 list is derived from its FP32 list
     if (h->e32.ready) FBIM_TRY(refresh_offsets<float>(h));
+    if (h->e64.ready) FBIM_TRY(refresh_offsets<double>(h));
     return FBIM_OK;
 }
 

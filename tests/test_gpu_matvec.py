@@ -100,6 +100,28 @@ def test_fp32_matvec_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box, wave):
     op.close()
 
 
+@pytest.mark.parametrize("n_b,n_p,L,seed,n_box", CASES)
+def test_fp32_handle_residual_operator_matches_oracle(torch, fb, n_b, n_p, L, seed, n_box):
+    """The FP64 operator of an FP32 handle (pairs from its FP32 list, float-float kernel
+    values) meets the FP64 bar, before and after a move of the bodies."""
+    ref, Q = _case(n_b, n_p, L, seed)
+    tol = 1e-13
+    xi = _xi(L, n_box, tol)
+    op = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, precision="fp32")
+    rng = np.random.default_rng(seed + 300)
+    mu = rng.standard_normal((n_b * n_p, 2))
+    mu_d = torch.tensor(mu, dtype=torch.float64, device="cuda")
+    op.apply_stokeslet(mu_d)  # FP32 list first: the FP64 list is derived from it
+    for Qk in (Q, Q + np.array([0.013, -0.021, 0.05])):
+        op.update_config(torch.tensor(Qk, device="cuda"))
+        M, _, _ = _oracle_parts(ref, Qk, L, xi)
+        v = op.apply_stokeslet_fp64(mu_d).cpu().numpy()
+        err = _rel(v, (M @ mu.reshape(-1)).reshape(-1, 2))
+        print(f"fp32 handle, fp64 operator {n_b}x{n_p}: rel err {err:.3e}")
+        assert err < FP64_TOL
+    op.close()
+
+
 def test_single_body_and_zero_input(torch, fb):
     ref, Q = _case(1, 64, 3.0, 1)
     xi = _xi(3.0, 4, 1e-13)
