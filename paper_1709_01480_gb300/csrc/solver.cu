@@ -179,6 +179,115 @@ __global__ void k_check_finite(int n, const double* __restrict__ x, int* __restr
 }
 
 // ---------------------------------------------------------------------------
+// Classical Gram-Schmidt (twice) for the Arnoldi step, fused: dots of w with the
+// K basis vectors, w -= V h with the next pass's dots (or |w|^2) in the same
+// sweep.  Each block owns CG_CHUNK consecutive entries (strided per thread for
+// coalescing) and writes one partial per dot; k_cgs_reduce sums the partials in
+// a fixed order, so the result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+constexpr int CG_TB = 256, CG_EPT = 4, CG_CHUNK = CG_TB * CG_EPT, CG_KMAX = 64;
+
+__device__ __forceinline__ double warp_sum(double s) {
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// part[j * nb + b] = sum over block b's entries of V_j w  (j < K), or of w w (K = 0 -> one slot)
+__device__ __forceinline__ void cgs_block_dots(int n, int K, const double* __restrict__ V, int ld, const double* wv,
+                                               int nb, double* __restrict__ part, double (*red)[8]) {
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i0 = b * CG_CHUNK + threadIdx.x;
+    const int KK = K > 0 ? K : 1;
+    for (int j = 0; j < KK; ++j) {
+        double sacc = 0.0;
+        if (K > 0) {
+            const double* v = V + (size_t)j * ld;
+#pragma unroll
+            for (int e = 0; e < CG_EPT; ++e) {
+                const int i = i0 + e * CG_TB;
+                if (i < n) sacc = fma(v[i], wv[e], sacc);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < CG_EPT; ++e) sacc = fma(wv[e], wv[e], sacc);
+        }
+        sacc = warp_sum(sacc);
+        if (lane == 0) red[j][warp] = sacc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < KK; j += CG_TB) {
+        double t = 0.0;
+        for (int q = 0; q < CG_TB / 32; ++q) t += red[j][q];
+        part[(size_t)j * nb + b] = t;
+    }
+}
+
+__global__ void __launch_bounds__(CG_TB) k_cgs_dots(int n, int K, const double* __restrict__ V, int ld,
+                                                    const double* __restrict__ w, int nb, double* __restrict__ part) {
+    __shared__ double red[CG_KMAX][8];
+    double wv[CG_EPT];
+    const int i0 = blockIdx.x * CG_CHUNK + threadIdx.x;
+#pragma unroll
+    for (int e = 0; e < CG_EPT; ++e) {
+        const int i = i0 + e * CG_TB;
+        wv[e] = i < n ? w[i] : 0.0;
+    }
+    cgs_block_dots(n, K, V, ld, wv, nb, part, red);
+}
+
+// w -= sum_{j<K} V_j h_j, then the partial dots of the new w with V (K2 = K) or |w|^2 (K2 = 0)
+__global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, int K, const double* __restrict__ V, int ld,
+                                                      const double* __restrict__ h, double* __restrict__ w, int K2,
+                                                      int nb, double* __restrict__ part) {
+    __shared__ double red[CG_KMAX][8];
+    __shared__ double hs[CG_KMAX];
+    for (int j = threadIdx.x; j < K; j += CG_TB) hs[j] = h[j];
+    __syncthreads();
+    double wv[CG_EPT];
+    const int i0 = blockIdx.x * CG_CHUNK + threadIdx.x;
+#pragma unroll
+    for (int e = 0; e < CG_EPT; ++e) {
+        const int i = i0 + e * CG_TB;
+        wv[e] = i < n ? w[i] : 0.0;
+    }
+    for (int j = 0; j < K; ++j) {
+        const double* v = V + (size_t)j * ld;
+        const double hj = hs[j];
+#pragma unroll
+        for (int e = 0; e < CG_EPT; ++e) {
+            const int i = i0 + e * CG_TB;
+            if (i < n) wv[e] = fma(-v[i], hj, wv[e]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < CG_EPT; ++e) {
+        const int i = i0 + e * CG_TB;
+        if (i < n) w[i] = wv[e];
+    }
+    cgs_block_dots(n, K2, V, ld, wv, nb, part, red);
+}
+
+// out[j] = sum_b part[j * nb + b], one warp per j (fixed order)
+__global__ void k_cgs_reduce(int K, int nb, const double* __restrict__ part, double* __restrict__ out) {
+    const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= K) return;
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += part[(size_t)j * nb + b];
+    s = warp_sum(s);
+    if (lane == 0) out[j] = s;
+}
+
+// y = a x, and a copy into y2 when given
+__global__ void k_scale_copy(int n, double a, const double* __restrict__ x, double* __restrict__ y,
+                             double* __restrict__ y2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = a * x[i];
+    y[i] = v;
+    if (y2) y2[i] = v;
+}
+
+// ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
 #define FBIM_CUBLAS_TRY(h, expr)                                                        \
@@ -354,6 +463,7 @@ fbim_status setup_solver(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&S->corr, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->hcol, sizeof(double) * (2 * (m + 1) + 1)));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gin, sizeof(double) * n));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->cg_part, sizeof(double) * CG_KMAX * ((n + CG_CHUNK - 1) / CG_CHUNK)));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gz, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gw, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMemsetAsync(S->gin, 0, sizeof(double) * n, h->stream));
@@ -382,7 +492,7 @@ void free_solver(fbim_handle_s* h) {
                     (void*)S->Gd64, (void*)S->G32, (void*)S->Gd32, (void*)S->V, (void*)S->Z, (void*)S->w,
                     (void*)S->r, (void*)S->d, (void*)S->t, (void*)S->hcol, S->zbuf, S->gbuf, (void*)S->lz,
                     (void*)S->lh, (void*)S->rfd, S->blas_ws, (void*)S->corr, (void*)S->gin, (void*)S->gz,
-                    (void*)S->gw})
+                    (void*)S->gw, (void*)S->cg_part})
         cudaFree(p);
     for (cudaGraphExec_t g : S->op_graph)
         if (g) cudaGraphExecDestroy(g);
@@ -414,6 +524,8 @@ template <> struct Gemm<double> {
         return cublasDgemm(b, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &one, A, m, B, k, &zero, C, m);
     }
 };
+// The FP32 preconditioner's GEMM stays in full FP32: TF32 operands (10-bit mantissa)
+// cost the FGMRES about 8% more iterations than they save in GEMM time.
 template <> struct Gemm<float> {
     static cublasStatus_t run(cublasHandle_t b, int m, int n, int k, const float* A, const float* B, float* C) {
         const float one = 1.0f, zero = 0.0f;
@@ -516,6 +628,8 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
     }
     std::vector<double> Hh((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), hc(2 * (m + 1) + 1);
     const bool use_graph = !h->timing;
+    const bool fused = m + 1 <= CG_KMAX;
+    int gin_holds = -1;  // index of the basis vector the captured operator's input holds
     if (use_graph) {
         FBIM_TRY(coarse_refresh(h));  // host-synchronising, and may reallocate: before the graph check
         FBIM_TRY(op_graph<T>(h));
@@ -541,9 +655,10 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
             return FBIM_ERR_NONFINITE;
         }
         if (rel_est <= tol || iters >= max_iter) return FBIM_OK;
-        double inv = 1.0 / beta;
-        FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->V, S->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-        FBIM_CUBLAS_TRY(h, cublasDscal(B, n, &inv, S->V, 1));
+        k_scale_copy<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0 / beta, S->w, S->V,
+                                                             use_graph ? S->gin : nullptr);
+        h->launches += 1;
+        gin_holds = 0;
         std::fill(gvec.begin(), gvec.end(), 0.0);
         gvec[0] = beta;
         int k_used = 0;
@@ -552,7 +667,9 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
             double* zk = S->Z + (size_t)k * ld;
             if (use_graph) {
                 const int gk = std::is_same<T, float>::value ? 0 : 1;
-                FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->gin, vk, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+                if (gin_holds != k)
+                    FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->gin, vk, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                                                     h->stream));
                 FBIM_CUDA_TRY(h, cudaGraphLaunch(S->op_graph[gk], h->stream));
                 FBIM_CUDA_TRY(h, cudaMemcpyAsync(zk, S->gz, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
                 FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->w, S->gw, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
@@ -562,17 +679,31 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
                 FBIM_TRY(saddle_apply<T>(h, zk, S->w));
             }
             // classical Gram-Schmidt, twice
-            FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero, S->hcol, 1));
-            FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol, 1, &one, S->w, 1));
-            FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero,
-                                           S->hcol + (m + 1), 1));
-            FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol + (m + 1), 1, &one,
-                                           S->w, 1));
-            // |w|^2 on the device next to the dot products: one read-back, one sync per step
-            cublasSetPointerMode(B, CUBLAS_POINTER_MODE_DEVICE);
-            const cublasStatus_t ds = cublasDdot(B, n, S->w, 1, S->w, 1, S->hcol + 2 * (m + 1));
-            cublasSetPointerMode(B, CUBLAS_POINTER_MODE_HOST);
-            FBIM_CUBLAS_TRY(h, ds);
+            if (fused) {
+                const int K = k + 1, nb = (n + CG_CHUNK - 1) / CG_CHUNK, rb = (K * 32 + 255) / 256;
+                k_cgs_dots<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->w, nb, S->cg_part);
+                k_cgs_reduce<<<rb, 256, 0, h->stream>>>(K, nb, S->cg_part, S->hcol);
+                k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol, S->w, K, nb, S->cg_part);
+                k_cgs_reduce<<<rb, 256, 0, h->stream>>>(K, nb, S->cg_part, S->hcol + (m + 1));
+                k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol + (m + 1), S->w, 0, nb,
+                                                          S->cg_part);
+                k_cgs_reduce<<<1, 32, 0, h->stream>>>(1, nb, S->cg_part, S->hcol + 2 * (m + 1));
+                h->launches += 6;
+                FBIM_CUDA_TRY(h, cudaGetLastError());
+            } else {
+                FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero, S->hcol, 1));
+                FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol, 1, &one, S->w, 1));
+                FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero,
+                                               S->hcol + (m + 1), 1));
+                FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol + (m + 1), 1,
+                                               &one, S->w, 1));
+                // |w|^2 on the device next to the dot products
+                cublasSetPointerMode(B, CUBLAS_POINTER_MODE_DEVICE);
+                const cublasStatus_t ds = cublasDdot(B, n, S->w, 1, S->w, 1, S->hcol + 2 * (m + 1));
+                cublasSetPointerMode(B, CUBLAS_POINTER_MODE_HOST);
+                FBIM_CUBLAS_TRY(h, ds);
+            }
+            // one read-back, one sync per step
             FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->hcol, sizeof(double) * (2 * (m + 1) + 1),
                                              cudaMemcpyDeviceToHost, h->stream));
             FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -585,10 +716,12 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
                 return FBIM_ERR_NONFINITE;
             }
             if (hn > 0) {
-                double ih = 1.0 / hn;
+                // V_{k+1} = w / h_{k+1,k}, also into the captured operator's input
                 double* vn = S->V + (size_t)(k + 1) * ld;
-                FBIM_CUDA_TRY(h, cudaMemcpyAsync(vn, S->w, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-                FBIM_CUBLAS_TRY(h, cublasDscal(B, n, &ih, vn, 1));
+                k_scale_copy<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0 / hn, S->w, vn,
+                                                                     use_graph ? S->gin : nullptr);
+                h->launches += 1;
+                gin_holds = k + 1;
             }
             for (int i = 0; i < k; ++i) {
                 double t0 = cs[i] * col[i] + sn[i] * col[i + 1];

@@ -45,6 +45,7 @@ struct Solver {
     // captured operator (precondition then saddle) per precision, [0] FP32 / [1] FP64:
     // reads gin, writes gz = P gin and gw = A gz; recaptured when the handle's layout changes
     double *gin = nullptr, *gz = nullptr, *gw = nullptr;
+    double* cg_part = nullptr;  // [64][blocks] partial dot products of the fused Gram-Schmidt
     cudaGraphExec_t op_graph[2] = {nullptr, nullptr};
     unsigned long long op_version[2] = {0, 0};
     long long op_kernels[2] = {0, 0};

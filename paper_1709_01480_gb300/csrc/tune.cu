@@ -5,7 +5,8 @@
 // the forward + inverse transform pair of a few admissible sizes in
 // [M_min, 1.3 M_min] (even, 2^a 3^b 5^c 7^d, with a wave-space tile side in
 // [max(16, (P - 1)/2), 64] dividing M) and keeps the cheapest.  FP32 handles
-// weigh the FP64 transform (used by the refinement residuals) at 0.1.
+// weigh the FP64 transform (used by the refinement residuals) at 0.1.  The
+// smallest side within 5% of the cheapest is kept.
 #include <cufft.h>
 
 #include <algorithm>
@@ -93,18 +94,22 @@ fbim_status tune_grid(fbim_handle_s* h, int M_min, int P, int& M_out, double& be
     }
     cudaMemsetAsync(grid, 0, gbytes, h->stream);
     const bool f32 = h->precision == FBIM_FP32;
+    std::vector<double> cost(cand.size(), -1.0);
     double best = 1e300;
-    for (int m : cand) {
-        double t = f32 ? time_fft(h->stream, m, true, grid, spec, e0, e1) : 0.0;
-        const double t64 = time_fft(h->stream, m, false, grid, spec, e0, e1);
+    for (size_t c = 0; c < cand.size(); ++c) {
+        const double t = f32 ? time_fft(h->stream, cand[c], true, grid, spec, e0, e1) : 0.0;
+        const double t64 = time_fft(h->stream, cand[c], false, grid, spec, e0, e1);
         if (t < 0 || t64 < 0) continue;
-        const double cost = f32 ? t + 0.1 * t64 : t64;
-        if (cost < best) {
-            best = cost;
-            M_out = m;
-        }
+        cost[c] = f32 ? t + 0.1 * t64 : t64;
+        best = std::min(best, cost[c]);
     }
-    best_ms = best < 1e300 ? best : 0.0;
+    // the smallest side within 5% of the cheapest: timing noise does not flip the choice
+    for (size_t c = 0; c < cand.size(); ++c)
+        if (cost[c] >= 0 && cost[c] <= 1.05 * best) {
+            M_out = cand[c];
+            best_ms = cost[c];
+            break;
+        }
     cudaFree(grid);
     cudaFree(spec);
     cudaEventDestroy(e0);
