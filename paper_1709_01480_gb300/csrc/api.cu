@@ -28,6 +28,9 @@ void release(fbim_handle h) {
     cudaSetDevice(h->device);
     for (auto& e : h->ev)
         if (e) cudaEventDestroy(e);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->aux) cudaStreamDestroy(h->aux);
     fbim::free_ewald(h);
     fbim::free_coarse(h);
     cudaFree(h->ref);
@@ -118,6 +121,10 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
         h->restart = p.restart > 0 ? p.restart : 60;
         h->autotune = p.autotune;
         h->stream = (cudaStream_t)p.stream;
+        FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
+        FBIM_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        FBIM_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        FBIM_CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
         h->host_ref.assign(ref_nodes_host, ref_nodes_host + 2 * n_p);
         for (int i = 0; i < 3 * n_b; ++i)
             if (!std::isfinite(Q_host[i])) {

@@ -539,6 +539,16 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     k_gather<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->perm, h->tperm, real, wave, h->rot,
                                                          (const double2*)mu, (T2*)e.mu_s, (T2*)e.mu_t, e.mu_r);
     h->mark(FBIM_ST_GATHER);
+    // real space on the auxiliary stream, concurrent with the wave space (sequential
+    // while the stage timers run, so that each stage is timed alone)
+    const bool fork = real && wave && h->aux && !h->timing;
+    if (fork) {
+        FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
+        FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+        k_pair_spmv<T><<<(N + 255) / 256, 256, 0, h->aux>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
+                                                            (const T2*)e.mu_s, (T2*)e.v_s);
+        FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_join, h->aux));
+    }
     const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
     const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
     const T ah2 = (T)(alpha * h->h * h->h);
@@ -564,7 +574,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         FBIM_CUFFT_TRY(h, FftType<T>::i(e.plan_i, (C*)e.spec, e.grid));
         h->mark(FBIM_ST_FFT_I);
     }
-    if (real) {
+    if (real && !fork) {
         k_pair_spmv<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
                                                                (const T2*)e.mu_s, (T2*)e.v_s);
         h->mark(FBIM_ST_PAIRS);
@@ -576,6 +586,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
             tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
         h->mark(FBIM_ST_INTERP);
     }
+    if (fork) FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
     k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, real ? 1 : 0, wave ? 1 : 0, h->slot,
                                                          h->tslot, (const T2*)e.v_s, (const T2*)e.v_t, h->rot,
                                                          h->band_dev, e.mu_r, (double2*)v);

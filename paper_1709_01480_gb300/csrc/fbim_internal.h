@@ -103,6 +103,10 @@ struct fbim_handle_s {
     int device = 0;
     int restart = 60;
     cudaStream_t stream = nullptr;
+    // the real-space pairs run on aux, forked from and joined to stream by events, so
+    // that they overlap the wave-space chain (also inside captured graphs)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 
     // ---- geometry (device) -------------------------------------------------
