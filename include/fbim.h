@@ -68,6 +68,12 @@ typedef struct {
     int    grid_tune;     /* 1 (default): when grid <= 0, time the FFT of a few admissible sides in
                              [M_min, 1.3 M_min] and keep the cheapest (any side >= the rule's M_min
                              meets tol); 0: use M_min                                          */
+    int    split_tune;    /* 0 (default): use r_c as given.  1: treat r_c > 0 as the smallest cutoff
+                             and time candidate cutoffs up to 2.2 r_c (xi then follows from r_c and
+                             tol; the given xi is ignored) on throwaway handles, keeping the one with
+                             the least 25 FP32 + 1 FP64 operator applications + 1 geometry update
+                             (one mixed-precision solve; 25 FP64 + 1 update for FBIM_FP64).  Set-up
+                             then costs a few handle set-ups more.                               */
 } fbim_params;
 
 /* Ewald parameters the library settled on (fbim_get_info). */
@@ -90,6 +96,8 @@ typedef struct {
                                 (library calls such as cuFFT and cuBLAS not included)  */
     int    grid_min;         /* the grid rule's smallest admissible side M_min          */
     double grid_tune_ms;     /* tuned cost (ms) of the chosen side's FFT pair, 0 if untuned */
+    int    split_candidates; /* cutoffs the split tuner timed (0: r_c as given)          */
+    double split_cost_ms;    /* the chosen cutoff's cost per solve-equivalent (ms)      */
 } fbim_info;
 
 /* Fill *p with defaults: FP64, order 4, automatic grid and support, eta = 1,

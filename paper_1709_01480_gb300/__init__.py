@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("alpert_order", ctypes.c_int), ("grid", ctypes.c_int),
                 ("support", ctypes.c_int), ("eta", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("restart", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("grid_tune", ctypes.c_int)]
+                ("grid_tune", ctypes.c_int), ("split_tune", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -68,7 +68,8 @@ class Info(ctypes.Structure):
                 ("alpert_window", ctypes.c_int), ("alpert_band", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tile", ctypes.c_int), ("pair_entries", ctypes.c_longlong),
                 ("wave_variant", ctypes.c_int), ("variant_ms", ctypes.c_double * 2),
-                ("launches", ctypes.c_longlong), ("grid_min", ctypes.c_int), ("grid_tune_ms", ctypes.c_double)]
+                ("launches", ctypes.c_longlong), ("grid_min", ctypes.c_int), ("grid_tune_ms", ctypes.c_double),
+                ("split_candidates", ctypes.c_int), ("split_cost_ms", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -190,7 +191,8 @@ class FBIM:
     """One suspension of rigid bodies of a single shape in a periodic box."""
 
     def __init__(self, ref_nodes, Q, L, *, tol=1e-8, r_c=0.0, xi=0.0, precision="fp64", order=4,
-                 grid=0, support=0, eta=1.0, stream=None, device=0, restart=60, wave="auto", grid_tune=True):
+                 grid=0, support=0, eta=1.0, stream=None, device=0, restart=60, wave="auto", grid_tune=True,
+                 split_tune=False):
         ref = np.ascontiguousarray(ref_nodes, dtype=np.float64)
         Qh = np.ascontiguousarray(Q, dtype=np.float64)
         self.n_p = ref.shape[0]
@@ -206,6 +208,7 @@ class FBIM:
         p.restart = restart
         p.autotune = {"auto": 1, "tile": 0, "warp": 2}[wave]
         p.grid_tune = 1 if grid_tune else 0
+        p.split_tune = 1 if split_tune else 0
         if stream is None:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream

@@ -84,12 +84,13 @@ extern "C" fbim_status fbim_default_params(fbim_params* p) {
     p->restart = 60;
     p->autotune = 1;
     p->grid_tune = 1;
+    p->split_tune = 0;
     return FBIM_OK;
 }
 
-extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const double* ref_nodes_host,
-                                  const double* Q_host, double L, double r_c, double xi, double tol,
-                                  const fbim_params* opt) {
+static fbim_status setup_one(fbim_handle* out, int n_b, int n_p, const double* ref_nodes_host,
+                             const double* Q_host, double L, double r_c, double xi, double tol,
+                             const fbim_params* opt) {
     if (!out || n_b <= 0 || n_p < 8 || !ref_nodes_host || !Q_host || !(L > 0) || !(tol > 0 && tol < 1)) {
         set_global_error("fbim_setup: invalid argument");
         return FBIM_ERR_INVALID_ARG;
@@ -276,6 +277,91 @@ extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const doub
     return FBIM_OK;
 }
 
+// Split tuner.  The Ewald split parameter moves work between the real-space pair
+// sum (grows with r_c^2) and the wave space (the grid side shrinks like 1/r_c); with
+// the pair sum running beside the wave-space chain the best r_c is found by timing.
+// Candidates r_c >= the given one (the Alpert band sets its lower bound), each on a
+// throwaway handle: cost = 25 FP32 operator applications + 1 FP64 residual
+// application + 1 geometry update (one mixed-precision solve), or 25 FP64
+// applications + 1 update for an FP64 handle.
+static fbim_status tune_split(int n_b, int n_p, const double* ref, const double* Q, double L, double r_c0, double tol,
+                              fbim_params p, double& r_best, int& n_cand, double& best_ms) {
+    p.split_tune = 0;
+    r_best = r_c0;
+    n_cand = 0;
+    best_ms = 0;
+    const bool f32 = p.precision == FBIM_FP32;
+    double best = 1e300;
+    int last_box = -1;
+    for (double fac : {1.0, 1.25, 1.5, 1.8, 2.2}) {
+        const double rc = std::min(r_c0 * fac, L / 3.0);
+        const int nbox = std::max(3, (int)std::floor(L / rc));
+        if (nbox == last_box) continue;
+        last_box = nbox;
+        fbim_handle h = nullptr;
+        if (setup_one(&h, n_b, n_p, ref, Q, L, L / nbox, 0.0, tol, &p) != FBIM_OK) continue;
+        double* buf = nullptr;
+        const size_t N = (size_t)h->N;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool ok = cudaMalloc(&buf, 2 * 2 * N * sizeof(double)) == cudaSuccess &&
+                  cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess &&
+                  cudaMemsetAsync(buf, 0, 2 * N * sizeof(double), h->stream) == cudaSuccess;
+        double* mu = buf;
+        double* v = buf + 2 * N;
+        auto timeit = [&](int warm, int reps, auto&& fn) -> double {
+            for (int r = 0; r < warm && ok; ++r) ok = fn() == FBIM_OK;
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < reps && ok; ++r) ok = fn() == FBIM_OK;
+            cudaEventRecord(e1, h->stream);
+            float ms = 0.f;
+            ok = ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            return ms / reps;
+        };
+        // a non-zero force on every node (the cost does not depend on the values)
+        if (ok) ok = cudaMemcpyAsync(mu, h->Q, sizeof(double) * std::min<size_t>(2 * N, 3 * (size_t)n_b),
+                                     cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess;
+        const double t_lo = f32 ? timeit(2, 5, [&] { return fbim_apply_stokeslet(h, mu, v); }) : 0.0;
+        const double t_hi = timeit(1, f32 ? 2 : 5, [&] { return fbim_apply_stokeslet_fp64(h, mu, v); });
+        const double t_up = timeit(1, 2, [&] { return fbim_update_config(h, h->Q); });
+        const double cost = f32 ? 25.0 * t_lo + t_hi + t_up : 25.0 * t_hi + t_up;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        cudaFree(buf);
+        fbim_destroy(h);
+        cudaGetLastError();
+        if (!ok) continue;
+        ++n_cand;
+        if (cost < best) {
+            best = cost;
+            r_best = L / nbox;
+        }
+    }
+    best_ms = best < 1e300 ? best : 0.0;
+    return n_cand > 0 ? FBIM_OK : FBIM_ERR_SETUP;
+}
+
+extern "C" fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const double* ref_nodes_host,
+                                  const double* Q_host, double L, double r_c, double xi, double tol,
+                                  const fbim_params* opt) {
+    fbim_params p;
+    fbim_default_params(&p);
+    if (opt) p = *opt;
+    if (!p.split_tune || !(r_c > 0) || !out || !(L > 0) || !(tol > 0 && tol < 1) || n_b <= 0 || n_p < 8 ||
+        !ref_nodes_host || !Q_host)
+        return setup_one(out, n_b, n_p, ref_nodes_host, Q_host, L, r_c, xi, tol, opt);
+    double r_best = r_c, cost = 0;
+    int n_cand = 0;
+    if (tune_split(n_b, n_p, ref_nodes_host, Q_host, L, r_c, tol, p, r_best, n_cand, cost) != FBIM_OK)
+        r_best = r_c;  // tuning is optional: fall back to the given cutoff
+    p.split_tune = 0;
+    const fbim_status st = setup_one(out, n_b, n_p, ref_nodes_host, Q_host, L, r_best, n_cand > 0 ? 0.0 : xi, tol, &p);
+    if (st == FBIM_OK) {
+        (*out)->split_candidates = n_cand;
+        (*out)->split_cost_ms = cost;
+    }
+    return st;
+}
+
 extern "C" fbim_status fbim_update_config(fbim_handle h, const double* Q_dev) {
     if (!h || !Q_dev) return FBIM_ERR_INVALID_ARG;
     return guarded(h, [&]() -> fbim_status {
@@ -341,6 +427,8 @@ extern "C" fbim_status fbim_get_info(fbim_handle h, fbim_info* info) {
     info->launches = h->launches;
     info->grid_min = h->M_min;
     info->grid_tune_ms = h->grid_tune_ms;
+    info->split_candidates = h->split_candidates;
+    info->split_cost_ms = h->split_cost_ms;
     return FBIM_OK;
 }
 

@@ -130,6 +130,8 @@ struct fbim_handle_s {
     int autotune = 1;            // time the wave-space kernel variants at setup
     int M_min = 0;               // the grid rule's smallest side
     double grid_tune_ms = 0;     // cost of the tuned FFT pair (0: not tuned)
+    int split_candidates = 0;    // cutoffs timed by the split tuner (0: not tuned)
+    double split_cost_ms = 0;    // the chosen cutoff's cost per solve-equivalent
     double zmax = 0;             // xi^2 r_c^2 (upper end of the E1 expansion)
     fbim::ChebE1<double> cheb64{};
     fbim::ChebE1<float> cheb32{};

@@ -3,7 +3,7 @@
 // (finer grid, same support P and the Gaussian shape eta_s recomputed for h).
 // cuFFT's speed depends strongly on the factorisation of M, so the setup times
 // the forward + inverse transform pair of a few admissible sizes in
-// [M_min, 1.3 M_min] (even, 2^a 3^b 5^c 7^d, with a wave-space tile side in
+// [M_min, 1.3 M_min] (multiples of 4, 2^a 3^b 5^c 7^d, with a wave-space tile side in
 // [max(16, (P - 1)/2), 64] dividing M) and keeps the cheapest.  FP32 handles
 // weigh the FP64 transform (used by the refinement residuals) at 0.1.  The
 // smallest side within 5% of the cheapest is kept.
@@ -70,7 +70,8 @@ static double time_fft(cudaStream_t st, int M, bool fp32, void* grid, void* spec
 fbim_status tune_grid(fbim_handle_s* h, int M_min, int P, int& M_out, double& best_ms) {
     std::vector<int> cand;
     const int ts_min = std::max(16, (P - 1) / 2);
-    for (int m = M_min + (M_min & 1); m <= (int)(1.3 * M_min) + 2 && cand.size() < 8; m += 2)
+    // multiples of 4 (the FP32 wave-space kernels then move float4 chunks)
+    for (int m = (M_min + 3) / 4 * 4; m <= (int)(1.3 * M_min) + 4 && cand.size() < 12; m += 4)
         if (nice(m) && tile_side(m) >= ts_min) cand.push_back(m);
     M_out = M_min;
     best_ms = 0;

@@ -346,6 +346,81 @@ __global__ void __launch_bounds__(256) k_interp_warp(int N, int M, int P, int hw
     }
 }
 
+// ---------------------------------------------------------------------------
+// Vector interpolation (FP32, P <= 13, M a multiple of 4).  Four lanes take a node
+// and eight nodes share a warp; lane c of a node owns grid columns
+// [a0 + 4c, a0 + 4c + 4), a0 = the window's first column rounded down to a multiple
+// of 4, so that 4 chunks cover the window (13 + 3 columns).  Every chunk is 16-byte
+// aligned and never wraps (M is a multiple of 4), so each row costs one float4 load
+// per chunk.  Row weights come from the two-sided recurrence in every lane.  (The
+// same layout with float4 atomic adds made spreading slower than the scalar
+// column-lane kernel, so spreading keeps that one.)
+// ---------------------------------------------------------------------------
+constexpr int kVecPMAX = 16;
+
+static __device__ __forceinline__ void vec_setup(int i, int N, int lane, int P, int hw, float a, float q2, float g0, int M,
+                                          const int2* __restrict__ tbase, const float2* __restrict__ tfrac,
+                                          bool& active, int& gc, int& gy, float (&wx)[4], float (&wy)[kVecPMAX]) {
+    constexpr int HW = (kVecPMAX - 1) / 2;
+    active = i < N;
+    int2 b = make_int2(0, 0);
+    float2 f = make_float2(0.f, 0.f);
+    if (active) {
+        b = tbase[i];
+        f = tfrac[i];
+    }
+    const int c = lane & 3;
+    const int gx0 = b.x - hw;                 // window's first column (may be negative)
+    const int off = ((gx0 % 4) + 4) % 4;      // columns before it in its aligned chunk
+    int a0 = gx0 - off + 4 * c;               // this lane's chunk, a multiple of 4
+    a0 += (a0 < 0) ? M : 0;
+    a0 -= (a0 >= M) ? M : 0;
+    gc = a0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int p = 4 * c + j - off;        // window column of chunk element j
+        const float d = float(p - hw) - f.x;
+        wx[j] = (active && p >= 0 && p < P) ? expf(-a * d * d) : 0.f;
+    }
+    window_recur<float, kVecPMAX>(f.y, a, q2, g0, wy);
+    (void)HW;
+    gy = b.y - hw;
+    gy += (gy < 0) ? M : 0;
+}
+
+static __global__ void __launch_bounds__(256) k_interp_vec(int N, int M, int P, int hw, float a, float q2, float g0,
+                                                   const int2* __restrict__ tbase, const float2* __restrict__ tfrac,
+                                                   const float* __restrict__ grid, float2* __restrict__ v_t) {
+    constexpr int HW = (kVecPMAX - 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 2);
+    bool active;
+    int gc, gy;
+    float wx[4], wy[kVecPMAX];
+    vec_setup(i, N, lane, P, hw, a, q2, g0, M, tbase, tfrac, active, gc, gy, wx, wy);
+    const size_t MM = (size_t)M * M;
+    const int shift = HW - hw;
+    float sx = 0.f, sy = 0.f;
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < kVecPMAX; ++j) {
+            if (j >= shift && j < shift + P) {
+                const float4 ux = __ldg(reinterpret_cast<const float4*>(grid + (size_t)gy * M + gc));
+                const float4 uy = __ldg(reinterpret_cast<const float4*>(grid + MM + (size_t)gy * M + gc));
+                sx = fmaf(wy[j], wx[0] * ux.x + wx[1] * ux.y + wx[2] * ux.z + wx[3] * ux.w, sx);
+                sy = fmaf(wy[j], wx[0] * uy.x + wx[1] * uy.y + wx[2] * uy.z + wx[3] * uy.w, sy);
+                gy = (gy + 1 == M) ? 0 : gy + 1;
+            }
+        }
+    }
+    // reduce over the node's four lanes (all lanes take part)
+    sx += __shfl_xor_sync(0xffffffffu, sx, 1);
+    sy += __shfl_xor_sync(0xffffffffu, sy, 1);
+    sx += __shfl_xor_sync(0xffffffffu, sx, 2);
+    sy += __shfl_xor_sync(0xffffffffu, sy, 2);
+    if (active && (lane & 3) == 0) v_t[i] = make_float2(sx, sy);
+}
+
 template <typename T>
 inline size_t spread_smem_bytes(int TS, int P) {
     const int W = TS + (P - 1), pitch = W | 1;

@@ -1,5 +1,6 @@
 // Wave-space tile kernels instantiated for float.
 #include <cmath>
+#include <cstdint>
 
 #include "wave_tiles.cuh"
 
@@ -70,6 +71,12 @@ static int warp_blocks(int N, int P) {
     return (int)((warps * 32 + 255) / 256);
 }
 
+// The float4 interpolation needs M % 4 == 0 (16-byte aligned chunks that never
+// wrap), a 16-byte aligned grid and P <= 13 (4 chunks of 4 columns cover the window).
+static bool vec_ok(const TileGeom& tg, const void* grid) {
+    return tg.P <= 13 && tg.M % 4 == 0 && (reinterpret_cast<uintptr_t>(grid) & 15) == 0;
+}
+
 template <>
 void warp_spread<float>(cudaStream_t st, int N, const TileGeom& tg, float a, float g0, const int2* tbase,
                       const void* tfrac, const void* mu_t, float* grid) {
@@ -82,6 +89,12 @@ template <>
 void warp_interp<float>(cudaStream_t st, int N, const TileGeom& tg, float a, float g0, const int2* tbase,
                       const void* tfrac, const float* grid, void* v_t) {
     using T2 = typename V2<float>::type;
+    if (vec_ok(tg, grid)) {
+        const float q2 = (float)std::exp(-2.0 * (double)a);
+        k_interp_vec<<<(unsigned)(((size_t)N * 4 + 255) / 256), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, q2, g0, tbase,
+                                                                            (const float2*)tfrac, grid, (float2*)v_t);
+        return;
+    }
     k_interp_warp<float><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
                                                             grid, (T2*)v_t);
 }
