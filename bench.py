@@ -56,10 +56,11 @@ BATCH_RC = 0.504
 # CPU baseline prices a solve as this many oracle matvecs plus one residual check
 ITERS_PER_SOLVE_REF = 16
 # DRAM bytes (read + write) per launch of each FP32 operator stage, from the ncu
-# capture summarised in profiles/ewald_matvec_dram_starfish1024.md; valid for the
-# kernels as they are now (None for a stage whose kernel changed since).
-MEASURED_DRAM_BYTES = {"spread": 22.31e6, "interp": 22.99e6, "pairs": 128.73e6, "finish": 5.31e6,
-                       "scale": 23.91e6, "gather": 3.17e6}
+# capture summarised in profiles/ewald_matvec_dram_starfish1024.md (cutoff L/91 and
+# grid 1296^2, the split and grid tuners' choice); valid for the kernels and the
+# configuration as they are now.
+MEASURED_DRAM_BYTES = {"pairs": 163.19e6, "spread": 15.20e6, "interp": 14.91e6, "finish": 5.31e6,
+                       "scale": 13.45e6, "gather": 3.17e6}
 
 
 def load_peaks():
@@ -320,7 +321,11 @@ def run_gpu(args):
     w = fbim_synth.workload(WORKLOAD)
     xi = math.sqrt(math.log(100.0 / w.tol)) / (w.L / N_BOX)
     # the chosen form lets the split tuner move r_c up from L/115; the plain FP64 form keeps it
-    ops = {"fp32": fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=w.L / N_BOX, precision="fp32", split_tune=True),
+    # (--r-c / --grid pin the chosen form's cutoff and grid, e.g. to profile the configuration a
+    # timed run picked: the tuners time kernels, and kernels time differently under a profiler)
+    pinned = args.r_c > 0
+    ops = {"fp32": fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=args.r_c if pinned else w.L / N_BOX,
+                           precision="fp32", split_tune=not pinned, grid=args.grid, grid_tune=args.grid <= 0),
            "fp64": fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=w.L / N_BOX, xi=xi, precision="fp64")}
     info = ops["fp32"].info
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -493,6 +498,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--r-c", type=float, default=0.0, help="pin the chosen form's cutoff (default: split tuner)")
+    ap.add_argument("--grid", type=int, default=0, help="pin the chosen form's FFT grid side (default: tuner)")
     ap.add_argument("--legs", default="batched,learned",
                     help="extra measurements: batched (independent suspensions), learned (coarse level); '' for none")
     args = ap.parse_args()
