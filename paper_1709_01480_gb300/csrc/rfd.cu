@@ -14,7 +14,7 @@
 namespace fbim {
 
 fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip, double tol, int max_iter,
-                           double* U, double* mu_out, int* iters_out, double* res_out);
+                           double* U, double* mu_out, int* iters_out, double* res_out, bool warm);
 fbim_status brownian_slip(fbim_handle_s* h, unsigned long long seed, unsigned long long counter, double kT, double dt,
                           const double* W_r, const double* Z_w, double tol, int max_iter, double* slip,
                           int* lanczos_iters);
@@ -67,7 +67,7 @@ fbim_status rfd_step(fbim_handle_s* h, const double* F, double dt, double kT, do
         FBIM_TRY(update_positions(h, Q));
         int lz = 0;
         FBIM_TRY(brownian_slip(h, seed, 3 * step, kT, dt, W_r, Z_w, std::max(tol, 1e-12), 200, slip, &lz));
-        fbim_status s1 = mobility_solve(h, F, slip, tol, max_iter, U, nullptr, &it, nullptr);
+        fbim_status s1 = mobility_solve(h, F, slip, tol, max_iter, U, nullptr, &it, nullptr, false);
         total += it;
         if (s1 != FBIM_OK && s1 != FBIM_ERR_NOT_CONVERGED) return s1;
         // (2) random finite difference of N along W~
@@ -78,12 +78,13 @@ fbim_status rfd_step(fbim_handle_s* h, const double* F, double dt, double kT, do
         }
         k_displace<<<(n3 + tb - 1) / tb, tb, 0, h->stream>>>(n3, Q, 0.5 * delta, wt, Qd);
         FBIM_TRY(update_positions(h, Qd));
-        fbim_status s2 = mobility_solve(h, wt, nullptr, tol, max_iter, Up, nullptr, &it, nullptr);
+        fbim_status s2 = mobility_solve(h, wt, nullptr, tol, max_iter, Up, nullptr, &it, nullptr, false);
         total += it;
         if (s2 != FBIM_OK && s2 != FBIM_ERR_NOT_CONVERGED) return s2;
         k_displace<<<(n3 + tb - 1) / tb, tb, 0, h->stream>>>(n3, Q, -0.5 * delta, wt, Qd);
         FBIM_TRY(update_positions(h, Qd));
-        fbim_status s3 = mobility_solve(h, wt, nullptr, tol, max_iter, Um, nullptr, &it, nullptr);
+        // same force at a configuration 2 delta/2 |W~| away: start from the Q+ solution
+        fbim_status s3 = mobility_solve(h, wt, nullptr, tol, max_iter, Um, nullptr, &it, nullptr, true);
         total += it;
         if (s3 != FBIM_OK && s3 != FBIM_ERR_NOT_CONVERGED) return s3;
         // (3) update and leave the handle at the new configuration

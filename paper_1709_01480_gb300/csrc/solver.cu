@@ -773,8 +773,10 @@ static fbim_status true_residual(fbim_handle_s* h, const double* b, const double
     return FBIM_OK;
 }
 
+// warm: start from the solution [mu; U] of the previous solve on this handle (kept in
+// the solver's workspace) instead of zero, e.g. for a nearby configuration.
 fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip, double tol, int max_iter,
-                           double* U, double* mu_out, int* iters_out, double* res_out) {
+                           double* U, double* mu_out, int* iters_out, double* res_out, bool warm) {
     FBIM_TRY(setup_solver(h));
     Solver* S = h->solver;
     const int n = S->n, N2 = 2 * h->N;
@@ -782,25 +784,33 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
     // b lives in S->t, x in S->d
     k_neg_rhs<<<nb, tb, 0, h->stream>>>(N2, 3 * h->n_b, slip, F, S->t);
     h->launches += 1;
-    FBIM_CUDA_TRY(h, cudaMemsetAsync(S->d, 0, sizeof(double) * n, h->stream));
+    warm = warm && S->have_x;
+    if (!warm) FBIM_CUDA_TRY(h, cudaMemsetAsync(S->d, 0, sizeof(double) * n, h->stream));
     int iters = 0;
     double rel = 1.0;
     if (h->precision == FBIM_FP64) {
         double est = 0;
-        FBIM_TRY(fgmres<double>(h, S->t, S->d, tol, max_iter, iters, est, true));
+        FBIM_TRY(fgmres<double>(h, S->t, S->d, tol, max_iter, iters, est, !warm));
         FBIM_TRY(true_residual(h, S->t, S->d, S->r, rel));
     } else {
         // Iterative refinement: FP32-operator corrections, FP64 residuals.  r holds the
         // residual b - A x and rel = |r| / |b|.  After a correction d computed from a
-        // residual that is not yet small (rel > 1e-3), x has changed by O(|x|) and r is
+        // residual that is not yet small (see recompute_above), x has changed a lot and r is
         // recomputed from scratch with the FP64 operator.  After a later correction,
         // |d| ~ rel |x|, so the inner GMRES's own residual estimate gives the new rel and
         // r - A_32 d the new residual to within ~3e-7 rel |b| (the FP32 operator's
         // error on d): one FP64 matvec per solve instead of one per correction.
         double* corr = S->corr;
         fbim_status st = FBIM_OK;
-        cudaMemcpyAsync(S->r, S->t, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);  // x = 0
-        rel = 1.0;
+        if (warm) {
+            FBIM_TRY(true_residual(h, S->t, S->d, S->r, rel));
+        } else {
+            cudaMemcpyAsync(S->r, S->t, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);  // x = 0
+            rel = 1.0;
+        }
+        // The residual advanced with the FP32 operator errs by ~1e-6 rel_prev |b| (FP32
+        // operator error with margin); it stays below 0.05 tol |b| while rel_prev <= 5e4 tol.
+        const double recompute_above = std::max(1e-3, 5e4 * tol);
         for (int outer = 0; outer < 40 && rel > tol && iters < max_iter; ++outer) {
             // Each correction solves A d = r with the FP32 operator to a relative 1e-4
             // (or tighter when that already meets tol), within one restart cycle: the
@@ -815,7 +825,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
             iters += it;
             k_axpby<<<nb, tb, 0, h->stream>>>(n, 1.0, corr, 1.0, S->d);
             h->launches += 1;
-            if (rel > 1e-3) {
+            if (rel > recompute_above) {
                 st = true_residual(h, S->t, S->d, S->r, rel);
                 if (st != FBIM_OK) break;
             } else {
@@ -835,6 +845,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
         }
         FBIM_TRY(st);
     }
+    S->have_x = std::isfinite(rel);
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(U, S->d + N2, sizeof(double) * 3 * h->n_b, cudaMemcpyDeviceToDevice,
                                      h->stream));
     if (mu_out)
@@ -883,7 +894,7 @@ extern "C" fbim_status fbim_mobility_solve(fbim_handle h, const double* F_dev, c
     if (!h || !F_dev || !U_dev || !(tol > 0) || max_iter <= 0) return FBIM_ERR_INVALID_ARG;
     try {
         if (cudaSetDevice(h->device) != cudaSuccess) return FBIM_ERR_CUDA;
-        return fbim::mobility_solve(h, F_dev, slip_dev, tol, max_iter, U_dev, mu_dev, iters, rel_residual);
+        return fbim::mobility_solve(h, F_dev, slip_dev, tol, max_iter, U_dev, mu_dev, iters, rel_residual, false);
     } catch (...) {
         h->fail("unexpected host exception in fbim_mobility_solve");
         return FBIM_ERR_SETUP;

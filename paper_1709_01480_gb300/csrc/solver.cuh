@@ -42,6 +42,7 @@ struct Solver {
     double* lh = nullptr;       // [2 lanczos_max] Lanczos dot products / coefficients
     void* blas_ws = nullptr;    // fixed cuBLAS workspace (so captured graphs never allocate)
     double* corr = nullptr;     // [n] refinement correction
+    bool have_x = false;        // d holds the last solve's solution (a warm start can use it)
     // captured operator (precondition then saddle) per precision, [0] FP32 / [1] FP64:
     // reads gin, writes gz = P gin and gw = A gz; recaptured when the handle's layout changes
     double *gin = nullptr, *gz = nullptr, *gw = nullptr;
