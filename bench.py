@@ -54,7 +54,7 @@ BATCH_RHS = 10          # per suspension: 8 random slips + the RFD pair
 BATCH_RC = 0.504
 # GMRES iterations per solve of the chosen form on this workload (measured); the
 # CPU baseline prices a solve as this many oracle matvecs plus one residual check
-ITERS_PER_SOLVE_REF = 16
+ITERS_PER_SOLVE_REF = 24
 # DRAM bytes (read + write) per launch of each FP32 operator stage, from the ncu
 # capture summarised in profiles/ewald_matvec_dram_starfish1024.md (cutoff L/91 and
 # grid 1296^2, the split and grid tuners' choice); valid for the kernels and the

@@ -63,6 +63,12 @@ DF_HD df add(df a, df b) {
     df u = quick_two_sum(s.hi, s.lo + t.hi);
     return quick_two_sum(u.hi, u.lo + t.lo);
 }
+// Cheaper sum (one two-sum on the leading parts): error bounded relative to
+// |a| + |b| rather than |a + b|; used inside recurrences whose terms stay bounded.
+DF_HD df add_fast(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
 DF_HD df neg(df a) { return {-a.hi, -a.lo}; }
 DF_HD df sub(df a, df b) { return add(a, neg(b)); }
 DF_HD df add_f(df a, float b) {
@@ -136,7 +142,7 @@ DF_HD df exp_neg(df z) {
     const df mr = sub(n_ln2(n), z);  // -r
     df t = {kInvFact[14][0], kInvFact[14][1]};
 #pragma unroll
-    for (int k = 13; k >= 0; --k) t = add(mul(t, mr), df{kInvFact[k][0], kInvFact[k][1]});
+    for (int k = 13; k >= 0; --k) t = add_fast(mul(t, mr), df{kInvFact[k][0], kInvFact[k][1]});
     return {ldexpf(t.hi, -(int)n), ldexpf(t.lo, -(int)n)};
 }
 
@@ -156,7 +162,7 @@ DF_HD df log(df x) {
     const df v = mul(u, u);
     df s = {kInvOdd[9][0], kInvOdd[9][1]};
 #pragma unroll
-    for (int k = 8; k >= 0; --k) s = add(mul(s, v), df{kInvOdd[k][0], kInvOdd[k][1]});
+    for (int k = 8; k >= 0; --k) s = add_fast(mul(s, v), df{kInvOdd[k][0], kInvOdd[k][1]});
     const df lm = mul(mul_f(u, 2.0f), s);
     const df r = add(n_ln2((float)e), lm);
     return add_f(r, x.lo / x.hi);
@@ -182,7 +188,7 @@ DF_HD df kernel_a(const ChebDF& ce, df z) {
     const df t2 = {2.0f * t.hi, 2.0f * t.lo};
     df b1 = {0.0f, 0.0f}, b2 = {0.0f, 0.0f};
     for (int k = ce.deg; k >= 1; --k) {
-        const df b0 = add(sub(mul(t2, b1), b2), df{ce.hi[k], ce.lo[k]});
+        const df b0 = add_fast(add_fast(mul(t2, b1), neg(b2)), df{ce.hi[k], ce.lo[k]});
         b2 = b1;
         b1 = b0;
     }
