@@ -190,3 +190,36 @@ def test_fp64_rfd_step_matches_oracle(torch, fb, tiny):
     print(f"rfd step: GMRES iterations {it}, rel err of the displacement {err:.3e}")
     assert err < 1e-8
     op.close()
+
+
+def test_mixed_precision_errors_vs_oracle(torch, fb, tiny):
+    """The mixed form's error against the FP64 oracle, reported apart for body velocities,
+    rotations and Brownian displacements (FP32 operator, FP64 refinement; solves and the
+    Lanczos near field to 1e-6).  Bars: 2e-5 for U (residual 1e-6 times the saddle
+    system's amplification, below 20 here), 5e-5 for the displacement (slip and solve
+    errors add)."""
+    w, M, K, xi, grid = tiny["w"], tiny["M"], tiny["K"], tiny["xi"], tiny["grid"]
+    op = _op(fb, tiny, "fp32")
+    U, _, _, _ = op.mobility_solve(torch.tensor(w.F, device="cuda"), tol=1e-6, max_iter=400)
+    _, U_or = saddle.solve_saddle(M, K, w.F.reshape(-1))
+    U = U.cpu().numpy()
+    U_or = U_or.reshape(-1, 3)
+    e_trans = np.max(np.abs(U[:, :2] - U_or[:, :2])) / np.max(np.abs(U_or[:, :2]))
+    e_rot = np.max(np.abs(U[:, 2] - U_or[:, 2])) / np.max(np.abs(U_or[:, 2]))
+    rng = np.random.default_rng(77)
+    W_r = rng.standard_normal((w.n, 2))
+    Z = rng.standard_normal((grid, grid, 2, 2))
+    dt, kT = 1e-3, 1.0
+    s, _ = op.brownian_slip(kT=kT, dt=dt, W_r=torch.tensor(W_r, device="cuda"), Z_w=torch.tensor(Z, device="cuda"),
+                            tol=1e-6, max_iter=200)
+    zero = torch.zeros((w.n_b, 3), dtype=torch.float64, device="cuda")
+    UB, _, _, _ = op.mobility_solve(zero, s, tol=1e-6, max_iter=400)
+    dQ = dt * UB.cpu().numpy().reshape(-1)
+    s_or = brownian.slip(tiny["X"], w.Q, w.ref_nodes, w.L, xi, kT, dt, W_r, Z)
+    _, UB_or = saddle.solve_saddle(M, K, np.zeros(3 * w.n_b), s_or.reshape(-1))
+    e_brown = _rel(dQ, dt * UB_or)
+    print(f"mixed precision vs FP64 oracle: velocities {e_trans:.2e}, rotations {e_rot:.2e}, "
+          f"Brownian displacements {e_brown:.2e}")
+    assert e_trans < 2e-5 and e_rot < 2e-5
+    assert e_brown < 5e-5
+    op.close()
