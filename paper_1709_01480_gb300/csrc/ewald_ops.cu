@@ -287,40 +287,48 @@ __global__ void k_scale(int M, T twopi_L, T inv4xi2, T one_minus_eta, T pref,
 }
 
 // Back to body order: v_m = v_s[slot[m]] + v_t[tslot[m]] + R_b A_ref[j] R_b^T mu (FP64 band).
-// mu_r: the forces already rotated into their body's frame (k_gather), so the band
-// costs four FP64 FMAs per entry.
+// Alpert band (FP64): v_band_m = R_b sum_o A_ref[j][o] R_b^T mu_{b, j+o}, with mu_r the
+// forces already rotated into their body's frame (k_gather), so each band entry costs
+// four FP64 FMAs.  It depends on the forces alone, so it runs beside the wave space.
+__global__ void k_band(int N, int n_p, int band, const double* __restrict__ rot, const double* __restrict__ A,
+                       const double2* __restrict__ mu_r, double2* __restrict__ v_band) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    const int b = m / n_p, j = m - b * n_p;
+    const double c = rot[2 * b], s = rot[2 * b + 1];
+    double ax = 0, ay = 0;
+    const int B = 2 * band + 1;
+    const double2* ub = mu_r + (size_t)b * n_p;
+    const double4_32a* a4 = reinterpret_cast<const double4_32a*>(A) + (size_t)j * B;
+    for (int o = -band; o <= band; ++o) {
+        int jj = j + o;
+        jj += (jj < 0) ? n_p : 0;
+        jj -= (jj >= n_p) ? n_p : 0;
+        const double2 u = ub[jj];
+        const double4_32a a = a4[o + band];
+        ax += a.x * u.x + a.y * u.y;
+        ay += a.z * u.x + a.w * u.y;
+    }
+    v_band[m] = make_double2(c * ax - s * ay, s * ax + c * ay);
+}
+
+// Back to body order: v_m = v_s[slot[m]] + v_band_m (real space) + v_t[tslot[m]] (wave space).
 template <typename T>
-__global__ void k_finish(int N, int n_p, int band, int with_real, int with_wave, const int* __restrict__ slot,
+__global__ void k_finish(int N, int with_real, int with_wave, const int* __restrict__ slot,
                          const int* __restrict__ tslot, const typename V2<T>::type* __restrict__ v_s,
-                         const typename V2<T>::type* __restrict__ v_t, const double* __restrict__ rot,
-                         const double* __restrict__ A, const double2* __restrict__ mu_r, double2* __restrict__ v) {
+                         const typename V2<T>::type* __restrict__ v_t, const double2* __restrict__ v_band,
+                         double2* __restrict__ v) {
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= N) return;
     double vx = 0, vy = 0;
     if (with_real) {
-        typename V2<T>::type w = v_s[slot[m]];
-        vx = (double)w.x;
-        vy = (double)w.y;
-        int b = m / n_p, j = m - b * n_p;
-        const double c = rot[2 * b], s = rot[2 * b + 1];
-        double ax = 0, ay = 0;
-        const int B = 2 * band + 1;
-        const double2* ub = mu_r + (size_t)b * n_p;
-        const double4_32a* a4 = reinterpret_cast<const double4_32a*>(A) + (size_t)j * B;
-        for (int o = -band; o <= band; ++o) {
-            int jj = j + o;
-            jj += (jj < 0) ? n_p : 0;
-            jj -= (jj >= n_p) ? n_p : 0;
-            const double2 u = ub[jj];
-            const double4_32a a = a4[o + band];
-            ax += a.x * u.x + a.y * u.y;
-            ay += a.z * u.x + a.w * u.y;
-        }
-        vx += c * ax - s * ay;
-        vy += s * ax + c * ay;
+        const typename V2<T>::type w = v_s[slot[m]];
+        const double2 a = v_band[m];
+        vx = (double)w.x + a.x;
+        vy = (double)w.y + a.y;
     }
     if (with_wave) {
-        typename V2<T>::type w = v_t[tslot[m]];
+        const typename V2<T>::type w = v_t[tslot[m]];
         vx += (double)w.x;
         vy += (double)w.y;
     }
@@ -500,6 +508,7 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_t, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.v_t, N * sizeof(T2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_r, N * sizeof(double2)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.v_band, N * sizeof(double2)));
     {
         const size_t W = h->TS + h->P - 1;
         FBIM_CUDA_TRY(h, cudaMalloc(&e.ring, (size_t)h->n_tile * h->n_tile * 2 * W * W * sizeof(T)));
@@ -547,6 +556,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
         k_pair_spmv<T><<<(N + 255) / 256, 256, 0, h->aux>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
                                                             (const T2*)e.mu_s, (T2*)e.v_s);
+        k_band<<<(N + tb - 1) / tb, tb, 0, h->aux>>>(N, h->n_p, h->band, h->rot, h->band_dev, e.mu_r, e.v_band);
         FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_join, h->aux));
     }
     const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
@@ -587,11 +597,13 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         h->mark(FBIM_ST_INTERP);
     }
     if (fork) FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, real ? 1 : 0, wave ? 1 : 0, h->slot,
-                                                         h->tslot, (const T2*)e.v_s, (const T2*)e.v_t, h->rot,
-                                                         h->band_dev, e.mu_r, (double2*)v);
+    if (real && !fork)
+        k_band<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, h->rot, h->band_dev, e.mu_r, e.v_band);
+    k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, real ? 1 : 0, wave ? 1 : 0, h->slot, h->tslot,
+                                                         (const T2*)e.v_s, (const T2*)e.v_t, e.v_band,
+                                                         (double2*)v);
     h->mark(FBIM_ST_FINISH);
-    h->launches += 2 + (wave ? (e.wave_variant == 1 ? 3 : 4) : 0) + (real ? 1 : 0);
+    h->launches += 2 + (wave ? (e.wave_variant == 1 ? 3 : 4) : 0) + (real ? 2 : 0);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     h->collect();
     return FBIM_OK;
@@ -687,9 +699,8 @@ fbim_status apply_noise(fbim_handle_s* h, const double* Z, unsigned long long se
         warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.grid, e.v_t);
     else
         tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
-    k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, 0, 1, h->slot, h->tslot,
-                                                         (const T2*)e.v_s, (const T2*)e.v_t, h->Q, h->band_dev,
-                                                         (const double2*)out, (double2*)out);
+    k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, 0, 1, h->slot, h->tslot, (const T2*)e.v_s,
+                                                         (const T2*)e.v_t, e.v_band, (double2*)out);
     h->launches += 3;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;
@@ -705,6 +716,7 @@ static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.mu_t);
     cudaFree(e.v_t);
     cudaFree(e.mu_r);
+    cudaFree(e.v_band);
     cudaFree(e.ring);
     cudaFree(e.grid);
     cudaFree(e.spec);

@@ -61,6 +61,7 @@ struct EwaldBuffers {
     void* mu_t = nullptr;    // [N] T2: forces in tile-sorted order (wave space)
     void* v_t = nullptr;     // [N] T2: wave-space velocities, tile-sorted
     double2* mu_r = nullptr; // [N] forces rotated into their body's frame (body order, FP64)
+    double2* v_band = nullptr; // [N] Alpert band velocities (body order, FP64)
     T* ring = nullptr;       // [n_tile^2][2][W][W] halo rings of the tile spread (W = TS + P - 1)
     T* grid = nullptr;       // [2][M][M] real grid (component-major)
     void* spec = nullptr;    // [2][M][M/2+1] complex half spectrum
