@@ -322,6 +322,8 @@ fbim_status batched_fgmres(fbim_batch B, int op_kind, int res_kind, const double
     BTRY(cudaMemsetAsync(d, 0, sizeof(double) * N, st));
     std::vector<double> bn2;
     BSTATUS(seg_norms2(B, rhs, bn2));
+    if (op_kind == 0)  // one Gram-Schmidt pass: the second pass's coefficients stay zero
+        BTRY(cudaMemsetAsync(B->dots + (size_t)n * stride, 0, sizeof(double) * n * stride, st));
     std::vector<double> bn(n), Hh((size_t)n * m * stride), cs((size_t)n * m), sn((size_t)n * m),
         gv((size_t)n * stride), scale(n), hc((size_t)3 * n * stride), Y((size_t)n * stride);
     for (int i = 0; i < n; ++i) bn[i] = std::sqrt(bn2[i]);
@@ -359,13 +361,16 @@ fbim_status batched_fgmres(fbim_batch B, int op_kind, int res_kind, const double
         bool cycle_done = false;
         for (; k < m && total < max_iter && !cycle_done; ++k) {
             BSTATUS(run_graph(B, op_kind, B->V + (size_t)k * ld, B->Z + (size_t)k * ld, B->w));
-            for (int pass = 0; pass < 2; ++pass) {
+            // classical Gram-Schmidt: twice with the FP64 operator, once for the FP32-operator
+            // corrections of refinement (they stop at ~1e-4; the FP64 residual decides)
+            const int passes = op_kind == 0 ? 1 : 2;
+            for (int pass = 0; pass < passes; ++pass) {
                 double* dst = B->dots + (size_t)pass * n * stride;
                 k_seg_dots<<<dim3(n, k + 1), 256, 0, st>>>(B->d_off, B->V, ld, B->w, dst, stride);
                 k_seg_update<<<blocks(N, tb), tb, 0, st>>>(N, B->d_off, n, k + 1, B->V, ld, dst, stride, B->w);
             }
             k_seg_dots<<<dim3(n, 1), 256, 0, st>>>(B->d_off, B->w, 0, B->w, B->dots + (size_t)2 * n * stride, stride);
-            B->launches += 5;
+            B->launches += 1 + 2 * passes;
             BTRY(cudaMemcpyAsync(hc.data(), B->dots, sizeof(double) * hc.size(), cudaMemcpyDeviceToHost, st));
             BTRY(cudaStreamSynchronize(st));
             ++total;

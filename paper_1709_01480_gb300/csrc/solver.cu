@@ -629,6 +629,9 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
     std::vector<double> Hh((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), hc(2 * (m + 1) + 1);
     const bool use_graph = !h->timing;
     const bool fused = m + 1 <= CG_KMAX;
+    const bool two_pass = !std::is_same<T, float>::value;
+    if (fused && !two_pass)  // the second pass's coefficients stay zero
+        FBIM_CUDA_TRY(h, cudaMemsetAsync(S->hcol + (m + 1), 0, sizeof(double) * (m + 1), h->stream));
     int gin_holds = -1;  // index of the basis vector the captured operator's input holds
     if (use_graph) {
         FBIM_TRY(coarse_refresh(h));  // host-synchronising, and may reallocate: before the graph check
@@ -678,17 +681,25 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
                 FBIM_TRY(precondition<T>(h, vk, zk));
                 FBIM_TRY(saddle_apply<T>(h, zk, S->w));
             }
-            // classical Gram-Schmidt, twice
+            // classical Gram-Schmidt: twice for FP64 solves; once for the FP32-operator
+            // corrections of refinement, which stop at ~1e-4 where the basis's loss of
+            // orthogonality (far below that) does not matter, the FP64 outer residual
+            // deciding the accuracy
             if (fused) {
                 const int K = k + 1, nb = (n + CG_CHUNK - 1) / CG_CHUNK, rb = (K * 32 + 255) / 256;
                 k_cgs_dots<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->w, nb, S->cg_part);
                 k_cgs_reduce<<<rb, 256, 0, h->stream>>>(K, nb, S->cg_part, S->hcol);
-                k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol, S->w, K, nb, S->cg_part);
-                k_cgs_reduce<<<rb, 256, 0, h->stream>>>(K, nb, S->cg_part, S->hcol + (m + 1));
-                k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol + (m + 1), S->w, 0, nb,
-                                                          S->cg_part);
+                if (two_pass) {
+                    k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol, S->w, K, nb, S->cg_part);
+                    k_cgs_reduce<<<rb, 256, 0, h->stream>>>(K, nb, S->cg_part, S->hcol + (m + 1));
+                    k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol + (m + 1), S->w, 0, nb,
+                                                              S->cg_part);
+                    h->launches += 2;
+                } else {
+                    k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol, S->w, 0, nb, S->cg_part);
+                }
                 k_cgs_reduce<<<1, 32, 0, h->stream>>>(1, nb, S->cg_part, S->hcol + 2 * (m + 1));
-                h->launches += 6;
+                h->launches += 4;
                 FBIM_CUDA_TRY(h, cudaGetLastError());
             } else {
                 FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero, S->hcol, 1));
