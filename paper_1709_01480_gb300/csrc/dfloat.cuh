@@ -198,18 +198,16 @@ DF_HD df kernel_a(const ChebDF& ce, df z) {
 }
 
 // The real-space kernel pref (a I + b r r^T), a = E1(z)/2 - e^{-z}, b = e^{-z} / r^2,
-// z = xi^2 r^2, for the separation (rx, ry); about 48-bit accurate.
-DF_HD void pair_value(double rx, double ry, df xi2, df pref, const ChebDF& ce, double& xx, double& xy,
-                      double& yy) {
-    const df x = from_double(rx), y = from_double(ry);
+// z = xi^2 r^2, for the separation (x, y); about 48-bit accurate.
+DF_HD void pair_value(df x, df y, df xi2, df pref, const ChebDF& ce, df& xx, df& xy, df& yy) {
     const df x2 = mul(x, x), y2 = mul(y, y), xy2 = mul(x, y);
     const df r2 = add(x2, y2);
     const df z = mul(xi2, r2);
     const df a = kernel_a(ce, z);
     const df b = div(exp_neg(z), r2);
-    xx = to_double(mul(pref, add(a, mul(b, x2))));
-    xy = to_double(mul(pref, mul(b, xy2)));
-    yy = to_double(mul(pref, add(a, mul(b, y2))));
+    xx = mul(pref, add(a, mul(b, x2)));
+    xy = mul(pref, mul(b, xy2));
+    yy = mul(pref, add(a, mul(b, y2)));
 }
 
 }  // namespace dfl

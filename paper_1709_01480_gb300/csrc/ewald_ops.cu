@@ -63,13 +63,17 @@ template <typename T>
 __global__ void k_gather(int N, int n_p, const int* __restrict__ perm, const int* __restrict__ tperm, int want_s,
                          int want_t, const double* __restrict__ rot, const double2* __restrict__ mu,
                          typename V2<T>::type* __restrict__ mu_s, typename V2<T>::type* __restrict__ mu_t,
-                         double2* __restrict__ mu_r) {
+                         double2* __restrict__ mu_r, float4* __restrict__ mu_df) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     if (want_s) {
         double2 v = mu[perm[s]];
         mu_s[s].x = (T)v.x;
         mu_s[s].y = (T)v.y;
+        if (mu_df) {
+            const dfl::df a = dfl::from_double(v.x), b = dfl::from_double(v.y);
+            mu_df[s] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        }
         // node s in body order, rotated into its body's frame for the Alpert band
         const int b = s / n_p;
         const double c = rot[2 * b], sn = rot[2 * b + 1];
@@ -91,6 +95,9 @@ __global__ void k_gather(int N, int n_p, const int* __restrict__ perm, const int
 template <typename T> struct PairEntry;
 template <> struct __align__(16) PairEntry<float> { float xx, xy, yy; int src; };
 template <> struct __align__(16) PairEntry<double> { double xx, xy, yy; long long src; };
+// An FP64-list entry of an FP32 handle in float-float form: the leading parts and the
+// source in the first 16 bytes, the trailing parts in the second.
+struct __align__(16) PairEntryDF { float xx_hi, xy_hi, yy_hi; int src; float xx_lo, xy_lo, yy_lo, pad; };
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_pair_count(int N, int n_box, T r_c, T rc2, const int* __restrict__ perm,
@@ -193,21 +200,20 @@ __global__ void __launch_bounds__(256) k_pair_eval_rows(int N, const int* __rest
 // then the kernel in float-float arithmetic (about 48 bits, ~1e-13 relative; the FP32
 // pipes run it far faster than the FP64 pipe would).  Pairs within rounding of r_c
 // may differ from an FP64 search; their kernel value is at the Ewald tolerance.
-__global__ void __launch_bounds__(256) k_pair_from32(int N, int n_box, double r_c, const int* __restrict__ perm,
-                                                    const int* __restrict__ cell, const double2* __restrict__ off,
+__global__ void __launch_bounds__(256) k_pair_from32(int N, int n_box, dfl::df r_c, const int* __restrict__ perm,
+                                                    const int* __restrict__ cell, const float4* __restrict__ off,
                                                     const int* __restrict__ slice_start,
                                                     const int* __restrict__ row_count,
                                                     const PairEntry<float>* __restrict__ p32, dfl::df xi2,
-                                                    dfl::df pref, dfl::ChebDF ce,
-                                                    PairEntry<double>* __restrict__ p64) {
+                                                    dfl::df pref, dfl::ChebDF ce, PairEntryDF* __restrict__ p64) {
     const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (t >= N) return;
     const int sl = t >> 5, base = slice_start[sl], len = slice_start[sl + 1] - base, n = row_count[t];
     const int ct = cell[perm[t]], cxt = ct % n_box, cyt = ct / n_box;
-    const double2 ot = off[t];
+    const float4 ot = off[t];
     const size_t r0 = (size_t)base * 32 + (t & 31);
     for (int k = lane; k < len; k += 32) {
-        PairEntry<double> e;
+        PairEntryDF e;
         if (k < n) {
             const int s = p32[r0 + (size_t)k * 32].src;
             const int cs = cell[perm[s]];
@@ -216,37 +222,136 @@ __global__ void __launch_bounds__(256) k_pair_from32(int N, int n_box, double r_
             dx -= (dx > 1) ? n_box : 0;
             dy += (dy < -1) ? n_box : 0;
             dy -= (dy > 1) ? n_box : 0;
-            const double2 os = off[s];
-            const double rx = (ot.x - dx * r_c) - os.x, ry = (ot.y - dy * r_c) - os.y;
-            dfl::pair_value(rx, ry, xi2, pref, ce, e.xx, e.xy, e.yy);
-            e.src = s;
+            const float4 os = off[s];
+            // (o_t - d r_c) - o_s with d in {-1, 0, 1}: d r_c is exact
+            dfl::df rx = {ot.x, ot.y}, ry = {ot.z, ot.w};
+            if (dx) rx = dfl::sub(rx, dx > 0 ? r_c : dfl::neg(r_c));
+            if (dy) ry = dfl::sub(ry, dy > 0 ? r_c : dfl::neg(r_c));
+            rx = dfl::sub(rx, dfl::df{os.x, os.y});
+            ry = dfl::sub(ry, dfl::df{os.z, os.w});
+            dfl::df xx, xy, yy;
+            dfl::pair_value(rx, ry, xi2, pref, ce, xx, xy, yy);
+            e = PairEntryDF{xx.hi, xy.hi, yy.hi, s, xx.lo, xy.lo, yy.lo, 0.0f};
         } else {
-            e.xx = e.xy = e.yy = 0.0;
-            e.src = t;
+            e = PairEntryDF{0.0f, 0.0f, 0.0f, t, 0.0f, 0.0f, 0.0f, 0.0f};
         }
         p64[r0 + (size_t)k * 32] = e;
     }
 }
 
+// Float-float copy of the FP64 cell offsets, one conversion per node.
+__global__ void k_off_df(int N, const double2* __restrict__ off, float4* __restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= N) return;
+    const double2 o = off[s];
+    const dfl::df x = dfl::from_double(o.x), y = dfl::from_double(o.y);
+    out[s] = make_float4(x.hi, x.lo, y.hi, y.lo);
+}
+
+// One pair-list entry read with an evict-first hint: the list is streamed once per
+// product and is larger than L2, where the gathered densities should stay.
+__device__ __forceinline__ PairEntry<float> ld_entry(const PairEntry<float>* p) {
+    const int4 v = __ldcs(reinterpret_cast<const int4*>(p));
+    PairEntry<float> e;
+    e.xx = __int_as_float(v.x);
+    e.xy = __int_as_float(v.y);
+    e.yy = __int_as_float(v.z);
+    e.src = v.w;
+    return e;
+}
+__device__ __forceinline__ PairEntry<double> ld_entry(const PairEntry<double>* p) {
+    const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    PairEntry<double> e;
+    e.xx = a.x;
+    e.xy = a.y;
+    e.yy = b.x;
+    e.src = __double_as_longlong(b.y);
+    return e;
+}
+
+// v_s[t] = sum_k pairs[t][k] mu_s[src]: one thread per row, the entries of a row
+// taken U at a time (U independent list loads, then U independent gathers) so
+// that each thread keeps several memory requests in flight; the products are
+// accumulated in the row's k order either way.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pair_spmv(int N, const int* __restrict__ slice_start,
                                                   const PairEntry<T>* __restrict__ pairs,
                                                   const typename V2<T>::type* __restrict__ mu_s,
                                                   typename V2<T>::type* __restrict__ v_s) {
+    constexpr int U = sizeof(T) == 4 ? 8 : 4;
+    using T2 = typename V2<T>::type;
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
     const int sl = t >> 5, lane = t & 31;
     const int base = slice_start[sl], len = slice_start[sl + 1] - base;
     const PairEntry<T>* row = pairs + (size_t)base * 32 + lane;
     T ax = 0, ay = 0;
-    for (int k = 0; k < len; ++k) {
-        PairEntry<T> e = row[(size_t)k * 32];
-        typename V2<T>::type m = mu_s[e.src];
+    int k = 0;
+    for (; k + U <= len; k += U) {
+        PairEntry<T> e[U];
+        T2 m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) e[u] = ld_entry(row + (size_t)(k + u) * 32);
+#pragma unroll
+        for (int u = 0; u < U; ++u) m[u] = __ldg(mu_s + e[u].src);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            ax = fma(e[u].xx, m[u].x, fma(e[u].xy, m[u].y, ax));
+            ay = fma(e[u].xy, m[u].x, fma(e[u].yy, m[u].y, ay));
+        }
+    }
+    for (; k < len; ++k) {
+        const PairEntry<T> e = ld_entry(row + (size_t)k * 32);
+        const T2 m = __ldg(mu_s + e.src);
         ax = fma(e.xx, m.x, fma(e.xy, m.y, ax));
         ay = fma(e.xy, m.x, fma(e.yy, m.y, ay));
     }
     v_s[t].x = ax;
     v_s[t].y = ay;
+}
+
+// The FP64 real-space product of an FP32 handle on its float-float list: products
+// and sums in float-float (about 2^-46 per operation, so ~1e-13 on a row sum),
+// the sum rounded to FP64 once per row.  Same row order and U-wide batching as
+// k_pair_spmv; nothing on the FP64 pipe but that final conversion.
+__global__ void __launch_bounds__(256) k_pair_spmv_df(int N, const int* __restrict__ slice_start,
+                                                     const PairEntryDF* __restrict__ pairs,
+                                                     const float4* __restrict__ mu_df, double2* __restrict__ v_s) {
+    constexpr int U = 4;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const int sl = t >> 5, lane = t & 31;
+    const int base = slice_start[sl], len = slice_start[sl + 1] - base;
+    const PairEntryDF* row = pairs + (size_t)base * 32 + lane;
+    dfl::df ax = {0.0f, 0.0f}, ay = {0.0f, 0.0f};
+    for (int k = 0; k < len; k += U) {
+        int4 hi[U];
+        float4 lo[U];
+        float4 m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (k + u < len) {
+                const int4* q = reinterpret_cast<const int4*>(row + (size_t)(k + u) * 32);
+                hi[u] = __ldcs(q);
+                lo[u] = __ldcs(reinterpret_cast<const float4*>(q + 1));
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (k + u < len) m[u] = __ldg(mu_df + hi[u].w);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (k + u < len) {
+                const dfl::df xx = {__int_as_float(hi[u].x), lo[u].x}, xy = {__int_as_float(hi[u].y), lo[u].y},
+                              yy = {__int_as_float(hi[u].z), lo[u].z};
+                const dfl::df mx = {m[u].x, m[u].y}, my = {m[u].z, m[u].w};
+                ax = dfl::add_fast(dfl::add_fast(ax, dfl::mul(xy, my)), dfl::mul(xx, mx));
+                ay = dfl::add_fast(dfl::add_fast(ay, dfl::mul(yy, my)), dfl::mul(xy, mx));
+            }
+        }
+    }
+    v_s[t] = make_double2(dfl::to_double(ax), dfl::to_double(ay));
 }
 
 // ---------------------------------------------------------------------------
@@ -370,6 +475,12 @@ static fbim_status build_pairs_from32(fbim_handle_s* h) {
     }
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.slice_start, f.slice_start, sizeof(int) * (n_slice + 1),
                                      cudaMemcpyDeviceToDevice, h->stream));
+    if (!e.off_df) {
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.off_df, (size_t)N * sizeof(float4)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_df, (size_t)N * sizeof(float4)));
+        ++h->layout_version;
+    }
+    k_off_df<<<(N + 255) / 256, 256, 0, h->stream>>>(N, (const double2*)e.off, e.off_df);
     dfl::ChebDF cdf;
     cdf.deg = h->cheb64.deg;
     for (int k = 0; k <= cdf.deg; ++k) {
@@ -381,12 +492,13 @@ static fbim_status build_pairs_from32(fbim_handle_s* h) {
     cdf.s_hi = sc.hi;
     cdf.s_lo = sc.lo;
     k_pair_from32<<<(unsigned)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(
-        N, h->n_box, h->r_c, h->perm, h->cell, (const double2*)e.off, f.slice_start, f.row_count,
+        N, h->n_box, dfl::from_double(h->r_c), h->perm, h->cell, e.off_df, f.slice_start, f.row_count,
         (const PairEntry<float>*)f.pairs, dfl::from_double(h->xi * h->xi),
-        dfl::from_double(1.0 / (4.0 * M_PI * h->eta)), cdf, (PairEntry<double>*)e.pairs);
-    h->launches += 1;
+        dfl::from_double(1.0 / (4.0 * M_PI * h->eta)), cdf, (PairEntryDF*)e.pairs);
+    h->launches += 2;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     e.n_padded = f.n_padded;
+    e.pairs_df = true;
     e.pairs_ready = true;
     e.pairs_geom = h->geom_version;
     return FBIM_OK;
@@ -426,6 +538,7 @@ static fbim_status build_pairs(fbim_handle_s* h) {
     h->launches += 4;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     e.n_padded = (long long)total * 32;
+    e.pairs_df = false;
     e.pairs_ready = true;
     e.pairs_geom = h->geom_version;
     return FBIM_OK;
@@ -440,6 +553,15 @@ fbim_status refresh_offsets(fbim_handle_s* h) {
                                                              h->n_box, h->r_c, h->h, (T2*)e.off, e.tbase,
                                                              (T2*)e.tfrac);
     h->launches += 1;
+    if constexpr (std::is_same<T, double>::value) {
+        if (e.wtab) {
+            const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
+            const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
+            node_weights<double>(h->stream, h->N, tg, alpha * h->h * h->h, 2.0 * h->xi * h->xi / (M_PI * h->eta_s),
+                                 e.tfrac, e.wtab);
+            h->launches += 1;
+        }
+    }
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return build_pairs<T>(h);
 }
@@ -468,8 +590,8 @@ static fbim_status autotune_wave(fbim_handle_s* h) {
             cudaEventRecord(ev[0], h->stream);
             if (variant == 1) {
                 cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream);
-                warp_spread<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.mu_t, e.grid);
-                warp_interp<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.grid, e.v_t);
+                warp_spread<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.mu_t, e.grid);
+                warp_interp<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
             } else {
                 tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
                 tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
@@ -514,6 +636,7 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
         FBIM_CUDA_TRY(h, cudaMalloc(&e.ring, (size_t)h->n_tile * h->n_tile * 2 * W * W * sizeof(T)));
     }
     FBIM_CUDA_TRY(h, cudaMalloc(&e.grid, 2 * M * M * sizeof(T)));
+    if (std::is_same<T, double>::value) FBIM_CUDA_TRY(h, cudaMalloc(&e.wtab, N * 2 * h->P * sizeof(T)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.spec, 2 * M * Mh * sizeof(C)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, scan_storage((int)n_slice) * sizeof(int)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.row_count, (n_slice * 33 + 1) * sizeof(int)));
@@ -536,6 +659,18 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     return FBIM_OK;
 }
 
+// v_s = (real-space pair list) mu_s, on the plain or the float-float list
+template <typename T>
+static void pair_product(cudaStream_t st, int N, EwaldBuffers<T>& e, bool df) {
+    using T2 = typename V2<T>::type;
+    if (df)
+        k_pair_spmv_df<<<(N + 63) / 64, 64, 0, st>>>(N, e.slice_start, (const PairEntryDF*)e.pairs, e.mu_df,
+                                                     (double2*)e.v_s);
+    else
+        k_pair_spmv<T><<<(N + 63) / 64, 64, 0, st>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
+                                                     (const T2*)e.mu_s, (T2*)e.v_s);
+}
+
 template <typename T>
 fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int which) {
     FBIM_TRY(ensure_ewald<T>(h));
@@ -545,8 +680,10 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     const int N = h->N, tb = 256;
     const bool real = which & 1, wave = which & 2;
     h->mark_begin();
+    const bool df = real && e.pairs_df;  // float-float FP64 list (FP32 handles)
     k_gather<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->perm, h->tperm, real, wave, h->rot,
-                                                         (const double2*)mu, (T2*)e.mu_s, (T2*)e.mu_t, e.mu_r);
+                                                         (const double2*)mu, (T2*)e.mu_s, (T2*)e.mu_t, e.mu_r,
+                                                         df ? e.mu_df : nullptr);
     h->mark(FBIM_ST_GATHER);
     // real space on the auxiliary stream, concurrent with the wave space (sequential
     // while the stage timers run, so that each stage is timed alone)
@@ -554,8 +691,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     if (fork) {
         FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
         FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-        k_pair_spmv<T><<<(N + 255) / 256, 256, 0, h->aux>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
-                                                            (const T2*)e.mu_s, (T2*)e.v_s);
+        pair_product<T>(h->aux, N, e, df);
         k_band<<<(N + tb - 1) / tb, tb, 0, h->aux>>>(N, h->n_p, h->band, h->rot, h->band_dev, e.mu_r, e.v_band);
         FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_join, h->aux));
     }
@@ -567,7 +703,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         const size_t M = h->M, Mh = h->M / 2 + 1;
         if (e.wave_variant == 1) {
             FBIM_CUDA_TRY(h, cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream));
-            warp_spread<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.mu_t, e.grid);
+            warp_spread<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.mu_t, e.grid);
         } else {
             tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
         }
@@ -585,13 +721,12 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         h->mark(FBIM_ST_FFT_I);
     }
     if (real && !fork) {
-        k_pair_spmv<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
-                                                               (const T2*)e.mu_s, (T2*)e.v_s);
+        pair_product<T>(h->stream, N, e, df);
         h->mark(FBIM_ST_PAIRS);
     }
     if (wave) {
         if (e.wave_variant == 1)
-            warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.grid, e.v_t);
+            warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
         else
             tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
         h->mark(FBIM_ST_INTERP);
@@ -696,7 +831,7 @@ fbim_status apply_noise(fbim_handle_s* h, const double* Z, unsigned long long se
     const T ah2 = (T)(alpha * h->h * h->h);
     const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
     if (e.wave_variant == 1)
-        warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.grid, e.v_t);
+        warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
     else
         tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
     k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, 0, 1, h->slot, h->tslot, (const T2*)e.v_s,
@@ -719,8 +854,11 @@ static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.v_band);
     cudaFree(e.ring);
     cudaFree(e.grid);
+    cudaFree(e.wtab);
     cudaFree(e.spec);
     cudaFree(e.pairs);
+    cudaFree(e.off_df);
+    cudaFree(e.mu_df);
     cudaFree(e.slice_start);
     cudaFree(e.row_count);
     if (e.plan_f) cufftDestroy(e.plan_f);

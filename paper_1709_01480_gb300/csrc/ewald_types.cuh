@@ -116,12 +116,16 @@ void tile_spread(cudaStream_t st, const TileGeom& tg, T a, T g0, const int* tsta
 template <typename T>
 void tile_interp(cudaStream_t st, const TileGeom& tg, T a, T g0, const int* tstart, const int2* tbase,
                  const void* tfrac, const T* grid, void* v_t);
-// Warp-per-node variants (grid zeroed by the caller before warp_spread).
+// Warp-per-node variants (grid zeroed by the caller before warp_spread); wtab: the
+// node window weights of node_weights, or null (computed per lane).
 template <typename T>
 void warp_spread(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const int2* tbase, const void* tfrac,
-                 const void* mu_t, T* grid);
+                 const T* wtab, const void* mu_t, T* grid);
 template <typename T>
 void warp_interp(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const int2* tbase, const void* tfrac,
-                 const T* grid, void* v_t);
+                 const T* wtab, const T* grid, void* v_t);
+// wtab[N][2][P]: every node's column and (times g0) row window weights.  One launch.
+template <typename T>
+void node_weights(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const void* tfrac, T* wtab);
 
 }  // namespace fbim

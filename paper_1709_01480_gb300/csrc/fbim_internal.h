@@ -64,6 +64,7 @@ struct EwaldBuffers {
     double2* v_band = nullptr; // [N] Alpert band velocities (body order, FP64)
     T* ring = nullptr;       // [n_tile^2][2][W][W] halo rings of the tile spread (W = TS + P - 1)
     T* grid = nullptr;       // [2][M][M] real grid (component-major)
+    T* wtab = nullptr;       // [N][2][P] node window weights, tile-sorted (FP64 buffers only)
     void* spec = nullptr;    // [2][M][M/2+1] complex half spectrum
     cufftHandle plan_f = 0;  // R2C / D2Z, batch 2
     cufftHandle plan_i = 0;  // C2R / Z2D, batch 2
@@ -76,6 +77,11 @@ struct EwaldBuffers {
     long long n_padded = 0;      // stored entries including padding
     bool pairs_ready = false;
     unsigned long long pairs_geom = ~0ull;  // geometry version the pair list was built for
+    // FP64 list of an FP32 handle, derived from its FP32 list: float-float entries
+    // (PairEntryDF), with float-float copies of the cell offsets and of the forces
+    bool pairs_df = false;
+    float4* off_df = nullptr;    // [N] (x hi, x lo, y hi, y lo), cell-sorted
+    float4* mu_df = nullptr;     // [N] forces, cell-sorted
     int wave_variant = 1;        // 0: tile kernels (shared memory), 1: warp-per-node kernels
     float variant_ms[2] = {0, 0};  // autotuner timings of spread + interp per variant
     bool ready = false;

@@ -22,6 +22,7 @@
 #include <cusolverDn.h>
 
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 #include <vector>
 
@@ -179,52 +180,68 @@ __global__ void k_check_finite(int n, const double* __restrict__ x, int* __restr
 }
 
 // ---------------------------------------------------------------------------
-// Classical Gram-Schmidt (twice) for the Arnoldi step, fused: dots of w with the
-// K basis vectors, w -= V h with the next pass's dots (or |w|^2) in the same
-// sweep.  Each block owns CG_CHUNK consecutive entries (strided per thread for
-// coalescing) and writes one partial per dot; k_cgs_reduce sums the partials in
-// a fixed order, so the result does not depend on scheduling.
+// The Arnoldi step on the device.  *kd is the index k of the newest basis vector,
+// the one the step expands, so that one captured graph serves every k.  Row k of
+// the step history holds the step's Gram-Schmidt coefficients (first pass at 0,
+// second at m+1), |w|^2 at 2(m+1) and 1/|w| at 2(m+1)+1; the norm kernel also
+// copies the row to mapped host memory, where the host reads it after the step's
+// event.  Classical Gram-Schmidt, fused: dots of w with the K = k+1 basis vectors,
+// then w -= V h with the next pass's dots (or |w|^2) in the same sweep.  Each
+// block owns CG_CHUNK consecutive entries (strided per thread for coalescing) and
+// writes one partial per dot; the reductions sum the partials in a fixed order,
+// so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-constexpr int CG_TB = 256, CG_EPT = 4, CG_CHUNK = CG_TB * CG_EPT, CG_KMAX = 64;
+constexpr int CG_TB = 256, CG_EPT = 4, CG_CHUNK = CG_TB * CG_EPT, CG_KCH = 64;
+
+__host__ __device__ inline int hist_stride(int m) { return 2 * (m + 1) + 2; }
 
 __device__ __forceinline__ double warp_sum(double s) {
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
-// part[j * nb + b] = sum over block b's entries of V_j w  (j < K), or of w w (K = 0 -> one slot)
+// part[j * nb + b] = sum over block b's entries of V_j w (j < K), or of w w (K = 0 -> one
+// slot); CG_KCH dots at a time through shared memory
 __device__ __forceinline__ void cgs_block_dots(int n, int K, const double* __restrict__ V, int ld, const double* wv,
                                                int nb, double* __restrict__ part, double (*red)[8]) {
     const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i0 = b * CG_CHUNK + threadIdx.x;
     const int KK = K > 0 ? K : 1;
-    for (int j = 0; j < KK; ++j) {
-        double sacc = 0.0;
-        if (K > 0) {
-            const double* v = V + (size_t)j * ld;
+    for (int j0 = 0; j0 < KK; j0 += CG_KCH) {
+        const int j1 = min(KK, j0 + CG_KCH);
+        for (int j = j0; j < j1; ++j) {
+            double sacc = 0.0;
+            if (K > 0) {
+                const double* v = V + (size_t)j * ld;
 #pragma unroll
-            for (int e = 0; e < CG_EPT; ++e) {
-                const int i = i0 + e * CG_TB;
-                if (i < n) sacc = fma(v[i], wv[e], sacc);
+                for (int e = 0; e < CG_EPT; ++e) {
+                    const int i = i0 + e * CG_TB;
+                    if (i < n) sacc = fma(v[i], wv[e], sacc);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < CG_EPT; ++e) sacc = fma(wv[e], wv[e], sacc);
             }
-        } else {
-#pragma unroll
-            for (int e = 0; e < CG_EPT; ++e) sacc = fma(wv[e], wv[e], sacc);
+            sacc = warp_sum(sacc);
+            if (lane == 0) red[j - j0][warp] = sacc;
         }
-        sacc = warp_sum(sacc);
-        if (lane == 0) red[j][warp] = sacc;
-    }
-    __syncthreads();
-    for (int j = threadIdx.x; j < KK; j += CG_TB) {
-        double t = 0.0;
-        for (int q = 0; q < CG_TB / 32; ++q) t += red[j][q];
-        part[(size_t)j * nb + b] = t;
+        __syncthreads();
+        for (int j = j0 + threadIdx.x; j < j1; j += CG_TB) {
+            double t = 0.0;
+            for (int q = 0; q < CG_TB / 32; ++q) t += red[j - j0][q];
+            part[(size_t)j * nb + b] = t;
+        }
+        __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(CG_TB) k_cgs_dots(int n, int K, const double* __restrict__ V, int ld,
-                                                    const double* __restrict__ w, int nb, double* __restrict__ part) {
-    __shared__ double red[CG_KMAX][8];
+// first pass: partial dots of w with V_0..V_k; also stores the step's preconditioned
+// vector z as Z_k
+__global__ void __launch_bounds__(CG_TB) k_cgs_dots(int n, const int* __restrict__ kd, const double* __restrict__ V,
+                                                    int ld, const double* __restrict__ w, const double* __restrict__ z,
+                                                    double* __restrict__ Z, int nb, double* __restrict__ part) {
+    __shared__ double red[CG_KCH][8];
+    const int k = *kd;
     double wv[CG_EPT];
     const int i0 = blockIdx.x * CG_CHUNK + threadIdx.x;
 #pragma unroll
@@ -232,17 +249,23 @@ __global__ void __launch_bounds__(CG_TB) k_cgs_dots(int n, int K, const double* 
         const int i = i0 + e * CG_TB;
         wv[e] = i < n ? w[i] : 0.0;
     }
-    cgs_block_dots(n, K, V, ld, wv, nb, part, red);
+    cgs_block_dots(n, k + 1, V, ld, wv, nb, part, red);
+#pragma unroll
+    for (int e = 0; e < CG_EPT; ++e) {
+        const int i = i0 + e * CG_TB;
+        if (i < n) Z[(size_t)k * ld + i] = z[i];
+    }
 }
 
-// w -= sum_{j<K} V_j h_j, then the partial dots of the new w with V (K2 = K) or |w|^2 (K2 = 0)
-__global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, int K, const double* __restrict__ V, int ld,
-                                                      const double* __restrict__ h, double* __restrict__ w, int K2,
-                                                      int nb, double* __restrict__ part) {
-    __shared__ double red[CG_KMAX][8];
-    __shared__ double hs[CG_KMAX];
-    for (int j = threadIdx.x; j < K; j += CG_TB) hs[j] = h[j];
-    __syncthreads();
+// w -= sum_{j<=k} V_j h_j with h the history row's pass at offset off, then the partial
+// dots of the new w with V (dots = 1) or |w|^2 (dots = 0)
+__global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, const int* __restrict__ kd, const double* __restrict__ V,
+                                                      int ld, const double* __restrict__ hist, int m, int off,
+                                                      double* __restrict__ w, int dots, int nb,
+                                                      double* __restrict__ part) {
+    __shared__ double red[CG_KCH][8];
+    const int k = *kd, K = k + 1;
+    const double* hrow = hist + (size_t)k * hist_stride(m) + off;
     double wv[CG_EPT];
     const int i0 = blockIdx.x * CG_CHUNK + threadIdx.x;
 #pragma unroll
@@ -252,7 +275,7 @@ __global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, int K, const double
     }
     for (int j = 0; j < K; ++j) {
         const double* v = V + (size_t)j * ld;
-        const double hj = hs[j];
+        const double hj = hrow[j];
 #pragma unroll
         for (int e = 0; e < CG_EPT; ++e) {
             const int i = i0 + e * CG_TB;
@@ -264,27 +287,61 @@ __global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, int K, const double
         const int i = i0 + e * CG_TB;
         if (i < n) w[i] = wv[e];
     }
-    cgs_block_dots(n, K2, V, ld, wv, nb, part, red);
+    cgs_block_dots(n, dots ? K : 0, V, ld, wv, nb, part, red);
 }
 
-// out[j] = sum_b part[j * nb + b], one warp per j (fixed order)
-__global__ void k_cgs_reduce(int K, int nb, const double* __restrict__ part, double* __restrict__ out) {
+// history row k, entries off + j = sum_b part[j * nb + b] for j <= k, one warp per j (fixed order)
+__global__ void k_cgs_reduce(const int* __restrict__ kd, int m, int nb, const double* __restrict__ part,
+                             double* __restrict__ hist, int off) {
+    const int k = *kd;
     const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (j >= K) return;
+    if (j > k) return;
     double s = 0.0;
     for (int b = lane; b < nb; b += 32) s += part[(size_t)j * nb + b];
     s = warp_sum(s);
-    if (lane == 0) out[j] = s;
+    if (lane == 0) hist[(size_t)k * hist_stride(m) + off + j] = s;
 }
 
-// y = a x, and a copy into y2 when given
-__global__ void k_scale_copy(int n, double a, const double* __restrict__ x, double* __restrict__ y,
-                             double* __restrict__ y2) {
+// One warp: |w|^2 and 1/|w| (0 when w = 0) into history row k, the row to the host
+// mirror, then k + 1 into *kd.
+__global__ void k_cgs_norm(int m, int nb, const double* __restrict__ part, int* __restrict__ kd,
+                           double* __restrict__ hist, double* __restrict__ hist_host) {
+    const int k = *kd, lane = threadIdx.x, hs = hist_stride(m);
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += part[b];
+    s = warp_sum(s);
+    double* row = hist + (size_t)k * hs;
+    if (lane == 0) {
+        row[2 * (m + 1)] = s;
+        row[2 * (m + 1) + 1] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    }
+    __syncwarp();
+    for (int i = lane; i < hs; i += 32) hist_host[(size_t)k * hs + i] = row[i];
+    __syncwarp();
+    if (lane == 0) *kd = k + 1;
+}
+
+// V_{k+1} = w / |w| (k + 1 = *kd after the norm kernel), also into the step input y2
+__global__ void k_normalize(int n, const int* __restrict__ kd, const double* __restrict__ hist, int m,
+                            const double* __restrict__ w, double* __restrict__ V, int ld, double* __restrict__ y2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double v = a * x[i];
-    y[i] = v;
-    if (y2) y2[i] = v;
+    const int k1 = *kd;
+    const double a = hist[(size_t)(k1 - 1) * hist_stride(m) + 2 * (m + 1) + 1];
+    const double v = a * w[i];
+    V[(size_t)k1 * ld + i] = v;
+    y2[i] = v;
+}
+
+// V_0 = a w, also into the step input y2; *kd = 0
+__global__ void k_start(int n, double a, const double* __restrict__ w, double* __restrict__ V,
+                        double* __restrict__ y2, int* __restrict__ kd) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *kd = 0;
+    if (i >= n) return;
+    const double v = a * w[i];
+    V[i] = v;
+    y2[i] = v;
 }
 
 // ---------------------------------------------------------------------------
@@ -461,9 +518,19 @@ fbim_status setup_solver(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&S->d, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->t, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->corr, sizeof(double) * n));
-    FBIM_CUDA_TRY(h, cudaMalloc(&S->hcol, sizeof(double) * (2 * (m + 1) + 1)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->hcol, sizeof(double) * (m + 1)));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gin, sizeof(double) * n));
-    FBIM_CUDA_TRY(h, cudaMalloc(&S->cg_part, sizeof(double) * CG_KMAX * ((n + CG_CHUNK - 1) / CG_CHUNK)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->cg_part, sizeof(double) * (m + 1) * ((n + CG_CHUNK - 1) / CG_CHUNK)));
+    // device history; the host mirror has room for y after its rows
+    const size_t hist_bytes = sizeof(double) * (m + 1) * hist_stride((int)m);
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->kd, sizeof(int)));
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(S->kd, 0, sizeof(int), h->stream));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->hist, hist_bytes));
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(S->hist, 0, hist_bytes, h->stream));
+    FBIM_CUDA_TRY(h, cudaHostAlloc(&S->hist_host, hist_bytes + sizeof(double) * (m + 1), cudaHostAllocMapped));
+    memset(S->hist_host, 0, hist_bytes + sizeof(double) * (m + 1));
+    FBIM_CUDA_TRY(h, cudaHostGetDevicePointer(&S->hist_map, S->hist_host, 0));
+    for (cudaEvent_t& ev : S->ev_step) FBIM_CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gz, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gw, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMemsetAsync(S->gin, 0, sizeof(double) * n, h->stream));
@@ -492,8 +559,11 @@ void free_solver(fbim_handle_s* h) {
                     (void*)S->Gd64, (void*)S->G32, (void*)S->Gd32, (void*)S->V, (void*)S->Z, (void*)S->w,
                     (void*)S->r, (void*)S->d, (void*)S->t, (void*)S->hcol, S->zbuf, S->gbuf, (void*)S->lz,
                     (void*)S->lh, (void*)S->rfd, S->blas_ws, (void*)S->corr, (void*)S->gin, (void*)S->gz,
-                    (void*)S->gw, (void*)S->cg_part})
+                    (void*)S->gw, (void*)S->cg_part, (void*)S->kd, (void*)S->hist})
         cudaFree(p);
+    if (S->hist_host) cudaFreeHost(S->hist_host);
+    for (cudaEvent_t ev : S->ev_step)
+        if (ev) cudaEventDestroy(ev);
     for (cudaGraphExec_t g : S->op_graph)
         if (g) cudaGraphExecDestroy(g);
     if (S->cap) cudaStreamDestroy(S->cap);
@@ -559,10 +629,41 @@ static fbim_status precondition(fbim_handle_s* h, const double* in, double* out)
     return FBIM_OK;
 }
 
-// The Krylov step's operator, z = P v and w = A z, captured once as a CUDA graph on
-// fixed buffers (gin -> gz, gw) so that each step costs one graph launch instead of
-// some twenty kernel, cuFFT and cuBLAS launches.  Recaptured when a buffer the
-// launches hold by pointer was reallocated (layout_version).
+// One Arnoldi step on the device (see k_cgs_dots): z = P v_k into gz and Z_k,
+// w = A z into gw, orthogonalised against V_0..V_k (classical Gram-Schmidt: twice
+// for FP64 solves; once for the FP32-operator corrections of refinement, which
+// stop at ~1e-4, where the basis's loss of orthogonality, far below that, does not
+// matter, the FP64 outer residual deciding the accuracy), then V_{k+1} = w / |w|,
+// also into gin, the next step's input.
+template <typename T>
+static fbim_status arnoldi_step(fbim_handle_s* h) {
+    Solver* S = h->solver;
+    const int n = S->n, m = S->restart, ld = S->ld;
+    const int nb = (n + CG_CHUNK - 1) / CG_CHUNK, rb = ((m + 1) * 32 + 255) / 256;
+    const bool two_pass = !std::is_same<T, float>::value;
+    FBIM_TRY(precondition<T>(h, S->gin, S->gz));
+    FBIM_TRY(saddle_apply<T>(h, S->gz, S->gw));
+    const cudaStream_t st = h->stream;
+    k_cgs_dots<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->gw, S->gz, S->Z, nb, S->cg_part);
+    k_cgs_reduce<<<rb, 256, 0, st>>>(S->kd, m, nb, S->cg_part, S->hist, 0);
+    if (two_pass) {
+        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, 0, S->gw, 1, nb, S->cg_part);
+        k_cgs_reduce<<<rb, 256, 0, st>>>(S->kd, m, nb, S->cg_part, S->hist, m + 1);
+        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, m + 1, S->gw, 0, nb, S->cg_part);
+    } else {
+        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, 0, S->gw, 0, nb, S->cg_part);
+    }
+    k_cgs_norm<<<1, 32, 0, st>>>(m, nb, S->cg_part, S->kd, S->hist, S->hist_map);
+    k_normalize<<<(n + 255) / 256, 256, 0, st>>>(n, S->kd, S->hist, m, S->gw, S->V, ld, S->gin);
+    h->launches += two_pass ? 7 : 5;
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    return FBIM_OK;
+}
+
+// The Arnoldi step captured once as a CUDA graph on fixed buffers, so that each
+// step costs one graph launch instead of some thirty kernel, cuFFT and cuBLAS
+// launches.  Recaptured when a buffer the launches hold by pointer was reallocated
+// (layout_version).
 template <typename T>
 static fbim_status op_graph(fbim_handle_s* h) {
     Solver* S = h->solver;
@@ -583,8 +684,7 @@ static fbim_status op_graph(fbim_handle_s* h) {
     h->timing = false;
     FBIM_CUDA_TRY(h, cudaStreamBeginCapture(S->cap, cudaStreamCaptureModeThreadLocal));
     bind_stream(h, S->cap);
-    fbim_status st = precondition<T>(h, S->gin, S->gz);
-    if (st == FBIM_OK) st = saddle_apply<T>(h, S->gz, S->gw);
+    fbim_status st = arnoldi_step<T>(h);
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(S->cap, &graph);
     bind_stream(h, orig);
@@ -595,14 +695,14 @@ static fbim_status op_graph(fbim_handle_s* h) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
         if (st != FBIM_OK) return st;
-        h->fail(std::string("operator capture: ") + cudaGetErrorString(ee));
+        h->fail(std::string("Arnoldi step capture: ") + cudaGetErrorString(ee));
         return FBIM_ERR_CUDA;
     }
     const cudaError_t ie = cudaGraphInstantiate(&S->op_graph[k], graph, 0);
     cudaGraphDestroy(graph);
     if (ie != cudaSuccess) {
         S->op_graph[k] = nullptr;
-        h->fail(std::string("operator graph instantiate: ") + cudaGetErrorString(ie));
+        h->fail(std::string("Arnoldi step graph instantiate: ") + cudaGetErrorString(ie));
         return FBIM_ERR_CUDA;
     }
     S->op_version[k] = h->layout_version;
@@ -612,127 +712,94 @@ static fbim_status op_graph(fbim_handle_s* h) {
 // Restarted flexible GMRES for A x = b with the operator and preconditioner in precision T.
 // x holds the initial guess on entry.  Returns the iteration count and the estimated
 // relative residual |b - A x| / |b| of the last cycle.
+//
+// The host keeps the Hessenberg matrix and its Givens rotations and reads each
+// step's coefficients from the mapped history row after the step's event.  Step
+// k+1 is queued before step k is read, so that the device does not wait for the
+// host between steps, except where step k is predicted to converge (the last ratio
+// of residual estimates carried one step on lands within 3 tol): a step run past
+// convergence costs far more than the wait it saves.  A step queued past the end
+// only writes V_{k+2}, Z_{k+1} and history row k+1, which the update x += Z y does
+// not read.
+// bnorm_in > 0 is |b| when the caller knows it (each norm costs a host sync).
 template <typename T>
 static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double tol, int max_iter, int& iters,
-                          double& rel_est, bool x_is_zero = false, bool trust_estimate = false) {
+                          double& rel_est, bool x_is_zero = false, bool trust_estimate = false,
+                          double bnorm_in = 0.0) {
     Solver* S = h->solver;
-    const int n = S->n, m = S->restart, ld = S->ld;
+    const int n = S->n, m = S->restart, ld = S->ld, hs = hist_stride(m);
     cublasHandle_t B = S->blas;
-    double bnorm = 0;
-    FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, b, &bnorm));
+    double bnorm = bnorm_in;
+    if (!(bnorm > 0.0)) FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, b, &bnorm));
     iters = 0;
     rel_est = 0;
     if (bnorm == 0) {
         FBIM_CUDA_TRY(h, cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
         return FBIM_OK;
     }
-    std::vector<double> Hh((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1), hc(2 * (m + 1) + 1);
+    std::vector<double> Hh((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1);
     const bool use_graph = !h->timing;
-    const bool fused = m + 1 <= CG_KMAX;
     const bool two_pass = !std::is_same<T, float>::value;
-    if (fused && !two_pass)  // the second pass's coefficients stay zero
-        FBIM_CUDA_TRY(h, cudaMemsetAsync(S->hcol + (m + 1), 0, sizeof(double) * (m + 1), h->stream));
-    int gin_holds = -1;  // index of the basis vector the captured operator's input holds
+    const int gk = std::is_same<T, float>::value ? 0 : 1;
     if (use_graph) {
         FBIM_TRY(coarse_refresh(h));  // host-synchronising, and may reallocate: before the graph check
         FBIM_TRY(op_graph<T>(h));
     }
-    const double one = 1.0, mone = -1.0, zero = 0.0;
+    auto enqueue = [&](int k) -> fbim_status {
+        if (use_graph) {
+            FBIM_CUDA_TRY(h, cudaGraphLaunch(S->op_graph[gk], h->stream));
+            h->launches += S->op_kernels[gk];
+        } else {
+            FBIM_TRY(arnoldi_step<T>(h));
+        }
+        FBIM_CUDA_TRY(h, cudaEventRecord(S->ev_step[k & 1], h->stream));
+        return FBIM_OK;
+    };
+    const double one = 1.0;
     const int tb = 256, nb = (n + tb - 1) / tb;
     bool first = true;
     while (true) {
         // r = b - A x (just b when the initial guess is zero)
+        double beta = 0;
         if (first && x_is_zero) {
             FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->w, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+            beta = bnorm;
         } else {
             FBIM_TRY(saddle_apply<T>(h, x, S->w));
             k_axpby<<<nb, tb, 0, h->stream>>>(n, 1.0, b, -1.0, S->w);  // w = b - w
             h->launches += 1;
+            FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, S->w, &beta));
         }
         first = false;
-        double beta = 0;
-        FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, S->w, &beta));
         rel_est = beta / bnorm;
         if (!std::isfinite(beta)) {
             h->fail("GMRES residual is not finite");
             return FBIM_ERR_NONFINITE;
         }
         if (rel_est <= tol || iters >= max_iter) return FBIM_OK;
-        k_scale_copy<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0 / beta, S->w, S->V,
-                                                             use_graph ? S->gin : nullptr);
+        k_start<<<nb, tb, 0, h->stream>>>(n, 1.0 / beta, S->w, S->V, S->gin, S->kd);
         h->launches += 1;
-        gin_holds = 0;
         std::fill(gvec.begin(), gvec.end(), 0.0);
         gvec[0] = beta;
         int k_used = 0;
+        double res1 = rel_est, res2 = 0.0;  // residual estimates after the last two steps
+        FBIM_TRY(enqueue(0));
         for (int k = 0; k < m; ++k) {
-            double* vk = S->V + (size_t)k * ld;
-            double* zk = S->Z + (size_t)k * ld;
-            if (use_graph) {
-                const int gk = std::is_same<T, float>::value ? 0 : 1;
-                if (gin_holds != k)
-                    FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->gin, vk, sizeof(double) * n, cudaMemcpyDeviceToDevice,
-                                                     h->stream));
-                FBIM_CUDA_TRY(h, cudaGraphLaunch(S->op_graph[gk], h->stream));
-                FBIM_CUDA_TRY(h, cudaMemcpyAsync(zk, S->gz, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-                FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->w, S->gw, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-                h->launches += S->op_kernels[gk];
-            } else {
-                FBIM_TRY(precondition<T>(h, vk, zk));
-                FBIM_TRY(saddle_apply<T>(h, zk, S->w));
+            bool ahead = k + 1 < m && iters + 1 < max_iter;
+            if (ahead) {
+                const double rho = res2 > 0.0 ? std::min(res1 / res2, 1.0) : 1.0;
+                ahead = res1 * rho > 3.0 * tol;
             }
-            // classical Gram-Schmidt: twice for FP64 solves; once for the FP32-operator
-            // corrections of refinement, which stop at ~1e-4 where the basis's loss of
-            // orthogonality (far below that) does not matter, the FP64 outer residual
-            // deciding the accuracy
-            if (fused) {
-                const int K = k + 1, nb = (n + CG_CHUNK - 1) / CG_CHUNK, rb = (K * 32 + 255) / 256;
-                k_cgs_dots<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->w, nb, S->cg_part);
-                k_cgs_reduce<<<rb, 256, 0, h->stream>>>(K, nb, S->cg_part, S->hcol);
-                if (two_pass) {
-                    k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol, S->w, K, nb, S->cg_part);
-                    k_cgs_reduce<<<rb, 256, 0, h->stream>>>(K, nb, S->cg_part, S->hcol + (m + 1));
-                    k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol + (m + 1), S->w, 0, nb,
-                                                              S->cg_part);
-                    h->launches += 2;
-                } else {
-                    k_cgs_update<<<nb, CG_TB, 0, h->stream>>>(n, K, S->V, ld, S->hcol, S->w, 0, nb, S->cg_part);
-                }
-                k_cgs_reduce<<<1, 32, 0, h->stream>>>(1, nb, S->cg_part, S->hcol + 2 * (m + 1));
-                h->launches += 4;
-                FBIM_CUDA_TRY(h, cudaGetLastError());
-            } else {
-                FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero, S->hcol, 1));
-                FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol, 1, &one, S->w, 1));
-                FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, S->V, ld, S->w, 1, &zero,
-                                               S->hcol + (m + 1), 1));
-                FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, S->V, ld, S->hcol + (m + 1), 1,
-                                               &one, S->w, 1));
-                // |w|^2 on the device next to the dot products
-                cublasSetPointerMode(B, CUBLAS_POINTER_MODE_DEVICE);
-                const cublasStatus_t ds = cublasDdot(B, n, S->w, 1, S->w, 1, S->hcol + 2 * (m + 1));
-                cublasSetPointerMode(B, CUBLAS_POINTER_MODE_HOST);
-                FBIM_CUBLAS_TRY(h, ds);
-            }
-            // one read-back, one sync per step
-            FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->hcol, sizeof(double) * (2 * (m + 1) + 1),
-                                             cudaMemcpyDeviceToHost, h->stream));
-            FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-            const double hn = std::sqrt(std::max(hc[2 * (m + 1)], 0.0));
+            if (ahead) FBIM_TRY(enqueue(k + 1));
+            FBIM_CUDA_TRY(h, cudaEventSynchronize(S->ev_step[k & 1]));
+            const double* row = S->hist_host + (size_t)k * hs;
+            const double hn = std::sqrt(std::max(row[2 * (m + 1)], 0.0));
             double* col = &Hh[(size_t)k * (m + 1)];
-            for (int i = 0; i <= k; ++i) col[i] = hc[i] + hc[(m + 1) + i];
+            for (int i = 0; i <= k; ++i) col[i] = two_pass ? row[i] + row[(m + 1) + i] : row[i];
             col[k + 1] = hn;
             if (!std::isfinite(hn)) {
                 h->fail("GMRES iterate is not finite");
                 return FBIM_ERR_NONFINITE;
-            }
-            if (hn > 0) {
-                // V_{k+1} = w / h_{k+1,k}, also into the captured operator's input
-                double* vn = S->V + (size_t)(k + 1) * ld;
-                k_scale_copy<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0 / hn, S->w, vn,
-                                                                     use_graph ? S->gin : nullptr);
-                h->launches += 1;
-                gin_holds = k + 1;
             }
             for (int i = 0; i < k; ++i) {
                 double t0 = cs[i] * col[i] + sn[i] * col[i + 1];
@@ -748,17 +815,20 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
             gvec[k] = cs[k] * gvec[k];
             ++iters;
             k_used = k + 1;
-            if (std::fabs(gvec[k + 1]) / bnorm <= tol || iters >= max_iter || hn == 0) break;
+            res2 = res1;
+            res1 = std::fabs(gvec[k + 1]) / bnorm;
+            if (res1 <= tol || iters >= max_iter || hn == 0) break;
+            if (!ahead && k + 1 < m) FBIM_TRY(enqueue(k + 1));
         }
-        // y = R^-1 g (upper triangular), x += Z y
-        std::vector<double> y(k_used);
+        // y = R^-1 g (upper triangular), x += Z y; y is staged in pinned memory after the
+        // history rows (the previous cycle's copy was complete at this cycle's first sync)
+        double* y = S->hist_host + (size_t)(m + 1) * hs;
         for (int i = k_used - 1; i >= 0; --i) {
             double acc = gvec[i];
             for (int j = i + 1; j < k_used; ++j) acc -= Hh[(size_t)j * (m + 1) + i] * y[j];
             y[i] = acc / Hh[(size_t)i * (m + 1) + i];
         }
-        FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->hcol, y.data(), sizeof(double) * k_used, cudaMemcpyHostToDevice,
-                                         h->stream));
+        FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->hcol, y, sizeof(double) * k_used, cudaMemcpyHostToDevice, h->stream));
         FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k_used, &one, S->Z, ld, S->hcol, 1, &one, x, 1));
         // A correction of iterative refinement stops on the cycle's own estimate: the
         // outer loop measures the true FP64 residual anyway, and a restart started only
@@ -770,16 +840,17 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
     }
 }
 
-// True relative residual |b - A_64 x| / |b| with the FP64 operator.
-static fbim_status true_residual(fbim_handle_s* h, const double* b, const double* x, double* r, double& rel) {
+// True residual r = b - A_64 x with the FP64 operator, rn = |r| and rel = rn / bn
+// (bn = |b|).
+static fbim_status true_residual(fbim_handle_s* h, const double* b, const double* x, double* r, double bn,
+                                 double& rn, double& rel) {
     Solver* S = h->solver;
     const int n = S->n;
     FBIM_TRY(saddle_apply<double>(h, x, r));
     k_axpby<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0, b, -1.0, r);
     h->launches += 1;
-    double rn = 0, bn = 0;
+    rn = 0;
     FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, r, &rn));
-    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, b, &bn));
     rel = bn > 0 ? rn / bn : 0.0;
     return FBIM_OK;
 }
@@ -798,11 +869,12 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
     warm = warm && S->have_x;
     if (!warm) FBIM_CUDA_TRY(h, cudaMemsetAsync(S->d, 0, sizeof(double) * n, h->stream));
     int iters = 0;
-    double rel = 1.0;
+    double rel = 1.0, bn = 0.0, rn = 0.0;  // |r| / |b|, |b|, |r|
+    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->t, &bn));
     if (h->precision == FBIM_FP64) {
         double est = 0;
-        FBIM_TRY(fgmres<double>(h, S->t, S->d, tol, max_iter, iters, est, !warm));
-        FBIM_TRY(true_residual(h, S->t, S->d, S->r, rel));
+        FBIM_TRY(fgmres<double>(h, S->t, S->d, tol, max_iter, iters, est, !warm, false, bn));
+        FBIM_TRY(true_residual(h, S->t, S->d, S->r, bn, rn, rel));
     } else {
         // Iterative refinement: FP32-operator corrections, FP64 residuals.  r holds the
         // residual b - A x and rel = |r| / |b|.  After a correction d computed from a
@@ -814,10 +886,11 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
         double* corr = S->corr;
         fbim_status st = FBIM_OK;
         if (warm) {
-            FBIM_TRY(true_residual(h, S->t, S->d, S->r, rel));
+            FBIM_TRY(true_residual(h, S->t, S->d, S->r, bn, rn, rel));
         } else {
             cudaMemcpyAsync(S->r, S->t, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);  // x = 0
-            rel = 1.0;
+            rn = bn;
+            rel = bn > 0 ? 1.0 : 0.0;
         }
         // The residual advanced with the FP32 operator errs by ~1e-6 rel_prev |b| (FP32
         // operator error with margin); it stays below 0.05 tol |b| while rel_prev <= 5e4 tol.
@@ -831,13 +904,14 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
             cudaMemsetAsync(corr, 0, sizeof(double) * n, h->stream);
             int it = 0;
             double est = 0;
-            st = fgmres<float>(h, S->r, corr, inner, std::min(max_iter - iters, S->restart), it, est, true, true);
+            st = fgmres<float>(h, S->r, corr, inner, std::min(max_iter - iters, S->restart), it, est, true, true,
+                               rn);
             if (st != FBIM_OK) break;
             iters += it;
             k_axpby<<<nb, tb, 0, h->stream>>>(n, 1.0, corr, 1.0, S->d);
             h->launches += 1;
             if (rel > recompute_above) {
-                st = true_residual(h, S->t, S->d, S->r, rel);
+                st = true_residual(h, S->t, S->d, S->r, bn, rn, rel);
                 if (st != FBIM_OK) break;
             } else {
                 const double rel_prev = rel;
@@ -847,9 +921,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
                     FBIM_TRY(saddle_apply<float>(h, corr, S->w));
                     k_axpby<<<nb, tb, 0, h->stream>>>(n, -1.0, S->w, 1.0, S->r);
                     h->launches += 1;
-                    double rn = 0, bn = 0;
                     FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->r, &rn));
-                    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->t, &bn));
                     rel = bn > 0 ? rn / bn : 0.0;
                 }
             }

@@ -33,7 +33,15 @@ struct Solver {
     double* r = nullptr;        // [n]
     double* d = nullptr;        // [n]
     double* t = nullptr;        // [n]
-    double* hcol = nullptr;     // [2 (m+1) + 1] dot products and the squared norm
+    double* hcol = nullptr;     // [m+1] the cycle's least-squares solution y (x += Z y)
+    // device-driven Arnoldi step (solver.cu): index of the newest basis vector, the step
+    // history (one row per step: two passes of coefficients, |w|^2, 1/|w|), its mapped
+    // host mirror, and one event per step in flight
+    int* kd = nullptr;
+    double* hist = nullptr;       // [(m+1)][2 (m+1) + 2]
+    double* hist_host = nullptr;  // same, mapped pinned host memory, then [m+1] for y
+    double* hist_map = nullptr;   // its device address
+    cudaEvent_t ev_step[2] = {nullptr, nullptr};
     void* zbuf = nullptr;       // [N][2] rotated residual (T)
     void* gbuf = nullptr;       // [N][2] M_ref^+ z (T)
     cublasHandle_t blas = nullptr;
@@ -43,10 +51,10 @@ struct Solver {
     void* blas_ws = nullptr;    // fixed cuBLAS workspace (so captured graphs never allocate)
     double* corr = nullptr;     // [n] refinement correction
     bool have_x = false;        // d holds the last solve's solution (a warm start can use it)
-    // captured operator (precondition then saddle) per precision, [0] FP32 / [1] FP64:
-    // reads gin, writes gz = P gin and gw = A gz; recaptured when the handle's layout changes
+    // captured Arnoldi step per precision, [0] FP32 / [1] FP64: gz = P gin, gw = A gz,
+    // orthogonalised and normalised into V and gin; recaptured when the handle's layout changes
     double *gin = nullptr, *gz = nullptr, *gw = nullptr;
-    double* cg_part = nullptr;  // [64][blocks] partial dot products of the fused Gram-Schmidt
+    double* cg_part = nullptr;  // [m+1][blocks] partial dot products of the fused Gram-Schmidt
     cudaGraphExec_t op_graph[2] = {nullptr, nullptr};
     unsigned long long op_version[2] = {0, 0};
     long long op_kernels[2] = {0, 0};

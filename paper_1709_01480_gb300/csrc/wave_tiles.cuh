@@ -252,12 +252,37 @@ __global__ void __launch_bounds__(256) k_interp_tiles(TileGeom tg, T a, T q2, T 
 // grid stays in L2); interpolation accumulates column sums, weights them by the
 // column weights and reduces over the lane group.
 // ---------------------------------------------------------------------------
+// Window weights of every node, once per geometry: wtab[i][0][p] = w(p - hw - f_x) and
+// wtab[i][1][p] = g0 w(p - hw - f_y), p < P, by the recurrence above (three
+// exponentials per dimension).  The FP64 warp kernels read them instead of taking
+// two FP64 exponentials per lane, which the FP64 pipe makes their largest cost.
+template <typename T, int PMAX>
+__global__ void k_node_weights(int N, int P, int hw, T a, T q2, T g0, const typename V2<T>::type* __restrict__ tfrac,
+                               T* __restrict__ wtab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    constexpr int HW = (PMAX - 1) / 2;
+    const int shift = HW - hw;
+    const typename V2<T>::type f = tfrac[i];
+    T w[PMAX];
+    T* out = wtab + (size_t)i * 2 * P;
+    window_recur<T, PMAX>(f.x, a, q2, T(1), w);
+#pragma unroll
+    for (int j = 0; j < PMAX; ++j)
+        if (j >= shift && j < shift + P) out[j - shift] = w[j];
+    window_recur<T, PMAX>(f.y, a, q2, g0, w);
+#pragma unroll
+    for (int j = 0; j < PMAX; ++j)
+        if (j >= shift && j < shift + P) out[P + j - shift] = w[j];
+}
+
+// wtab: the node weights above, or null to compute them per lane.
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread_warp(int N, int M, int P, int hw, T a, T g0,
                                                     const int2* __restrict__ tbase,
                                                     const typename V2<T>::type* __restrict__ tfrac,
                                                     const typename V2<T>::type* __restrict__ mu_t,
-                                                    T* __restrict__ grid) {
+                                                    const T* __restrict__ wtab, T* __restrict__ grid) {
     const int lane = threadIdx.x & 31;
     const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const bool two = P <= 16;
@@ -269,12 +294,20 @@ __global__ void __launch_bounds__(256) k_spread_warp(int N, int M, int P, int hw
     typename V2<T>::type f = {T(0), T(0)}, mu = {T(0), T(0)};
     if (active) {
         b = tbase[i];
-        f = tfrac[i];
+        if (!wtab) f = tfrac[i];
         mu = mu_t[i];
     }
-    const T dx = T(p - hw) - f.x, dy = T(p - hw) - f.y;
-    const T wx = active ? acc_exp(-a * dx * dx) : T(0);
-    const T wy = active ? g0 * acc_exp(-a * dy * dy) : T(0);  // row weight of row p
+    T wx = T(0), wy = T(0);  // column weight of column p, row weight of row p
+    if (active) {
+        if (wtab) {
+            wx = wtab[(size_t)i * 2 * P + p];
+            wy = wtab[(size_t)i * 2 * P + P + p];
+        } else {
+            const T dx = T(p - hw) - f.x, dy = T(p - hw) - f.y;
+            wx = acc_exp(-a * dx * dx);
+            wy = g0 * acc_exp(-a * dy * dy);
+        }
+    }
     const T cx = wx * mu.x, cy = wx * mu.y;
     int gx = b.x - hw + p;
     gx += (gx < 0) ? M : 0;
@@ -298,7 +331,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_interp_warp(int N, int M, int P, int hw, T a, T g0,
                                                     const int2* __restrict__ tbase,
                                                     const typename V2<T>::type* __restrict__ tfrac,
-                                                    const T* __restrict__ grid,
+                                                    const T* __restrict__ wtab, const T* __restrict__ grid,
                                                     typename V2<T>::type* __restrict__ v_t) {
     const int lane = threadIdx.x & 31;
     const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -311,11 +344,19 @@ __global__ void __launch_bounds__(256) k_interp_warp(int N, int M, int P, int hw
     typename V2<T>::type f = {T(0), T(0)};
     if (active) {
         b = tbase[i];
-        f = tfrac[i];
+        if (!wtab) f = tfrac[i];
     }
-    const T dx = T(p - hw) - f.x, dy = T(p - hw) - f.y;
-    const T wx = active ? acc_exp(-a * dx * dx) : T(0);
-    const T wy = active ? g0 * acc_exp(-a * dy * dy) : T(0);
+    T wx = T(0), wy = T(0);
+    if (active) {
+        if (wtab) {
+            wx = wtab[(size_t)i * 2 * P + p];
+            wy = wtab[(size_t)i * 2 * P + P + p];
+        } else {
+            const T dx = T(p - hw) - f.x, dy = T(p - hw) - f.y;
+            wx = acc_exp(-a * dx * dx);
+            wy = g0 * acc_exp(-a * dy * dy);
+        }
+    }
     int gx = b.x - hw + p;
     gx += (gx < 0) ? M : 0;
     gx -= (gx >= M) ? M : 0;

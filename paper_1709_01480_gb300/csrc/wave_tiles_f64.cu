@@ -72,18 +72,34 @@ static int warp_blocks(int N, int P) {
 
 template <>
 void warp_spread<double>(cudaStream_t st, int N, const TileGeom& tg, double a, double g0, const int2* tbase,
-                      const void* tfrac, const void* mu_t, double* grid) {
+                      const void* tfrac, const double* wtab, const void* mu_t, double* grid) {
     using T2 = typename V2<double>::type;
     k_spread_warp<double><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
-                                                            (const T2*)mu_t, grid);
+                                                            (const T2*)mu_t, wtab, grid);
 }
 
 template <>
 void warp_interp<double>(cudaStream_t st, int N, const TileGeom& tg, double a, double g0, const int2* tbase,
-                      const void* tfrac, const double* grid, void* v_t) {
+                      const void* tfrac, const double* wtab, const double* grid, void* v_t) {
     using T2 = typename V2<double>::type;
     k_interp_warp<double><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
-                                                            grid, (T2*)v_t);
+                                                            wtab, grid, (T2*)v_t);
+}
+
+template <>
+void node_weights<double>(cudaStream_t st, int N, const TileGeom& tg, double a, double g0, const void* tfrac,
+                          double* wtab) {
+    using T2 = typename V2<double>::type;
+    const double q2 = std::exp(-2.0 * a);
+    const unsigned nb = (unsigned)((N + 127) / 128);
+    switch (pmax_for(tg.P)) {
+#define FBIM_LAUNCH(PM)                                                                                       \
+    case PM:                                                                                                  \
+        k_node_weights<double, PM><<<nb, 128, 0, st>>>(N, tg.P, tg.hw, a, q2, g0, (const T2*)tfrac, wtab);   \
+        break;
+        FBIM_PMAX_CASES(FBIM_LAUNCH)
+#undef FBIM_LAUNCH
+    }
 }
 
 }  // namespace fbim
