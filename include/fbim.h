@@ -98,6 +98,9 @@ typedef struct {
     double grid_tune_ms;     /* tuned cost (ms) of the chosen side's FFT pair, 0 if untuned */
     int    split_candidates; /* cutoffs the split tuner timed (0: r_c as given)          */
     double split_cost_ms;    /* the chosen cutoff's cost per solve-equivalent (ms)      */
+    int    fp64_fft;         /* transforms and Fourier scale of the FP64 operator: 1 float-
+                                float kernels (FP32 handles with an even 5-smooth grid),
+                                -1 cuFFT double, 0 not yet set up (first FP64 use)      */
 } fbim_info;
 
 /* Fill *p with defaults: FP64, order 4, automatic grid and support, eta = 1,

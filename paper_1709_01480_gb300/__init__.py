@@ -69,7 +69,8 @@ class Info(ctypes.Structure):
                 ("tile", ctypes.c_int), ("pair_entries", ctypes.c_longlong),
                 ("wave_variant", ctypes.c_int), ("variant_ms", ctypes.c_double * 2),
                 ("launches", ctypes.c_longlong), ("grid_min", ctypes.c_int), ("grid_tune_ms", ctypes.c_double),
-                ("split_candidates", ctypes.c_int), ("split_cost_ms", ctypes.c_double)]
+                ("split_candidates", ctypes.c_int), ("split_cost_ms", ctypes.c_double),
+                ("fp64_fft", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

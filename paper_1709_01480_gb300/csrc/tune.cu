@@ -5,8 +5,9 @@
 // the forward + inverse transform pair of a few admissible sizes in
 // [M_min, 1.3 M_min] (multiples of 4, 2^a 3^b 5^c 7^d, with a wave-space tile side in
 // [max(16, (P - 1)/2), 64] dividing M) and keeps the cheapest.  FP32 handles
-// weigh the FP64 transform (used by the refinement residuals) at 0.1.  The
-// smallest side within 5% of the cheapest is kept.
+// weigh the FP64 transform (used by the refinement residuals) at 0.1 and take
+// 5-smooth sides only, which their float-float FFT supports.  The smallest side
+// within 5% of the cheapest is kept.
 #include <cufft.h>
 
 #include <algorithm>
@@ -17,10 +18,10 @@
 
 namespace fbim {
 
-static bool nice(int m) {
+static bool nice(int m, bool seven) {
     int r = m;
     for (int f : {2, 3, 5, 7})
-        while (r % f == 0) r /= f;
+        while ((f != 7 || seven) && r % f == 0) r /= f;
     return r == 1;
 }
 
@@ -72,7 +73,7 @@ fbim_status tune_grid(fbim_handle_s* h, int M_min, int P, int& M_out, double& be
     const int ts_min = std::max(16, (P - 1) / 2);
     // multiples of 4 (the FP32 wave-space kernels then move float4 chunks)
     for (int m = (M_min + 3) / 4 * 4; m <= (int)(1.3 * M_min) + 4 && cand.size() < 12; m += 4)
-        if (nice(m) && tile_side(m) >= ts_min) cand.push_back(m);
+        if (nice(m, h->precision != FBIM_FP32) && tile_side(m) >= ts_min) cand.push_back(m);
     M_out = M_min;
     best_ms = 0;
     if (cand.size() <= 1) {

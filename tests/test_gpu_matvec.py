@@ -122,6 +122,52 @@ def test_fp32_handle_residual_operator_matches_oracle(torch, fb, n_b, n_p, L, se
     op.close()
 
 
+def _smooth5(m):
+    for f in (2, 3, 5):
+        while m % f == 0:
+            m //= f
+    return m == 1
+
+
+def test_float_float_fft_matches_cufft_double(torch, fb):
+    """The FP64 operator of an FP32 handle takes its transforms and Fourier scale in
+    float-float (packed two-real FFT, Stockham radix 4/2/3/5 passes); on sides that
+    exercise every radix it agrees with the FP64 handle's cuFFT double path to 1e-12
+    and with the oracle to the FP64 bar.  A side with a factor 7 keeps cuFFT."""
+    ref, Q = _case(4, 64, 4.0, 0)
+    L, tol, n_box = 4.0, 1e-13, 6
+    xi = _xi(L, n_box, tol)
+    probe = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, grid_tune=False)
+    m0 = probe.info["grid"]
+    probe.close()
+    picks = []
+    for want in (lambda m: m % 5 == 0 and m % 3 == 0, lambda m: m % 9 == 0, lambda m: m % 16 == 0 and m % 3 != 0,
+                 lambda m: m % 4 == 2):
+        m = m0 + (m0 % 2)
+        while not (_smooth5(m) and want(m)):
+            m += 2
+        picks.append(m)
+    m7 = m0 + (m0 % 2)
+    while m7 % 7 != 0 or _smooth5(m7):
+        m7 += 2
+    M, _, _ = _oracle_parts(ref, Q, L, xi)
+    mu = np.random.default_rng(11).standard_normal((4 * 64, 2))
+    mu_d = torch.tensor(mu, dtype=torch.float64, device="cuda")
+    expect = (M @ mu.reshape(-1)).reshape(-1, 2)
+    for grid in picks + [m7]:
+        op32 = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, grid=grid, precision="fp32")
+        op64 = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, grid=grid, precision="fp64")
+        v_df = op32.apply_stokeslet_fp64(mu_d).cpu().numpy()
+        v_64 = op64.apply_stokeslet(mu_d).cpu().numpy()
+        mode = op32.info["fp64_fft"]
+        e_cmp, e_or = _rel(v_df, v_64), _rel(v_df, expect)
+        print(f"grid {grid}: fp64_fft {mode}, vs cuFFT double {e_cmp:.2e}, vs oracle {e_or:.2e}")
+        assert mode == (1 if grid in picks else -1)
+        assert e_cmp < 1e-12 and e_or < FP64_TOL
+        op32.close()
+        op64.close()
+
+
 def test_single_body_and_zero_input(torch, fb):
     ref, Q = _case(1, 64, 3.0, 1)
     xi = _xi(3.0, 4, 1e-13)
