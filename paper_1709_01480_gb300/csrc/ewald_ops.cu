@@ -651,7 +651,7 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     FBIM_CUFFT_TRY(h, cufftSetStream(e.plan_i, h->stream));
     FBIM_CUDA_TRY(h, tile_set_smem<T>(TileGeom{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2}));
     if constexpr (std::is_same<T, double>::value) {
-        if (h->precision == FBIM_FP32) FBIM_TRY(dfft_setup(h));
+        if (h->precision == FBIM_FP32) FBIM_TRY(wfft_setup(h));
     }
     e.ready = true;
     FBIM_TRY(refresh_offsets<T>(h));
@@ -711,20 +711,20 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
             tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
         }
         h->mark(FBIM_ST_SPREAD);
-        bool df_fft = false;  // float-float FFTs and scale (FP64 operator of an FP32 handle)
+        bool own_fft = false;  // float-float transforms and scale (FP64 operator of an FP32 handle)
         if constexpr (std::is_same<T, double>::value) {
-            df_fft = h->dfft.state == 1;
-            if (df_fft) {
-                dfft_forward(h, h->stream, e.grid);
+            own_fft = h->fft64.state == 1;
+            if (own_fft) {
+                wfft_forward(h, h->stream, e.grid);
                 h->mark(FBIM_ST_FFT_F);
-                dfft_scale(h, h->stream);
+                wfft_scale(h, h->stream);
                 h->mark(FBIM_ST_SCALE);
-                dfft_inverse(h, h->stream, e.grid);
+                wfft_inverse(h, h->stream, e.grid);
                 h->mark(FBIM_ST_FFT_I);
                 h->launches += 2;
             }
         }
-        if (!df_fft) {
+        if (!own_fft) {
             FBIM_CUFFT_TRY(h, FftType<T>::f(e.plan_f, e.grid, (C*)e.spec));
             h->mark(FBIM_ST_FFT_F);
             const double V = h->L * h->L;
@@ -887,7 +887,7 @@ static void free_one(EwaldBuffers<T>& e) {
 void free_ewald(fbim_handle_s* h) {
     free_one(h->e64);
     free_one(h->e32);
-    dfft_free(h);
+    wfft_free(h);
 }
 
 template fbim_status ensure_ewald<double>(fbim_handle_s*);

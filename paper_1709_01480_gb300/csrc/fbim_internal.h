@@ -97,20 +97,21 @@ struct ChebE1 {
     int deg;
 };
 
-// Float-float FFT and Fourier scale of the FP64 residual operator of FP32 handles
-// (fft_df.cu).
-constexpr int kDfFftMaxPasses = 24;
-struct DfFftPlan {
+// Float-float Stockham FFTs and Fourier scale of the FP64 residual operator of FP32
+// handles (wave_fft.cu).
+constexpr int kFftMaxPasses = 24;
+struct FftPlan {
     int M = 0, nr = 0;
-    int radix[kDfFftMaxPasses] = {};  // Stockham passes: radix 4s, then 2, 3s, 5s
+    int radix[kFftMaxPasses] = {};  // Stockham passes: radix 4s, then 2, 3s, 5s
 };
-struct DfFft {
-    int state = 0;         // 0 not set up, 1 in use, -1 unavailable (M odd, not 5-smooth or too large)
-    DfFftPlan plan;
-    float4* tw = nullptr;  // [M] e^{-2 pi i m/M}, float-float (re hi, re lo, im hi, im lo)
-    float4* tab = nullptr; // [M/2][M][2] scale factors of the pairs (k, -k)
-    float4* T1 = nullptr;  // [M][M] spectrum after the x pass, [k_x][y]
-    float4* T2 = nullptr;  // [M][M] after the y pass and scale, [y][k_x]
+struct WaveFft {
+    int state = 0;          // 0 not set up, 1 in use, -1 unavailable (M odd, not 5-smooth or
+                            // too large for shared memory)
+    FftPlan plan;
+    float4* tw = nullptr;   // [M] e^{-2 pi i m/M} (re hi, re lo, im hi, im lo)
+    float4* tab = nullptr;  // [M/2][M][2] scale factors of the pairs (k, -k)
+    float4* T1 = nullptr;   // [M][M] after the x pass, [k_x][y]
+    float4* T2 = nullptr;   // [M][M] after the y pass and scale, [k_x][y]
 };
 
 }  // namespace fbim
@@ -160,7 +161,7 @@ struct fbim_handle_s {
     fbim::ChebE1<float> cheb32{};
 
     fbim::EwaldBuffers<double> e64;
-    fbim::DfFft dfft;  // FP64 wave space of FP32 handles
+    fbim::WaveFft fft64;  // float-float transforms of the FP64 operator (FP32 handles)
     fbim::EwaldBuffers<float> e32;
 
     std::vector<double> host_ref;
@@ -241,12 +242,12 @@ template <typename T> fbim_status apply_operator(fbim_handle_s* h, const double*
 template <typename T>
 fbim_status apply_noise(fbim_handle_s* h, const double* Z, unsigned long long seed, unsigned counter, double* out);
 void free_ewald(fbim_handle_s* h);
-// fft_df.cu: set up (state 1) or mark unavailable (state -1) once per handle; the three
-// launches replace the FP64 FFTs and scale on the grid in place
-fbim_status dfft_setup(fbim_handle_s* h);
-void dfft_free(fbim_handle_s* h);
-void dfft_forward(fbim_handle_s* h, cudaStream_t st, const double* grid);
-void dfft_scale(fbim_handle_s* h, cudaStream_t st);
-void dfft_inverse(fbim_handle_s* h, cudaStream_t st, double* grid);
+// wave_fft.cu: set up (state 1) or mark unavailable (state -1) once per handle; the
+// three launches replace the FP64 FFTs and scale on the grid in place
+fbim_status wfft_setup(fbim_handle_s* h);
+void wfft_free(fbim_handle_s* h);
+void wfft_forward(fbim_handle_s* h, cudaStream_t st, const double* grid);
+void wfft_scale(fbim_handle_s* h, cudaStream_t st);
+void wfft_inverse(fbim_handle_s* h, cudaStream_t st, double* grid);
 
 }  // namespace fbim

@@ -133,7 +133,8 @@ def test_float_float_fft_matches_cufft_double(torch, fb):
     """The FP64 operator of an FP32 handle takes its transforms and Fourier scale in
     float-float (packed two-real FFT, Stockham radix 4/2/3/5 passes); on sides that
     exercise every radix it agrees with the FP64 handle's cuFFT double path to 1e-12
-    and with the oracle to the FP64 bar.  A side with a factor 7 keeps cuFFT."""
+    and with the oracle to the FP64 bar, and the handle's FP32 operator stays within
+    the FP32 bar.  A side with a factor 7 keeps cuFFT."""
     ref, Q = _case(4, 64, 4.0, 0)
     L, tol, n_box = 4.0, 1e-13, 6
     xi = _xi(L, n_box, tol)
@@ -159,11 +160,13 @@ def test_float_float_fft_matches_cufft_double(torch, fb):
         op64 = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, grid=grid, precision="fp64")
         v_df = op32.apply_stokeslet_fp64(mu_d).cpu().numpy()
         v_64 = op64.apply_stokeslet(mu_d).cpu().numpy()
+        v_32 = op32.apply_stokeslet(mu_d).cpu().numpy()
         mode = op32.info["fp64_fft"]
-        e_cmp, e_or = _rel(v_df, v_64), _rel(v_df, expect)
-        print(f"grid {grid}: fp64_fft {mode}, vs cuFFT double {e_cmp:.2e}, vs oracle {e_or:.2e}")
+        e_cmp, e_or, e_32 = _rel(v_df, v_64), _rel(v_df, expect), _rel(v_32, expect)
+        print(f"grid {grid}: fp64_fft {mode}, vs cuFFT double {e_cmp:.2e}, vs oracle {e_or:.2e}; "
+              f"FP32 operator vs oracle {e_32:.2e}")
         assert mode == (1 if grid in picks else -1)
-        assert e_cmp < 1e-12 and e_or < FP64_TOL
+        assert e_cmp < 1e-12 and e_or < FP64_TOL and e_32 < FP32_TOL
         op32.close()
         op64.close()
 
