@@ -171,44 +171,3 @@ DF_HD df log(df x) {
 }  // namespace dfl
 }  // namespace fbim
 
-namespace fbim {
-namespace dfl {
-
-// Chebyshev series on [0, zmax] in float-float: coefficients and scale 2 / zmax.
-constexpr int kChebDF = 48;
-struct ChebDF {
-    float hi[kChebDF], lo[kChebDF];
-    float s_hi, s_lo;
-    int deg;
-};
-
-// E1(z)/2 - e^{-z} = S(z) - ln(z)/2, S by Clenshaw's recurrence.
-DF_HD df kernel_a(const ChebDF& ce, df z) {
-    const df t = sub(mul(z, df{ce.s_hi, ce.s_lo}), df{1.0f, 0.0f});
-    const df t2 = {2.0f * t.hi, 2.0f * t.lo};
-    df b1 = {0.0f, 0.0f}, b2 = {0.0f, 0.0f};
-    for (int k = ce.deg; k >= 1; --k) {
-        const df b0 = add_fast(add_fast(mul(t2, b1), neg(b2)), df{ce.hi[k], ce.lo[k]});
-        b2 = b1;
-        b1 = b0;
-    }
-    const df S = add(sub(mul(t, b1), b2), df{ce.hi[0], ce.lo[0]});
-    const df l = log(z);
-    return sub(S, df{0.5f * l.hi, 0.5f * l.lo});
-}
-
-// The real-space kernel pref (a I + b r r^T), a = E1(z)/2 - e^{-z}, b = e^{-z} / r^2,
-// z = xi^2 r^2, for the separation (x, y); about 48-bit accurate.
-DF_HD void pair_value(df x, df y, df xi2, df pref, const ChebDF& ce, df& xx, df& xy, df& yy) {
-    const df x2 = mul(x, x), y2 = mul(y, y), xy2 = mul(x, y);
-    const df r2 = add(x2, y2);
-    const df z = mul(xi2, r2);
-    const df a = kernel_a(ce, z);
-    const df b = div(exp_neg(z), r2);
-    xx = mul(pref, add(a, mul(b, x2)));
-    xy = mul(pref, mul(b, xy2));
-    yy = mul(pref, add(a, mul(b, y2)));
-}
-
-}  // namespace dfl
-}  // namespace fbim

@@ -200,42 +200,83 @@ __global__ void __launch_bounds__(256) k_pair_eval_rows(int N, const int* __rest
 // then the kernel in float-float arithmetic (about 48 bits, ~1e-13 relative; the FP32
 // pipes run it far faster than the FP64 pipe would).  Pairs within rounding of r_c
 // may differ from an FP64 search; their kernel value is at the Ewald tolerance.
+// The pair value in float-float from the piecewise tables in shared memory: S and
+// e^{-z} by Horner in t = (z - zc[k]) inv_w on the piece k holding z, the logarithm
+// of Sec. 3.2's a = S - ln(z)/2 by dfl::log.
+__device__ __forceinline__ void pair_value_pw(dfl::df x, dfl::df y, dfl::df xi2, dfl::df pref,
+                                              const float* __restrict__ zc, const float2* __restrict__ cS,
+                                              const float2* __restrict__ cE, int K, float inv_w, float kscale,
+                                              dfl::df& xx, dfl::df& xy, dfl::df& yy) {
+    using namespace dfl;
+    constexpr int D = kPwDeg;
+    const df x2 = mul(x, x), y2 = mul(y, y), xy2 = mul(x, y);
+    const df r2 = add(x2, y2);
+    const df z = mul(xi2, r2);
+    const int k = min(max((int)(z.hi * kscale), 0), K - 1);
+    const df t = mul_f(add_f(z, -zc[k]), inv_w);
+    const float2* s = cS + k * (D + 1);
+    const float2* e = cE + k * (D + 1);
+    df S = {s[D].x, s[D].y}, E = {e[D].x, e[D].y};
+#pragma unroll
+    for (int j = D - 1; j >= 0; --j) {
+        S = add_fast(mul(S, t), df{s[j].x, s[j].y});
+        E = add_fast(mul(E, t), df{e[j].x, e[j].y});
+    }
+    const df l = log(z);
+    const df a = sub(S, df{0.5f * l.hi, 0.5f * l.lo});
+    const df b = div(E, r2);
+    xx = mul(pref, add(a, mul(b, x2)));
+    xy = mul(pref, mul(b, xy2));
+    yy = mul(pref, add(a, mul(b, y2)));
+}
+
+// One warp per target row, lanes over the row's entries; blocks loop over the rows
+// (the tables are loaded into shared memory once per block).
 __global__ void __launch_bounds__(256) k_pair_from32(int N, int n_box, dfl::df r_c, const int* __restrict__ perm,
                                                     const int* __restrict__ cell, const float4* __restrict__ off,
                                                     const int* __restrict__ slice_start,
                                                     const int* __restrict__ row_count,
                                                     const PairEntry<float>* __restrict__ p32, dfl::df xi2,
-                                                    dfl::df pref, dfl::ChebDF ce, PairEntryDF* __restrict__ p64) {
-    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (t >= N) return;
-    const int sl = t >> 5, base = slice_start[sl], len = slice_start[sl + 1] - base, n = row_count[t];
-    const int ct = cell[perm[t]], cxt = ct % n_box, cyt = ct / n_box;
-    const float4 ot = off[t];
-    const size_t r0 = (size_t)base * 32 + (t & 31);
-    for (int k = lane; k < len; k += 32) {
-        PairEntryDF e;
-        if (k < n) {
-            const int s = p32[r0 + (size_t)k * 32].src;
-            const int cs = cell[perm[s]];
-            int dx = cs % n_box - cxt, dy = cs / n_box - cyt;
-            dx += (dx < -1) ? n_box : 0;
-            dx -= (dx > 1) ? n_box : 0;
-            dy += (dy < -1) ? n_box : 0;
-            dy -= (dy > 1) ? n_box : 0;
-            const float4 os = off[s];
-            // (o_t - d r_c) - o_s with d in {-1, 0, 1}: d r_c is exact
-            dfl::df rx = {ot.x, ot.y}, ry = {ot.z, ot.w};
-            if (dx) rx = dfl::sub(rx, dx > 0 ? r_c : dfl::neg(r_c));
-            if (dy) ry = dfl::sub(ry, dy > 0 ? r_c : dfl::neg(r_c));
-            rx = dfl::sub(rx, dfl::df{os.x, os.y});
-            ry = dfl::sub(ry, dfl::df{os.z, os.w});
-            dfl::df xx, xy, yy;
-            dfl::pair_value(rx, ry, xi2, pref, ce, xx, xy, yy);
-            e = PairEntryDF{xx.hi, xy.hi, yy.hi, s, xx.lo, xy.lo, yy.lo, 0.0f};
-        } else {
-            e = PairEntryDF{0.0f, 0.0f, 0.0f, t, 0.0f, 0.0f, 0.0f, 0.0f};
+                                                    dfl::df pref, const float* __restrict__ pw, int K, float inv_w,
+                                                    float kscale, PairEntryDF* __restrict__ p64) {
+    extern __shared__ float pw_s[];
+    const int n_tab = K + 4 * K * (kPwDeg + 1);
+    for (int i = threadIdx.x; i < n_tab; i += blockDim.x) pw_s[i] = pw[i];
+    __syncthreads();
+    const float* zc = pw_s;
+    const float2* cS = reinterpret_cast<const float2*>(pw_s + K);
+    const float2* cE = cS + K * (kPwDeg + 1);
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < N; t += gridDim.x * warps) {
+        const int sl = t >> 5, base = slice_start[sl], len = slice_start[sl + 1] - base, n = row_count[t];
+        const int ct = cell[perm[t]], cxt = ct % n_box, cyt = ct / n_box;
+        const float4 ot = off[t];
+        const size_t r0 = (size_t)base * 32 + (t & 31);
+        for (int k = lane; k < len; k += 32) {
+            PairEntryDF e;
+            if (k < n) {
+                const int s = p32[r0 + (size_t)k * 32].src;
+                const int cs = cell[perm[s]];
+                int dx = cs % n_box - cxt, dy = cs / n_box - cyt;
+                dx += (dx < -1) ? n_box : 0;
+                dx -= (dx > 1) ? n_box : 0;
+                dy += (dy < -1) ? n_box : 0;
+                dy -= (dy > 1) ? n_box : 0;
+                const float4 os = off[s];
+                // (o_t - d r_c) - o_s with d in {-1, 0, 1}: d r_c is exact
+                dfl::df rx = {ot.x, ot.y}, ry = {ot.z, ot.w};
+                if (dx) rx = dfl::sub(rx, dx > 0 ? r_c : dfl::neg(r_c));
+                if (dy) ry = dfl::sub(ry, dy > 0 ? r_c : dfl::neg(r_c));
+                rx = dfl::sub(rx, dfl::df{os.x, os.y});
+                ry = dfl::sub(ry, dfl::df{os.z, os.w});
+                dfl::df xx, xy, yy;
+                pair_value_pw(rx, ry, xi2, pref, zc, cS, cE, K, inv_w, kscale, xx, xy, yy);
+                e = PairEntryDF{xx.hi, xy.hi, yy.hi, s, xx.lo, xy.lo, yy.lo, 0.0f};
+            } else {
+                e = PairEntryDF{0.0f, 0.0f, 0.0f, t, 0.0f, 0.0f, 0.0f, 0.0f};
+            }
+            p64[r0 + (size_t)k * 32] = e;
         }
-        p64[r0 + (size_t)k * 32] = e;
     }
 }
 
@@ -481,20 +522,39 @@ static fbim_status build_pairs_from32(fbim_handle_s* h) {
         ++h->layout_version;
     }
     k_off_df<<<(N + 255) / 256, 256, 0, h->stream>>>(N, (const double2*)e.off, e.off_df);
-    dfl::ChebDF cdf;
-    cdf.deg = h->cheb64.deg;
-    for (int k = 0; k <= cdf.deg; ++k) {
-        const dfl::df c = dfl::from_double(h->cheb64.c[k]);
-        cdf.hi[k] = c.hi;
-        cdf.lo[k] = c.lo;
+    if (!e.pw) {
+        // piece half-width <= 0.09 keeps both series' truncation near 1e-15 at degree 8
+        const int K = std::max(8, (int)std::ceil(h->zmax / 0.18));
+        std::vector<float> zc;
+        std::vector<double> cS, cE;
+        float inv_w = 0.f;
+        e1_piecewise(h->zmax, K, kPwDeg, zc, inv_w, cS, cE);
+        std::vector<float> tab(zc);
+        for (const auto* c : {&cS, &cE})
+            for (double v : *c) {
+                const dfl::df x = dfl::from_double(v);
+                tab.push_back(x.hi);
+                tab.push_back(x.lo);
+            }
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.pw, tab.size() * sizeof(float)));
+        FBIM_CUDA_TRY(h, cudaMemcpy(e.pw, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
+        e.pw_K = K;
+        e.pw_inv_w = inv_w;
+        e.pw_kscale = (float)(K / h->zmax);
+        const size_t smem = tab.size() * sizeof(float);
+        FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_pair_from32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    const dfl::df sc = dfl::from_double(h->cheb64.scale);
-    cdf.s_hi = sc.hi;
-    cdf.s_lo = sc.lo;
-    k_pair_from32<<<(unsigned)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(
+    const size_t smem = ((size_t)e.pw_K * (1 + 4 * (kPwDeg + 1))) * sizeof(float);
+    int sms = 0, dev = 0;
+    FBIM_CUDA_TRY(h, cudaGetDevice(&dev));
+    FBIM_CUDA_TRY(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 0;
+    FBIM_CUDA_TRY(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_from32, 256, smem));
+    const unsigned blocks = (unsigned)std::min<long long>(((long long)N + 7) / 8, (long long)std::max(per_sm, 1) * sms);
+    k_pair_from32<<<blocks, 256, smem, h->stream>>>(
         N, h->n_box, dfl::from_double(h->r_c), h->perm, h->cell, e.off_df, f.slice_start, f.row_count,
         (const PairEntry<float>*)f.pairs, dfl::from_double(h->xi * h->xi),
-        dfl::from_double(1.0 / (4.0 * M_PI * h->eta)), cdf, (PairEntryDF*)e.pairs);
+        dfl::from_double(1.0 / (4.0 * M_PI * h->eta)), e.pw, e.pw_K, e.pw_inv_w, e.pw_kscale, (PairEntryDF*)e.pairs);
     h->launches += 2;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     e.n_padded = f.n_padded;
@@ -877,6 +937,7 @@ static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.pairs);
     cudaFree(e.off_df);
     cudaFree(e.mu_df);
+    cudaFree(e.pw);
     cudaFree(e.slice_start);
     cudaFree(e.row_count);
     if (e.plan_f) cufftDestroy(e.plan_f);

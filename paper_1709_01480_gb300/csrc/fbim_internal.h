@@ -82,6 +82,11 @@ struct EwaldBuffers {
     bool pairs_df = false;
     float4* off_df = nullptr;    // [N] (x hi, x lo, y hi, y lo), cell-sorted
     float4* mu_df = nullptr;     // [N] forces, cell-sorted
+    // piecewise tables of its pair values (e1_piecewise): [K] piece centres, then
+    // [2][K][kPwDeg + 1] float-float coefficients (S, then e^{-z}) as (hi, lo)
+    float* pw = nullptr;
+    int pw_K = 0;
+    float pw_inv_w = 0.f, pw_kscale = 0.f;  // 1 / half-width, K / zmax
     int wave_variant = 1;        // 0: tile kernels (shared memory), 1: warp-per-node kernels
     float variant_ms[2] = {0, 0};  // autotuner timings of spread + interp per variant
     bool ready = false;
@@ -90,6 +95,7 @@ struct EwaldBuffers {
 // Chebyshev expansion of S(z) = (E1(z) + ln z)/2 - e^{-z} on [0, zmax], so that
 // the real-space kernel coefficient E1(z)/2 - e^{-z} = S(z) - ln(z)/2.
 constexpr int kChebMax = 48;
+constexpr int kPwDeg = 8;  // degree of the piecewise pair-value polynomials (float-float list)
 template <typename T>
 struct ChebE1 {
     T c[kChebMax];
@@ -142,7 +148,8 @@ struct fbim_handle_s {
     int* cell_fill = nullptr;    // [n_cell]
     int* perm = nullptr;         // [N] slot -> node
     int* slot = nullptr;         // [N] node -> slot
-    int* flags = nullptr;        // [4] device error flags
+    int* flags = nullptr;        // [4] device flags: 0 non-finite coordinates, 1 coincident nodes,
+                                 // 3 scratch of update_positions_if_moved
     double* band_dev = nullptr;  // [n_p][2 band + 1][2][2] symmetrised M(a)_ref
     int2* gbase = nullptr;       // [N] nearest grid point of each node (body order)
     int* tile_start = nullptr;   // [n_tile^2 + 1] wave-space tiles of TS x TS grid points
@@ -196,6 +203,12 @@ double host_e1(double z);
 fbim_status alpert_rule(int order, std::vector<double>& v, std::vector<double>& w, int& a, std::string& err);
 fbim_status alpert_reference_band(fbim_handle_s* h, std::vector<double>& band_out);
 void e1_chebyshev(double zmax, int deg, std::vector<double>& coef);
+// Piecewise polynomials on K equal pieces of [0, zmax] for the float-float pair values:
+// on piece k, z = zc[k] + t / inv_w (zc[k] and inv_w floats, |t| <= 1.05), and
+// S(z) = (E1(z) + ln z)/2 - e^{-z} = sum_j cS[k (D+1) + j] t^j (interpolated at the
+// piece's Chebyshev points), e^{-z} = sum_j cE[k (D+1) + j] t^j (its Taylor series).
+void e1_piecewise(double zmax, int K, int D, std::vector<float>& zc, float& inv_w, std::vector<double>& cS,
+                  std::vector<double>& cE);
 void g_real_host(double rx, double ry, double xi, double eta, double G[4]);
 void reference_blocks(fbim_handle_s* h, const std::vector<double>& band_sym, std::vector<double>& Mr,
                       std::vector<double>& Mfull);
@@ -211,6 +224,9 @@ void scan_exclusive(cudaStream_t st, const int* in, int n, int* out);
 size_t scan_storage(int n);
 // copy body coordinates Q_dev (device, [n_b][3]) into the handle and rebuild the geometry
 fbim_status update_positions(fbim_handle_s* h, const double* Q_dev);
+// The same, skipped when Q_dev holds the current body coordinates bit for bit (one
+// comparison kernel and a host sync instead of the rebuild).
+fbim_status update_positions_if_moved(fbim_handle_s* h, const double* Q_dev);
 
 // solvers (solver.cu)
 void free_solver(fbim_handle_s* h);

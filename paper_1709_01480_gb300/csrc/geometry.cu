@@ -216,4 +216,23 @@ fbim_status update_positions(fbim_handle_s* h, const double* Q_dev) {
     return build_geometry(h);
 }
 
+namespace {
+__global__ void k_differs(int n, const double* __restrict__ a, const double* __restrict__ b, int* __restrict__ flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && __double_as_longlong(a[i]) != __double_as_longlong(b[i])) atomicOr(flag, 1);
+}
+}  // namespace
+
+fbim_status update_positions_if_moved(fbim_handle_s* h, const double* Q_dev) {
+    if (Q_dev == h->Q) return update_positions(h, Q_dev);
+    const int n = 3 * h->n_b;
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(h->flags + 3, 0, sizeof(int), h->stream));
+    k_differs<<<(n + 255) / 256, 256, 0, h->stream>>>(n, Q_dev, h->Q, h->flags + 3);
+    h->launches += 1;
+    int moved = 1;
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(&moved, h->flags + 3, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return moved ? update_positions(h, Q_dev) : FBIM_OK;
+}
+
 }  // namespace fbim

@@ -63,8 +63,9 @@ fbim_status rfd_step(fbim_handle_s* h, const double* F, double dt, double kT, do
     fbim_status st = FBIM_OK;
     int it = 0, total = 0;
     auto run = [&]() -> fbim_status {
-        // (1) geometry at Q, slip, and the velocity N F + N^1/2 W
-        FBIM_TRY(update_positions(h, Q));
+        // (1) geometry at Q (already in place when the previous step left the handle
+        // there), slip, and the velocity N F + N^1/2 W
+        FBIM_TRY(update_positions_if_moved(h, Q));
         int lz = 0;
         FBIM_TRY(brownian_slip(h, seed, 3 * step, kT, dt, W_r, Z_w, std::max(tol, 1e-12), 200, slip, &lz));
         fbim_status s1 = mobility_solve(h, F, slip, tol, max_iter, U, nullptr, &it, nullptr, false);

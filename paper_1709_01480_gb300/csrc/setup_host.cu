@@ -78,6 +78,71 @@ void e1_chebyshev(double zmax, int deg, std::vector<double>& coef) {
     coef[0] *= 0.5;
 }
 
+// S(z) = (E1(z) + ln z)/2 - e^{-z} in long double: the power series of its entire
+// part for z < 3 (no logarithm to cancel; also valid for z < 0), E1 by its continued
+// fraction above.
+static ld s_ld(ld z) {
+    if (z < 3) {
+        ld term = 1, sum = 0;
+        for (int k = 1; k <= 80; ++k) {
+            term *= -z / k;
+            const ld add = term / k;
+            sum += add;
+            if (fabsl(add) <= 1e-24L * fabsl(sum)) break;
+        }
+        return 0.5L * (-kEulerGamma - sum) - expl(-z);
+    }
+    return 0.5L * (e1_ld(z) + logl(z)) - expl(-z);
+}
+
+void e1_piecewise(double zmax, int K, int D, std::vector<float>& zc, float& inv_w, std::vector<double>& cS,
+                  std::vector<double>& cE) {
+    const ld w = (ld)zmax / (2 * K);
+    inv_w = (float)(1.0L / w);
+    const ld hw = 1.0L / (ld)inv_w;  // the half-width the device's t = (z - z_c) inv_w implies
+    const int n = D + 1;
+    zc.assign(K, 0.f);
+    cS.assign((size_t)K * n, 0.0);
+    cE.assign((size_t)K * n, 0.0);
+    // monomial coefficients of T_0 .. T_D: T[m][j] = coefficient of t^j in T_m(t)
+    std::vector<ld> T((size_t)n * n, 0.0L);
+    T[0] = 1;
+    if (n > 1) T[(size_t)1 * n + 1] = 1;
+    for (int m = 2; m < n; ++m)
+        for (int j = 0; j < n; ++j)
+            T[(size_t)m * n + j] = (j > 0 ? 2 * T[(size_t)(m - 1) * n + j - 1] : 0) - T[(size_t)(m - 2) * n + j];
+    const ld margin = 1.05L;  // t may pass +-1 by the rounding of z_c, inv_w and the piece index
+    std::vector<ld> f(n), a(n);
+    for (int k = 0; k < K; ++k) {
+        zc[k] = (float)((2 * k + 1) * w);
+        const ld c = zc[k];
+        for (int i = 0; i < n; ++i) {
+            const ld t = margin * cosl(kPi * (i + 0.5L) / n);
+            f[i] = s_ld(c + hw * t);  // the first piece's points reach below 0: S is entire
+        }
+        for (int j = 0; j < n; ++j) {
+            ld acc = 0;
+            for (int i = 0; i < n; ++i) acc += f[i] * cosl(j * kPi * (i + 0.5L) / n);
+            a[j] = acc * 2 / n;
+        }
+        a[0] *= 0.5L;
+        // p(t) = sum_m a_m T_m(t / margin)
+        ld scale = 1;
+        for (int j = 0; j < n; ++j) {
+            ld acc = 0;
+            for (int m = j; m < n; ++m) acc += a[m] * T[(size_t)m * n + j];
+            cS[(size_t)k * n + j] = (double)(acc * scale);
+            scale /= margin;
+        }
+        // e^{-(c + hw t)} = e^{-c} sum_j (-hw)^j t^j / j!
+        ld term = expl(-c);
+        for (int j = 0; j < n; ++j) {
+            cE[(size_t)k * n + j] = (double)term;
+            term *= -hw / (j + 1);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Parameter rules (Sec. 3.2): C_r e^{-xi^2 r_c^2} <= tol, C_w H^(k_max) <= tol,
 // e^{-pi P / 2} <= tol, m = sqrt(pi P), eta_s = (2 w xi / m)^2 with w = P h / 2.
