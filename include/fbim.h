@@ -74,6 +74,11 @@ typedef struct {
                              the least 25 FP32 + 1 FP64 operator applications + 1 geometry update
                              (one mixed-precision solve; 25 FP64 + 1 update for FBIM_FP64).  Set-up
                              then costs a few handle set-ups more.                               */
+    int    fp32_support;  /* Gaussian support of the FP32 operator's wave space (odd; FBIM_FP32
+                             handles), at most the FP64 support.  <= 0 (default): the support rule
+                             e^{-pi P/2} <= max(tol, 1e-7) -- the FP32 operator's own rounding is
+                             ~3e-7, and its refinement corrections need ~1e-4.  Grid, xi and tiles
+                             stay those of the FP64 operator.                                    */
 } fbim_params;
 
 /* Ewald parameters the library settled on (fbim_get_info). */
@@ -98,6 +103,8 @@ typedef struct {
     double grid_tune_ms;     /* tuned cost (ms) of the chosen side's FFT pair, 0 if untuned */
     int    split_candidates; /* cutoffs the split tuner timed (0: r_c as given)          */
     double split_cost_ms;    /* the chosen cutoff's cost per solve-equivalent (ms)      */
+    int    support32;        /* Gaussian support of the FP32 operator (FP32 handles; P otherwise) */
+    double eta_s32;          /* its Gaussian shape parameter                            */
     int    fp64_fft;         /* transforms and Fourier scale of the FP64 operator: 1 float-
                                 float kernels (FP32 handles with an even 5-smooth grid),
                                 -1 cuFFT double, 0 not yet set up (first FP64 use)      */

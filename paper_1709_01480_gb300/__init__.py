@@ -56,7 +56,7 @@ class Params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("alpert_order", ctypes.c_int), ("grid", ctypes.c_int),
                 ("support", ctypes.c_int), ("eta", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("restart", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("grid_tune", ctypes.c_int), ("split_tune", ctypes.c_int)]
+                ("grid_tune", ctypes.c_int), ("split_tune", ctypes.c_int), ("fp32_support", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -70,7 +70,7 @@ class Info(ctypes.Structure):
                 ("wave_variant", ctypes.c_int), ("variant_ms", ctypes.c_double * 2),
                 ("launches", ctypes.c_longlong), ("grid_min", ctypes.c_int), ("grid_tune_ms", ctypes.c_double),
                 ("split_candidates", ctypes.c_int), ("split_cost_ms", ctypes.c_double),
-                ("fp64_fft", ctypes.c_int)]
+                ("support32", ctypes.c_int), ("eta_s32", ctypes.c_double), ("fp64_fft", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -193,7 +193,7 @@ class FBIM:
 
     def __init__(self, ref_nodes, Q, L, *, tol=1e-8, r_c=0.0, xi=0.0, precision="fp64", order=4,
                  grid=0, support=0, eta=1.0, stream=None, device=0, restart=60, wave="auto", grid_tune=True,
-                 split_tune=False):
+                 split_tune=False, fp32_support=0):
         ref = np.ascontiguousarray(ref_nodes, dtype=np.float64)
         Qh = np.ascontiguousarray(Q, dtype=np.float64)
         self.n_p = ref.shape[0]
@@ -210,6 +210,7 @@ class FBIM:
         p.autotune = {"auto": 1, "tile": 0, "warp": 2}[wave]
         p.grid_tune = 1 if grid_tune else 0
         p.split_tune = 1 if split_tune else 0
+        p.fp32_support = fp32_support
         if stream is None:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream

@@ -85,6 +85,7 @@ extern "C" fbim_status fbim_default_params(fbim_params* p) {
     p->autotune = 1;
     p->grid_tune = 1;
     p->split_tune = 0;
+    p->fp32_support = 0;
     return FBIM_OK;
 }
 
@@ -198,6 +199,14 @@ static fbim_status setup_one(fbim_handle* out, int n_b, int n_p, const double* r
         h->TS = TS;
         h->n_tile = M / TS;
         h->n_box = nbox;
+        // FP32 operator: its own support on the same grid (the support rule at the
+        // larger of tol and 1e-7), the Gaussian shape following it
+        {
+            int P32 = p.fp32_support > 0 ? (p.fp32_support | 1)
+                                         : (int)std::ceil(2.0 * std::log(1.0 / std::max(tol, 1e-7)) / M_PI);
+            if (P32 % 2 == 0) ++P32;
+            h->P32 = p.precision == FBIM_FP32 ? std::max(3, std::min(P32, P)) : P;
+        }
         h->r_c = rc;
         h->xi = xx;
         h->M = M;
@@ -206,6 +215,9 @@ static fbim_status setup_one(fbim_handle* out, int n_b, int n_p, const double* r
         {
             double wdt = P * h->h / 2.0, m = std::sqrt(M_PI * P);
             h->eta_s = std::pow(2.0 * wdt * h->xi / m, 2);
+            wdt = h->P32 * h->h / 2.0;
+            m = std::sqrt(M_PI * h->P32);
+            h->eta_s32 = std::pow(2.0 * wdt * h->xi / m, 2);
         }
         if (!(h->eta_s < 1.0) || P > M || P > 23) {
             h->fail("Gaussian support/grid inconsistent (need eta_s < 1, P <= min(M, 23), i.e. tol >= 1e-15)");
@@ -412,6 +424,8 @@ extern "C" fbim_status fbim_get_info(fbim_handle h, fbim_info* info) {
     info->grid = h->M;
     info->support = h->P;
     info->eta_s = h->eta_s;
+    info->support32 = h->P32;
+    info->eta_s32 = h->eta_s32;
     info->h = h->h;
     info->alpert_order = h->order;
     info->alpert_nodes = h->aj;

@@ -615,9 +615,9 @@ fbim_status refresh_offsets(fbim_handle_s* h) {
     h->launches += 1;
     if constexpr (std::is_same<T, double>::value) {
         if (e.wtab) {
-            const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
-            const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
-            node_weights<double>(h->stream, h->N, tg, alpha * h->h * h->h, 2.0 * h->xi * h->xi / (M_PI * h->eta_s),
+            const TileGeom tg{h->M, h->TS, h->n_tile, e.P, (e.P - 1) / 2};
+            const double alpha = 2.0 * h->xi * h->xi / e.eta_s;
+            node_weights<double>(h->stream, h->N, tg, alpha * h->h * h->h, 2.0 * h->xi * h->xi / (M_PI * e.eta_s),
                                  e.tfrac, e.wtab);
             h->launches += 1;
         }
@@ -633,10 +633,10 @@ static fbim_status autotune_wave(fbim_handle_s* h) {
     auto& e = bufs<T>(h);
     using T2 = typename V2<T>::type;
     const size_t M = h->M;
-    const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
-    const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
+    const TileGeom tg{h->M, h->TS, h->n_tile, e.P, (e.P - 1) / 2};
+    const double alpha = 2.0 * h->xi * h->xi / e.eta_s;
     const T ah2 = (T)(alpha * h->h * h->h);
-    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
+    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * e.eta_s));
     std::vector<T2> ones(h->N);
     for (auto& o : ones) o.x = o.y = T(1);
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.mu_t, ones.data(), h->N * sizeof(T2), cudaMemcpyHostToDevice, h->stream));
@@ -678,6 +678,8 @@ template <typename T>
 fbim_status ensure_ewald(fbim_handle_s* h) {
     auto& e = bufs<T>(h);
     if (e.ready) return FBIM_OK;
+    e.P = std::is_same<T, float>::value ? h->P32 : h->P;
+    e.eta_s = std::is_same<T, float>::value ? h->eta_s32 : h->eta_s;
     using T2 = typename V2<T>::type;
     using C = typename Cplx<T>::type;
     const size_t N = h->N, M = h->M, Mh = h->M / 2 + 1;
@@ -692,11 +694,11 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_r, N * sizeof(double2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.v_band, N * sizeof(double2)));
     {
-        const size_t W = h->TS + h->P - 1;
+        const size_t W = h->TS + e.P - 1;
         FBIM_CUDA_TRY(h, cudaMalloc(&e.ring, (size_t)h->n_tile * h->n_tile * 2 * W * W * sizeof(T)));
     }
     FBIM_CUDA_TRY(h, cudaMalloc(&e.grid, 2 * M * M * sizeof(T)));
-    if (std::is_same<T, double>::value) FBIM_CUDA_TRY(h, cudaMalloc(&e.wtab, N * 2 * h->P * sizeof(T)));
+    if (std::is_same<T, double>::value) FBIM_CUDA_TRY(h, cudaMalloc(&e.wtab, N * 2 * e.P * sizeof(T)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.spec, 2 * M * Mh * sizeof(C)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, scan_storage((int)n_slice) * sizeof(int)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.row_count, (n_slice * 33 + 1) * sizeof(int)));
@@ -709,7 +711,7 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
                                     FftType<T>::inv, 2));
     FBIM_CUFFT_TRY(h, cufftSetStream(e.plan_f, h->stream));
     FBIM_CUFFT_TRY(h, cufftSetStream(e.plan_i, h->stream));
-    FBIM_CUDA_TRY(h, tile_set_smem<T>(TileGeom{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2}));
+    FBIM_CUDA_TRY(h, tile_set_smem<T>(TileGeom{h->M, h->TS, h->n_tile, e.P, (e.P - 1) / 2}));
     if constexpr (std::is_same<T, double>::value) {
         if (h->precision == FBIM_FP32) FBIM_TRY(wfft_setup(h));
     }
@@ -758,10 +760,10 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         k_band<<<(N + tb - 1) / tb, tb, 0, h->aux>>>(N, h->n_p, h->band, h->rot, h->band_dev, e.mu_r, e.v_band);
         FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_join, h->aux));
     }
-    const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
-    const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
+    const TileGeom tg{h->M, h->TS, h->n_tile, e.P, (e.P - 1) / 2};
+    const double alpha = 2.0 * h->xi * h->xi / e.eta_s;
     const T ah2 = (T)(alpha * h->h * h->h);
-    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
+    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * e.eta_s));
     if (wave) {
         const size_t M = h->M, Mh = h->M / 2 + 1;
         if (e.wave_variant == 1) {
@@ -791,7 +793,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
             const double h4 = h->h * h->h * h->h * h->h;
             size_t ns = M * Mh;
             k_scale<T><<<(unsigned)((ns + tb - 1) / tb), tb, 0, h->stream>>>(
-                (int)M, (T)(2.0 * M_PI / h->L), (T)(1.0 / (4.0 * h->xi * h->xi)), (T)(1.0 - h->eta_s),
+                (int)M, (T)(2.0 * M_PI / h->L), (T)(1.0 / (4.0 * h->xi * h->xi)), (T)(1.0 - e.eta_s),
                 (T)(h4 / (h->eta * V)), (C*)e.spec);
             h->mark(FBIM_ST_SCALE);
             FBIM_CUFFT_TRY(h, FftType<T>::i(e.plan_i, (C*)e.spec, e.grid));
@@ -901,13 +903,13 @@ fbim_status apply_noise(fbim_handle_s* h, const double* Z, unsigned long long se
     const size_t M = h->M, Mh = h->M / 2 + 1, ns = M * Mh;
     const double V = h->L * h->L;
     k_noise_spec<T><<<(unsigned)((ns + tb - 1) / tb), tb, 0, h->stream>>>(
-        (int)M, (T)(2.0 * M_PI / h->L), (T)(1.0 / (4.0 * h->xi * h->xi)), (T)(1.0 - h->eta_s),
+        (int)M, (T)(2.0 * M_PI / h->L), (T)(1.0 / (4.0 * h->xi * h->xi)), (T)(1.0 - e.eta_s),
         (T)(h->h * h->h / std::sqrt(h->eta * V)), Z, seed, counter, (C*)e.spec);
     FBIM_CUFFT_TRY(h, FftType<T>::i(e.plan_i, (C*)e.spec, e.grid));
-    const TileGeom tg{h->M, h->TS, h->n_tile, h->P, (h->P - 1) / 2};
-    const double alpha = 2.0 * h->xi * h->xi / h->eta_s;
+    const TileGeom tg{h->M, h->TS, h->n_tile, e.P, (e.P - 1) / 2};
+    const double alpha = 2.0 * h->xi * h->xi / e.eta_s;
     const T ah2 = (T)(alpha * h->h * h->h);
-    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * h->eta_s));
+    const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * e.eta_s));
     if (e.wave_variant == 1)
         warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
     else

@@ -89,6 +89,8 @@ struct EwaldBuffers {
     float pw_inv_w = 0.f, pw_kscale = 0.f;  // 1 / half-width, K / zmax
     int wave_variant = 1;        // 0: tile kernels (shared memory), 1: warp-per-node kernels
     float variant_ms[2] = {0, 0};  // autotuner timings of spread + interp per variant
+    int P = 0;               // Gaussian support of this precision's wave space
+    double eta_s = 0;        // its Gaussian shape
     bool ready = false;
 };
 
@@ -128,6 +130,8 @@ struct fbim_handle_s {
     double L = 0, xi = 0, r_c = 0, tol = 0, eta = 1;
     int n_box = 0, M = 0, P = 0;
     double eta_s = 0, h = 0;
+    int P32 = 0;           // Gaussian support of the FP32 operator (<= P; P for FP64 handles)
+    double eta_s32 = 0;    // its Gaussian shape
     int order = 4, aj = 0, aa = 0, band = 0;  // Alpert: nodes per side, window, half band
     int precision = FBIM_FP64;
     int device = 0;
