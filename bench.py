@@ -465,8 +465,10 @@ def run_gpu(args):
                        "solve_tol": SOLVE_TOL, "step": "EM-RFD step: slip + 3 mobility solves",
                        "dt": DT, "kT": KT, "rfd_delta": delta, "xi": info["xi"], "r_c": info["r_c"],
                        "grid": M, "grid_min": info["grid_min"], "split_candidates": info["split_candidates"],
-                       "support": info["support"], "n_pairs_within_rc": n_pairs,
-                       "pair_entries": n_entries, "tile": info["tile"], "wave_variant": info["wave_variant"],
+                       "support": info["support"], "support32": info["support32"], "n_pairs_within_rc": n_pairs,
+                       "pair_entries": n_entries, "tile": info["tile"],
+                       "spread_variant": ("tile", "warp")[info["wave_variant"]],
+                       "interp_variant": ("tile", "warp")[info["interp_variant"]],
                        "l2": "flushed (256 MB write) before every timed step",
                        "precision": "FP32 Ewald operator and preconditioner GEMM; FP64 Alpert band, "
                                     "Krylov vectors, orthogonalisation and refinement residuals"},

@@ -95,14 +95,16 @@ typedef struct {
     int    tile;          /* wave-space tile side (divides grid)                   */
     long long pair_entries;  /* stored real-space pair entries of the handle's precision
                                 (ordered pairs within r_c plus sliced-ELL padding)     */
-    int    wave_variant;     /* spread/interp kernels in use: 0 tile, 1 warp-per-node  */
-    double variant_ms[2];    /* autotuner timings (ms) of spread + interp per variant  */
+    int    wave_variant;     /* spread kernel in use: 0 tile, 1 warp-per-node          */
+    double variant_ms[2];    /* autotuner timings (ms) of the spread per variant       */
     long long launches;      /* kernels this library has launched for the handle so far
                                 (library calls such as cuFFT and cuBLAS not included)  */
     int    grid_min;         /* the grid rule's smallest admissible side M_min          */
     double grid_tune_ms;     /* tuned cost (ms) of the chosen side's FFT pair, 0 if untuned */
     int    split_candidates; /* cutoffs the split tuner timed (0: r_c as given)          */
     double split_cost_ms;    /* the chosen cutoff's cost per solve-equivalent (ms)      */
+    int    interp_variant;   /* interpolation kernel in use: 0 tile, 1 warp-per-node   */
+    double interp_ms[2];     /* autotuner timings (ms) of the interpolation per variant */
     int    support32;        /* Gaussian support of the FP32 operator (FP32 handles; P otherwise) */
     double eta_s32;          /* its Gaussian shape parameter                            */
     int    fp64_fft;         /* transforms and Fourier scale of the FP64 operator: 1 float-

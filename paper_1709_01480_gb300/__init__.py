@@ -70,11 +70,13 @@ class Info(ctypes.Structure):
                 ("wave_variant", ctypes.c_int), ("variant_ms", ctypes.c_double * 2),
                 ("launches", ctypes.c_longlong), ("grid_min", ctypes.c_int), ("grid_tune_ms", ctypes.c_double),
                 ("split_candidates", ctypes.c_int), ("split_cost_ms", ctypes.c_double),
+                ("interp_variant", ctypes.c_int), ("interp_ms", ctypes.c_double * 2),
                 ("support32", ctypes.c_int), ("eta_s32", ctypes.c_double), ("fp64_fft", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["variant_ms"] = list(self.variant_ms)
+        d["interp_ms"] = list(self.interp_ms)
         return d
 
 

@@ -435,9 +435,12 @@ extern "C" fbim_status fbim_get_info(fbim_handle h, fbim_info* info) {
     info->tile = h->TS;
     const bool f32 = h->precision == FBIM_FP32;
     info->pair_entries = f32 ? h->e32.n_padded : h->e64.n_padded;
-    info->wave_variant = f32 ? h->e32.wave_variant : h->e64.wave_variant;
-    info->variant_ms[0] = f32 ? h->e32.variant_ms[0] : h->e64.variant_ms[0];
-    info->variant_ms[1] = f32 ? h->e32.variant_ms[1] : h->e64.variant_ms[1];
+    info->wave_variant = f32 ? h->e32.spread_variant : h->e64.spread_variant;
+    info->interp_variant = f32 ? h->e32.interp_variant : h->e64.interp_variant;
+    for (int v = 0; v < 2; ++v) {
+        info->variant_ms[v] = f32 ? h->e32.variant_ms[0][v] : h->e64.variant_ms[0][v];
+        info->interp_ms[v] = f32 ? h->e32.variant_ms[1][v] : h->e64.variant_ms[1][v];
+    }
     info->launches = h->launches;
     info->grid_min = h->M_min;
     info->grid_tune_ms = h->grid_tune_ms;

@@ -626,8 +626,9 @@ fbim_status refresh_offsets(fbim_handle_s* h) {
     return build_pairs<T>(h);
 }
 
-// Autotuner: time spread + interpolation of both kernel variants on the current
-// geometry (forces = 1 on every node) and keep the faster one.
+// Autotuner: time the spread and the interpolation of both kernel variants on the
+// current geometry (forces = 1 on every node), each stage on its own (the spread
+// variants leave the same grid), and keep the faster variant of each.
 template <typename T>
 static fbim_status autotune_wave(fbim_handle_s* h) {
     auto& e = bufs<T>(h);
@@ -640,37 +641,43 @@ static fbim_status autotune_wave(fbim_handle_s* h) {
     std::vector<T2> ones(h->N);
     for (auto& o : ones) o.x = o.y = T(1);
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.mu_t, ones.data(), h->N * sizeof(T2), cudaMemcpyHostToDevice, h->stream));
-    cudaEvent_t ev[3];
+    cudaEvent_t ev[2];
     for (auto& x : ev) FBIM_CUDA_TRY(h, cudaEventCreate(&x));
-    float best = 1e30f;
-    int choice = 1;
-    for (int variant = 0; variant < 2; ++variant) {
-        float tot = 0;
-        for (int rep = 0; rep < 4; ++rep) {
-            cudaEventRecord(ev[0], h->stream);
-            if (variant == 1) {
-                cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream);
-                warp_spread<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.mu_t, e.grid);
-                warp_interp<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
-            } else {
-                tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
-                tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
+    auto spread = [&](int v) {
+        if (v == 1) {
+            cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream);
+            warp_spread<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.mu_t, e.grid);
+        } else {
+            tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
+        }
+    };
+    auto interp = [&](int v) {
+        if (v == 1)
+            warp_interp<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
+        else
+            tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
+    };
+    for (int stage = 0; stage < 2; ++stage) {
+        for (int v = 0; v < 2; ++v) {
+            float tot = 0;
+            for (int rep = 0; rep < 4; ++rep) {
+                cudaEventRecord(ev[0], h->stream);
+                if (stage == 0)
+                    spread(v);
+                else
+                    interp(v);
+                cudaEventRecord(ev[1], h->stream);
+                cudaEventSynchronize(ev[1]);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, ev[0], ev[1]);
+                if (rep > 0) tot += ms;  // first repetition warms up
             }
-            cudaEventRecord(ev[1], h->stream);
-            cudaEventSynchronize(ev[1]);
-            float ms = 0;
-            cudaEventElapsedTime(&ms, ev[0], ev[1]);
-            if (rep > 0) tot += ms;  // first repetition warms up
+            e.variant_ms[stage][v] = tot / 3;
         }
-        e.variant_ms[variant] = tot / 3;
-        if (tot < best) {
-            best = tot;
-            choice = variant;
-        }
+        (stage == 0 ? e.spread_variant : e.interp_variant) = e.variant_ms[stage][1] <= e.variant_ms[stage][0] ? 1 : 0;
     }
     for (auto& x : ev) cudaEventDestroy(x);
     FBIM_CUDA_TRY(h, cudaGetLastError());
-    e.wave_variant = choice;
     return FBIM_OK;
 }
 
@@ -720,7 +727,7 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     if (h->autotune == 1)
         FBIM_TRY(autotune_wave<T>(h));
     else
-        e.wave_variant = h->autotune == 2 ? 1 : 0;
+        e.spread_variant = e.interp_variant = h->autotune == 2 ? 1 : 0;
     return FBIM_OK;
 }
 
@@ -766,7 +773,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * e.eta_s));
     if (wave) {
         const size_t M = h->M, Mh = h->M / 2 + 1;
-        if (e.wave_variant == 1) {
+        if (e.spread_variant == 1) {
             FBIM_CUDA_TRY(h, cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream));
             warp_spread<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.mu_t, e.grid);
         } else {
@@ -805,7 +812,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         h->mark(FBIM_ST_PAIRS);
     }
     if (wave) {
-        if (e.wave_variant == 1)
+        if (e.interp_variant == 1)
             warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
         else
             tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
@@ -818,7 +825,7 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
                                                          (const T2*)e.v_s, (const T2*)e.v_t, e.v_band,
                                                          (double2*)v);
     h->mark(FBIM_ST_FINISH);
-    h->launches += 2 + (wave ? (e.wave_variant == 1 ? 3 : 4) : 0) + (real ? 2 : 0);
+    h->launches += 2 + (wave ? (e.spread_variant == 1 ? 3 : 4) : 0) + (real ? 2 : 0);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     h->collect();
     return FBIM_OK;
@@ -910,7 +917,7 @@ fbim_status apply_noise(fbim_handle_s* h, const double* Z, unsigned long long se
     const double alpha = 2.0 * h->xi * h->xi / e.eta_s;
     const T ah2 = (T)(alpha * h->h * h->h);
     const T g0 = (T)(2.0 * h->xi * h->xi / (M_PI * e.eta_s));
-    if (e.wave_variant == 1)
+    if (e.interp_variant == 1)
         warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
     else
         tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);

@@ -87,8 +87,9 @@ struct EwaldBuffers {
     float* pw = nullptr;
     int pw_K = 0;
     float pw_inv_w = 0.f, pw_kscale = 0.f;  // 1 / half-width, K / zmax
-    int wave_variant = 1;        // 0: tile kernels (shared memory), 1: warp-per-node kernels
-    float variant_ms[2] = {0, 0};  // autotuner timings of spread + interp per variant
+    int spread_variant = 1;      // 0: tile kernel (shared memory), 1: warp-per-node kernel
+    int interp_variant = 1;      // the same for the interpolation
+    float variant_ms[2][2] = {}; // autotuner timings [spread, interp][tile, warp]
     int P = 0;               // Gaussian support of this precision's wave space
     double eta_s = 0;        // its Gaussian shape
     bool ready = false;
