@@ -59,7 +59,7 @@ ITERS_PER_SOLVE_REF = 24
 # capture summarised in profiles/ewald_matvec_dram_starfish1024.md (cutoff L/91 and
 # grid 1296^2, the split and grid tuners' choice); valid for the kernels and the
 # configuration as they are now.
-MEASURED_DRAM_BYTES = {"pairs": 163.19e6, "spread": 15.20e6, "interp": 14.91e6, "finish": 5.31e6,
+MEASURED_DRAM_BYTES = {"pairs": 163.14e6, "spread": 14.77e6, "interp": 14.72e6, "finish": 5.25e6,
                        "scale": 13.45e6, "gather": 3.17e6}
 
 

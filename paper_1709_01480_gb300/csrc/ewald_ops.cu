@@ -536,13 +536,20 @@ static fbim_status build_pairs_from32(fbim_handle_s* h) {
                 tab.push_back(x.hi);
                 tab.push_back(x.lo);
             }
+        // the kernel's limit, raised to the device maximum (shared by all handles)
+        int dev = 0, optin = 0;
+        FBIM_CUDA_TRY(h, cudaGetDevice(&dev));
+        FBIM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (tab.size() * sizeof(float) > (size_t)optin) {
+            h->fail("piecewise pair-value tables exceed shared memory (xi r_c too large)");
+            return FBIM_ERR_INVALID_ARG;
+        }
         FBIM_CUDA_TRY(h, cudaMalloc(&e.pw, tab.size() * sizeof(float)));
         FBIM_CUDA_TRY(h, cudaMemcpy(e.pw, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
         e.pw_K = K;
         e.pw_inv_w = inv_w;
         e.pw_kscale = (float)(K / h->zmax);
-        const size_t smem = tab.size() * sizeof(float);
-        FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_pair_from32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_pair_from32, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     }
     const size_t smem = ((size_t)e.pw_K * (1 + 4 * (kPwDeg + 1))) * sizeof(float);
     int sms = 0, dev = 0;

@@ -382,9 +382,11 @@ fbim_status wfft_setup(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const size_t sx = smem_x<A>(M), sy = smem_y<A>(M);
     if (sx > (size_t)optin || sy > (size_t)optin) return FBIM_OK;
-    FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_x_fwd<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx));
-    FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_x_inv<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sx));
-    FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_y_scale<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sy));
+    // the limit belongs to the kernel, not the handle: the device maximum, so that
+    // handles of other sizes never lower it under this one's launches
+    FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_x_fwd<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_x_inv<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+    FBIM_CUDA_TRY(h, cudaFuncSetAttribute(k_fft_y_scale<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
     FBIM_TRY(upload_constants(h));
     std::vector<typename A::W> tw(M);
     for (int m = 0; m < M; ++m) {

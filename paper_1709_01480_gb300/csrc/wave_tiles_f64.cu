@@ -10,17 +10,25 @@ namespace fbim {
 
 static int pmax_for(int P) { return P <= 9 ? 9 : P <= 13 ? 13 : P <= 17 ? 17 : P <= 23 ? 23 : 0; }
 
+// The kernels' dynamic shared-memory limit is a property of the kernel, not of a
+// handle: it is raised to the device's opt-in maximum, and this handle's sizes are
+// checked against that, so that handles of different sizes never lower it under one
+// another's launches.
 template <>
 cudaError_t tile_set_smem<double>(const TileGeom& tg) {
-    cudaError_t err = cudaErrorInvalidValue;
-    const int ss = (int)spread_smem_bytes<double>(tg.TS, tg.P);
-    const int si = (int)interp_smem_bytes<double>(tg.TS, tg.P);
+    int dev = 0, optin = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (err != cudaSuccess) return err;
+    if ((int)spread_smem_bytes<double>(tg.TS, tg.P) > optin || (int)interp_smem_bytes<double>(tg.TS, tg.P) > optin)
+        return cudaErrorInvalidValue;
+    err = cudaErrorInvalidValue;
     switch (pmax_for(tg.P)) {
 #define FBIM_SET(PM)                                                                                        \
     case PM:                                                                                                \
-        err = cudaFuncSetAttribute(k_spread_tiles<double, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, ss); \
+        err = cudaFuncSetAttribute(k_spread_tiles<double, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin); \
         if (err == cudaSuccess)                                                                             \
-            err = cudaFuncSetAttribute(k_interp_tiles<double, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, si); \
+            err = cudaFuncSetAttribute(k_interp_tiles<double, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin); \
         break;
         FBIM_PMAX_CASES(FBIM_SET)
 #undef FBIM_SET

@@ -171,6 +171,26 @@ def test_float_float_fft_matches_cufft_double(torch, fb):
         op64.close()
 
 
+def test_handles_of_different_sizes_interleave(torch, fb):
+    """Kernel launch limits (dynamic shared memory) are per kernel, not per handle: a
+    handle set up after another with a smaller grid must not break the first one's
+    launches (the float-float FFT of a 800^2 grid needs 51 KB per CTA)."""
+    ref, Q = _case(4, 64, 4.0, 0)
+    L, tol, n_box = 4.0, 1e-13, 6
+    xi = _xi(L, n_box, tol)
+    big = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, grid=800, precision="fp32")
+    small = fb.FBIM(ref, Q, L, tol=tol, r_c=L / n_box, xi=xi, grid=160, precision="fp32")
+    mu = torch.tensor(np.random.default_rng(5).standard_normal((4 * 64, 2)), device="cuda")
+    v0 = big.apply_stokeslet_fp64(mu).clone()
+    vs = small.apply_stokeslet_fp64(mu)
+    v1 = big.apply_stokeslet_fp64(mu)
+    assert big.info["fp64_fft"] == 1 and small.info["fp64_fft"] == 1
+    assert float((v1 - v0).abs().max()) == 0.0
+    assert _rel(vs.cpu().numpy(), v0.cpu().numpy()) < 1e-11
+    big.close()
+    small.close()
+
+
 def test_single_body_and_zero_input(torch, fb):
     ref, Q = _case(1, 64, 3.0, 1)
     xi = _xi(3.0, 4, 1e-13)
