@@ -43,10 +43,16 @@ __global__ void k_rot_in(int N, int n_p, const double* __restrict__ rot, const d
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= N) return;
     int b = m / n_p;
-    double c = rot[2 * b], s = rot[2 * b + 1];
-    double ux = in[2 * m], uy = in[2 * m + 1];
-    z[2 * m] = (T)(c * ux + s * uy);
-    z[2 * m + 1] = (T)(-s * ux + c * uy);
+    const double2 u = reinterpret_cast<const double2*>(in)[m];
+    if constexpr (std::is_same<T, float>::value) {
+        // an FP32 preconditioner rotates in FP32 (GB300's FP64 pipe is ~1/74 of its FP32 rate)
+        const float c = (float)rot[2 * b], s = (float)rot[2 * b + 1], ux = (float)u.x, uy = (float)u.y;
+        reinterpret_cast<float2*>(z)[m] = make_float2(fmaf(c, ux, s * uy), fmaf(-s, ux, c * uy));
+    } else {
+        const double c = rot[2 * b], s = rot[2 * b + 1];
+        z[2 * m] = c * u.x + s * u.y;
+        z[2 * m + 1] = -s * u.x + c * u.y;
+    }
 }
 
 // One block per body: U' = -N~ (R^T r_U + K_ref^T g), mu = R (g + H U').
@@ -58,14 +64,16 @@ __global__ void k_body_solve(int n_p, const double* __restrict__ ref, const doub
     const int b = blockIdx.x;
     const int n2 = 2 * n_p;
     const T* gb = g + (size_t)b * n2;
-    double sx = 0, sy = 0, st = 0;
+    // sums over the body's nodes in T (an FP32 preconditioner stays off the FP64 pipe),
+    // the 3x3 solve in FP64
+    T sx = 0, sy = 0, st = 0;
     for (int j = threadIdx.x; j < n_p; j += blockDim.x) {
-        double gx = (double)gb[2 * j], gy = (double)gb[2 * j + 1];
+        const T gx = gb[2 * j], gy = gb[2 * j + 1];
         sx += gx;
         sy += gy;
-        st += ref[2 * j] * gy - ref[2 * j + 1] * gx;
+        st += (T)ref[2 * j] * gy - (T)ref[2 * j + 1] * gx;
     }
-    __shared__ double red[3][32];
+    __shared__ T red[3][32];
     __shared__ double Up[3];
     for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
@@ -102,39 +110,41 @@ __global__ void k_body_solve(int n_p, const double* __restrict__ ref, const doub
         out_U[3 * b + 2] = u2;
     }
     __syncthreads();
-    const double u0 = Up[0], u1 = Up[1], u2 = Up[2];
+    const T u0 = (T)Up[0], u1 = (T)Up[1], u2 = (T)Up[2], cT = (T)c, sT = (T)s;
     for (int i = threadIdx.x; i < n_p; i += blockDim.x) {
-        double mx = (double)gb[2 * i] + (double)H[2 * i] * u0 + (double)H[n2 + 2 * i] * u1 +
-                    (double)H[2 * n2 + 2 * i] * u2;
-        double my = (double)gb[2 * i + 1] + (double)H[2 * i + 1] * u0 + (double)H[n2 + 2 * i + 1] * u1 +
-                    (double)H[2 * n2 + 2 * i + 1] * u2;
-        size_t m = (size_t)b * n_p + i;
-        out_mu[2 * m] = c * mx - s * my;
-        out_mu[2 * m + 1] = s * mx + c * my;
+        const T mx = gb[2 * i] + H[2 * i] * u0 + H[n2 + 2 * i] * u1 + H[2 * n2 + 2 * i] * u2;
+        const T my = gb[2 * i + 1] + H[2 * i + 1] * u0 + H[n2 + 2 * i + 1] * u1 + H[2 * n2 + 2 * i + 1] * u2;
+        const size_t m = (size_t)b * n_p + i;
+        reinterpret_cast<double2*>(out_mu)[m] = make_double2((double)(cT * mx - sT * my), (double)(sT * mx + cT * my));
     }
 }
 
-// y_mu -= K U at every node; y_U = -K^T mu per body (one block per body).
+// y_mu -= K U at every node; y_U = -K^T mu per body (one block per body).  The
+// arithmetic is in T: the FP32 operator's saddle coupling stays off the FP64 pipe.
+template <typename T>
 __global__ void k_saddle_K(int n_p, const double* __restrict__ ref, const double* __restrict__ rot,
                            const double* __restrict__ mu, const double* __restrict__ U, double* __restrict__ ymu,
                            double* __restrict__ yU) {
     const int b = blockIdx.x;
-    const double c = rot[2 * b], s = rot[2 * b + 1];
-    const double ux = U[3 * b], uy = U[3 * b + 1], om = U[3 * b + 2];
-    double fx = 0, fy = 0, tq = 0;
+    const T c = (T)rot[2 * b], s = (T)rot[2 * b + 1];
+    const T ux = (T)U[3 * b], uy = (T)U[3 * b + 1], om = (T)U[3 * b + 2];
+    T fx = 0, fy = 0, tq = 0;
     for (int j = threadIdx.x; j < n_p; j += blockDim.x) {
         // x - q = R gamma_ref
-        double rx = c * ref[2 * j] - s * ref[2 * j + 1];
-        double ry = s * ref[2 * j] + c * ref[2 * j + 1];
-        size_t m = (size_t)b * n_p + j;
-        ymu[2 * m] -= ux - om * ry;
-        ymu[2 * m + 1] -= uy + om * rx;
-        double mx = mu[2 * m], my = mu[2 * m + 1];
+        const T gx = (T)ref[2 * j], gy = (T)ref[2 * j + 1];
+        const T rx = c * gx - s * gy, ry = s * gx + c * gy;
+        const size_t m = (size_t)b * n_p + j;
+        double2 y = reinterpret_cast<double2*>(ymu)[m];
+        y.x -= (double)(ux - om * ry);
+        y.y -= (double)(uy + om * rx);
+        reinterpret_cast<double2*>(ymu)[m] = y;
+        const double2 mv = reinterpret_cast<const double2*>(mu)[m];
+        const T mx = (T)mv.x, my = (T)mv.y;
         fx += mx;
         fy += my;
         tq += rx * my - ry * mx;
     }
-    __shared__ double red[3][32];
+    __shared__ T red[3][32];
     for (int o = 16; o > 0; o >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
@@ -581,7 +591,7 @@ template <typename T>
 static fbim_status saddle_apply(fbim_handle_s* h, const double* x, double* y) {
     const int N2 = 2 * h->N;
     FBIM_TRY(apply_operator<T>(h, x, y, 3));
-    k_saddle_K<<<h->n_b, 128, 0, h->stream>>>(h->n_p, h->ref, h->rot, x, x + N2, y, y + N2);
+    k_saddle_K<T><<<h->n_b, 128, 0, h->stream>>>(h->n_p, h->ref, h->rot, x, x + N2, y, y + N2);
     h->launches += 1;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;
