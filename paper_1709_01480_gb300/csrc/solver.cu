@@ -193,13 +193,13 @@ __global__ void k_check_finite(int n, const double* __restrict__ x, int* __restr
 // The Arnoldi step on the device.  *kd is the index k of the newest basis vector,
 // the one the step expands, so that one captured graph serves every k.  Row k of
 // the step history holds the step's Gram-Schmidt coefficients (first pass at 0,
-// second at m+1), |w|^2 at 2(m+1) and 1/|w| at 2(m+1)+1; the norm kernel also
+// second at m+1), |w|^2 at 2(m+1) and 1/|w| at 2(m+1)+1; the last sweep also
 // copies the row to mapped host memory, where the host reads it after the step's
 // event.  Classical Gram-Schmidt, fused: dots of w with the K = k+1 basis vectors,
 // then w -= V h with the next pass's dots (or |w|^2) in the same sweep.  Each
 // block owns CG_CHUNK consecutive entries (strided per thread for coalescing) and
-// writes one partial per dot; the reductions sum the partials in a fixed order,
-// so the result does not depend on scheduling.
+// writes one partial per dot; the sweep's last block to finish sums the partials
+// in a fixed order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
 constexpr int CG_TB = 256, CG_EPT = 4, CG_CHUNK = CG_TB * CG_EPT, CG_KCH = 64;
 
@@ -245,11 +245,37 @@ __device__ __forceinline__ void cgs_block_dots(int n, int K, const double* __res
     }
 }
 
+// After every block has written its partials: the last block to arrive (an atomic
+// count, which that block resets) returns true, behind a fence that makes the other
+// blocks' partials visible to it.
+__device__ __forceinline__ bool cgs_last_block(unsigned* __restrict__ count) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(count, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// out[j] = sum_b part[j nb + b] for j < K: a warp per j, its lanes strided over the
+// blocks, then a warp sum (a fixed order)
+__device__ __forceinline__ void cgs_sum_partials(int K, int nb, const double* part, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = warp; j < K; j += nw) {
+        double s = 0.0;
+        for (int b = lane; b < nb; b += 32) s += __ldcg(part + (size_t)j * nb + b);
+        s = warp_sum(s);
+        if (lane == 0) out[j] = s;
+    }
+}
+
 // first pass: partial dots of w with V_0..V_k; also stores the step's preconditioned
 // vector z as Z_k
 __global__ void __launch_bounds__(CG_TB) k_cgs_dots(int n, const int* __restrict__ kd, const double* __restrict__ V,
                                                     int ld, const double* __restrict__ w, const double* __restrict__ z,
-                                                    double* __restrict__ Z, int nb, double* __restrict__ part) {
+                                                    double* __restrict__ Z, int nb, double* __restrict__ part,
+                                                    double* __restrict__ hist, int m, unsigned* __restrict__ count) {
     __shared__ double red[CG_KCH][8];
     const int k = *kd;
     double wv[CG_EPT];
@@ -265,14 +291,21 @@ __global__ void __launch_bounds__(CG_TB) k_cgs_dots(int n, const int* __restrict
         const int i = i0 + e * CG_TB;
         if (i < n) Z[(size_t)k * ld + i] = z[i];
     }
+    if (cgs_last_block(count)) {  // the first pass's coefficients into history row k
+        cgs_sum_partials(k + 1, nb, part, hist + (size_t)k * hist_stride(m));
+        if (threadIdx.x == 0) *count = 0u;
+    }
 }
 
 // w -= sum_{j<=k} V_j h_j with h the history row's pass at offset off, then the partial
-// dots of the new w with V (dots = 1) or |w|^2 (dots = 0)
-__global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, const int* __restrict__ kd, const double* __restrict__ V,
-                                                      int ld, const double* __restrict__ hist, int m, int off,
+// dots of the new w with V (dots = 1) or |w|^2 (dots = 0).  The last block sums them:
+// the second pass's coefficients into the row at m+1, or |w|^2 and 1/|w| (0 when w = 0)
+// at 2(m+1) and 2(m+1)+1, the row to the host mirror and k + 1 into *kd.
+__global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, int* __restrict__ kd, const double* __restrict__ V,
+                                                      int ld, double* __restrict__ hist, int m, int off,
                                                       double* __restrict__ w, int dots, int nb,
-                                                      double* __restrict__ part) {
+                                                      double* __restrict__ part, double* __restrict__ hist_host,
+                                                      unsigned* __restrict__ count) {
     __shared__ double red[CG_KCH][8];
     const int k = *kd, K = k + 1;
     const double* hrow = hist + (size_t)k * hist_stride(m) + off;
@@ -298,40 +331,31 @@ __global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, const int* __restri
         if (i < n) w[i] = wv[e];
     }
     cgs_block_dots(n, dots ? K : 0, V, ld, wv, nb, part, red);
-}
-
-// history row k, entries off + j = sum_b part[j * nb + b] for j <= k, one warp per j (fixed order)
-__global__ void k_cgs_reduce(const int* __restrict__ kd, int m, int nb, const double* __restrict__ part,
-                             double* __restrict__ hist, int off) {
-    const int k = *kd;
-    const int j = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (j > k) return;
-    double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += part[(size_t)j * nb + b];
-    s = warp_sum(s);
-    if (lane == 0) hist[(size_t)k * hist_stride(m) + off + j] = s;
-}
-
-// One warp: |w|^2 and 1/|w| (0 when w = 0) into history row k, the row to the host
-// mirror, then k + 1 into *kd.
-__global__ void k_cgs_norm(int m, int nb, const double* __restrict__ part, int* __restrict__ kd,
-                           double* __restrict__ hist, double* __restrict__ hist_host) {
-    const int k = *kd, lane = threadIdx.x, hs = hist_stride(m);
-    double s = 0.0;
-    for (int b = lane; b < nb; b += 32) s += part[b];
-    s = warp_sum(s);
+    if (!cgs_last_block(count)) return;
+    const int hs = hist_stride(m);
     double* row = hist + (size_t)k * hs;
-    if (lane == 0) {
-        row[2 * (m + 1)] = s;
-        row[2 * (m + 1) + 1] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+    if (dots) {
+        cgs_sum_partials(K, nb, part, row + (m + 1));
+    } else {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            double sq = 0.0;
+            for (int b = lane; b < nb; b += 32) sq += __ldcg(part + b);
+            sq = warp_sum(sq);
+            if (lane == 0) {
+                row[2 * (m + 1)] = sq;
+                row[2 * (m + 1) + 1] = sq > 0.0 ? 1.0 / sqrt(sq) : 0.0;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < hs; i += blockDim.x) hist_host[(size_t)k * hs + i] = row[i];
+        __syncthreads();
+        if (threadIdx.x == 0) *kd = k + 1;
     }
-    __syncwarp();
-    for (int i = lane; i < hs; i += 32) hist_host[(size_t)k * hs + i] = row[i];
-    __syncwarp();
-    if (lane == 0) *kd = k + 1;
+    if (threadIdx.x == 0) *count = 0u;
 }
 
-// V_{k+1} = w / |w| (k + 1 = *kd after the norm kernel), also into the step input y2
+// V_{k+1} = w / |w| (k + 1 = *kd after the last update), also into the step input y2
 __global__ void k_normalize(int n, const int* __restrict__ kd, const double* __restrict__ hist, int m,
                             const double* __restrict__ w, double* __restrict__ V, int ld, double* __restrict__ y2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -535,6 +559,8 @@ fbim_status setup_solver(fbim_handle_s* h) {
     const size_t hist_bytes = sizeof(double) * (m + 1) * hist_stride((int)m);
     FBIM_CUDA_TRY(h, cudaMalloc(&S->kd, sizeof(int)));
     FBIM_CUDA_TRY(h, cudaMemsetAsync(S->kd, 0, sizeof(int), h->stream));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->cg_count, sizeof(unsigned)));
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(S->cg_count, 0, sizeof(unsigned), h->stream));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->hist, hist_bytes));
     FBIM_CUDA_TRY(h, cudaMemsetAsync(S->hist, 0, hist_bytes, h->stream));
     FBIM_CUDA_TRY(h, cudaHostAlloc(&S->hist_host, hist_bytes + sizeof(double) * (m + 1), cudaHostAllocMapped));
@@ -569,7 +595,7 @@ void free_solver(fbim_handle_s* h) {
                     (void*)S->Gd64, (void*)S->G32, (void*)S->Gd32, (void*)S->V, (void*)S->Z, (void*)S->w,
                     (void*)S->r, (void*)S->d, (void*)S->t, (void*)S->hcol, S->zbuf, S->gbuf, (void*)S->lz,
                     (void*)S->lh, (void*)S->rfd, S->blas_ws, (void*)S->corr, (void*)S->gin, (void*)S->gz,
-                    (void*)S->gw, (void*)S->cg_part, (void*)S->kd, (void*)S->hist})
+                    (void*)S->gw, (void*)S->cg_part, (void*)S->kd, (void*)S->hist, (void*)S->cg_count})
         cudaFree(p);
     if (S->hist_host) cudaFreeHost(S->hist_host);
     for (cudaEvent_t ev : S->ev_step)
@@ -649,23 +675,23 @@ template <typename T>
 static fbim_status arnoldi_step(fbim_handle_s* h) {
     Solver* S = h->solver;
     const int n = S->n, m = S->restart, ld = S->ld;
-    const int nb = (n + CG_CHUNK - 1) / CG_CHUNK, rb = ((m + 1) * 32 + 255) / 256;
+    const int nb = (n + CG_CHUNK - 1) / CG_CHUNK;
     const bool two_pass = !std::is_same<T, float>::value;
     FBIM_TRY(precondition<T>(h, S->gin, S->gz));
     FBIM_TRY(saddle_apply<T>(h, S->gz, S->gw));
     const cudaStream_t st = h->stream;
-    k_cgs_dots<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->gw, S->gz, S->Z, nb, S->cg_part);
-    k_cgs_reduce<<<rb, 256, 0, st>>>(S->kd, m, nb, S->cg_part, S->hist, 0);
+    k_cgs_dots<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->gw, S->gz, S->Z, nb, S->cg_part, S->hist, m, S->cg_count);
     if (two_pass) {
-        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, 0, S->gw, 1, nb, S->cg_part);
-        k_cgs_reduce<<<rb, 256, 0, st>>>(S->kd, m, nb, S->cg_part, S->hist, m + 1);
-        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, m + 1, S->gw, 0, nb, S->cg_part);
+        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, 0, S->gw, 1, nb, S->cg_part, S->hist_map,
+                                           S->cg_count);
+        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, m + 1, S->gw, 0, nb, S->cg_part,
+                                           S->hist_map, S->cg_count);
     } else {
-        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, 0, S->gw, 0, nb, S->cg_part);
+        k_cgs_update<<<nb, CG_TB, 0, st>>>(n, S->kd, S->V, ld, S->hist, m, 0, S->gw, 0, nb, S->cg_part, S->hist_map,
+                                           S->cg_count);
     }
-    k_cgs_norm<<<1, 32, 0, st>>>(m, nb, S->cg_part, S->kd, S->hist, S->hist_map);
     k_normalize<<<(n + 255) / 256, 256, 0, st>>>(n, S->kd, S->hist, m, S->gw, S->V, ld, S->gin);
-    h->launches += two_pass ? 7 : 5;
+    h->launches += two_pass ? 4 : 3;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;
 }

@@ -38,6 +38,7 @@ struct Solver {
     // history (one row per step: two passes of coefficients, |w|^2, 1/|w|), its mapped
     // host mirror, and one event per step in flight
     int* kd = nullptr;
+    unsigned* cg_count = nullptr;  // blocks of the running Gram-Schmidt sweep that have finished
     double* hist = nullptr;       // [(m+1)][2 (m+1) + 2]
     double* hist_host = nullptr;  // same, mapped pinned host memory, then [m+1] for y
     double* hist_map = nullptr;   // its device address
