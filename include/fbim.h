@@ -182,6 +182,8 @@ fbim_status fbim_mobility_solve(fbim_handle h, const double* F_dev, const double
  *   Z_w_dev: double [M][M][2][2] standard normals (grid index j_y, j_x, component,
  *            real/imaginary; M = fbim_info.grid), or NULL to draw them from Philox
  *            (seed, stream 1, counter) at index ((j_y M + j_x) 2 + comp) 2 + re/im.
+ *   Drawn normals are those of fbim_philox_normals; an FBIM_FP32 handle takes the
+ *   Box-Muller transform of the same uniforms in FP32 (normals to FP32 rounding).
  *   slip_dev: double [N][2] output.  lanczos_iters: NULL or output.  Synchronises. */
 fbim_status fbim_brownian_slip(fbim_handle h, uint64_t seed, uint64_t counter, double kT, double dt,
                                const double* W_r_dev, const double* Z_w_dev, double tol, int max_iter,

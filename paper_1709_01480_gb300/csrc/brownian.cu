@@ -28,11 +28,18 @@ fbim_status ensure_solver(fbim_handle_s* h);
 
 namespace {
 
-__global__ void k_philox_normals(size_t n, unsigned long long seed, unsigned stream, unsigned counter,
+// f32: the transform in FP32 (the near-field noise of an FP32 handle)
+__global__ void k_philox_normals(size_t n, unsigned long long seed, unsigned stream, unsigned counter, int f32,
                                  double* __restrict__ out) {
     size_t blk = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * blk >= n) return;
-    double2 z = philox_normals(seed, stream, counter, blk);
+    double2 z;
+    if (f32) {
+        const float2 zf = philox_normals_f(seed, stream, counter, blk);
+        z = make_double2(zf.x, zf.y);
+    } else {
+        z = philox_normals(seed, stream, counter, blk);
+    }
     out[2 * blk] = z.x;
     if (2 * blk + 1 < n) out[2 * blk + 1] = z.y;
 }
@@ -256,8 +263,8 @@ fbim_status brownian_slip(fbim_handle_s* h, unsigned long long seed, unsigned lo
     const int n = 2 * h->N;
     double* Wn = S->d;  // [>= n] scratch
     if (!W_r) {
-        k_philox_normals<<<(unsigned)((n / 2 + 256) / 256), 256, 0, h->stream>>>((size_t)n, seed, 0u,
-                                                                                (unsigned)counter, Wn);
+        k_philox_normals<<<(unsigned)((n / 2 + 256) / 256), 256, 0, h->stream>>>(
+            (size_t)n, seed, 0u, (unsigned)counter, h->precision == FBIM_FP32 ? 1 : 0, Wn);
         FBIM_CUDA_TRY(h, cudaGetLastError());
         h->launches += 1;
         W_r = Wn;
@@ -301,7 +308,7 @@ extern "C" fbim_status fbim_philox_normals(fbim_handle h, uint64_t seed, uint32_
     if (!h || !out_dev) return FBIM_ERR_INVALID_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return FBIM_ERR_CUDA;
     if (n == 0) return FBIM_OK;
-    fbim::k_philox_normals<<<(unsigned)(((n + 1) / 2 + 255) / 256), 256, 0, h->stream>>>(n, seed, stream, counter,
+    fbim::k_philox_normals<<<(unsigned)(((n + 1) / 2 + 255) / 256), 256, 0, h->stream>>>(n, seed, stream, counter, 0,
                                                                                     out_dev);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;

@@ -883,6 +883,13 @@ __global__ void k_noise_spec(int M, T twopi_L, T inv4xi2, T one_minus_eta, T pre
         zi[0] = z[1];
         zr[1] = z[2];
         zi[1] = z[3];
+    } else if constexpr (std::is_same<T, float>::value) {
+        const float2 a = philox_normals_f(seed, 1u, counter, base * 2);
+        const float2 b = philox_normals_f(seed, 1u, counter, base * 2 + 1);
+        zr[0] = a.x;
+        zi[0] = a.y;
+        zr[1] = b.x;
+        zi[1] = b.y;
     } else {
         double2 a = philox_normals(seed, 1u, counter, base * 2);
         double2 b = philox_normals(seed, 1u, counter, base * 2 + 1);

@@ -68,6 +68,23 @@ __device__ __forceinline__ double2 philox_normals(unsigned long long seed, unsig
     return make_double2(rad * c2, rad * s);
 }
 
+// The same pair from the same 53-bit uniforms, the logarithm, square root, sine and
+// cosine in FP32: the noise of an FP32 operator (GB300's FP64 transcendentals run on
+// its slow FP64 pipe).  Agrees with philox_normals to FP32 rounding.
+__device__ __forceinline__ float2 philox_normals_f(unsigned long long seed, unsigned stream, unsigned counter,
+                                                  unsigned long long idx) {
+    uint4 c = make_uint4((unsigned)(idx & 0xffffffffull), (unsigned)(idx >> 32), stream, counter);
+    uint2 k = make_uint2((unsigned)(seed & 0xffffffffull), (unsigned)(seed >> 32));
+    uint4 x = philox4x32_10(c, k);
+    const float two_m53 = 1.1102230246251565e-16f;  // 2^-53, exact
+    const float u1 = ((float)(x.x >> 5) * 67108864.0f + ((float)(x.y >> 6) + 0.5f)) * two_m53;
+    const float u2 = ((float)(x.z >> 5) * 67108864.0f + ((float)(x.w >> 6) + 0.5f)) * two_m53;
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float s, c2;
+    sincospif(2.0f * u2, &s, &c2);
+    return make_float2(rad * c2, rad * s);
+}
+
 // Visit the sources s != t within r_c of cell-sorted target t over the 9 cells
 // around t's cell; f(s, rx, ry, r2) gets the separation x_t - x_s.  Offsets are
 // measured from each node's cell corner, so the periodic wrap is the cell shift.
