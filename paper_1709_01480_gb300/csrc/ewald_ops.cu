@@ -311,45 +311,60 @@ __device__ __forceinline__ PairEntry<double> ld_entry(const PairEntry<double>* p
     return e;
 }
 
-// v_s[t] = sum_k pairs[t][k] mu_s[src]: one thread per row, the entries of a row
-// taken U at a time (U independent list loads, then U independent gathers) so
-// that each thread keeps several memory requests in flight; the products are
-// accumulated in the row's k order either way.
+// v_s[t] = sum_k pairs[t][k] mu_s[src]: one block per 32-row slice, SPMV_P warps
+// over each row's entries (warp p takes k = p, p + SPMV_P, ..., so that a warp still
+// reads 32 consecutive entries), each thread taking its entries U at a time (U
+// independent list loads, then U independent gathers) to keep several memory
+// requests in flight; the SPMV_P partial sums are added in warp order.
+constexpr int SPMV_P = 4;
 template <typename T>
-__global__ void __launch_bounds__(256) k_pair_spmv(int N, const int* __restrict__ slice_start,
-                                                  const PairEntry<T>* __restrict__ pairs,
-                                                  const typename V2<T>::type* __restrict__ mu_s,
-                                                  typename V2<T>::type* __restrict__ v_s) {
+__global__ void __launch_bounds__(32 * SPMV_P) k_pair_spmv(int N, const int* __restrict__ slice_start,
+                                                           const PairEntry<T>* __restrict__ pairs,
+                                                           const typename V2<T>::type* __restrict__ mu_s,
+                                                           typename V2<T>::type* __restrict__ v_s) {
     constexpr int U = sizeof(T) == 4 ? 8 : 4;
     using T2 = typename V2<T>::type;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
-    const int sl = t >> 5, lane = t & 31;
-    const int base = slice_start[sl], len = slice_start[sl + 1] - base;
-    const PairEntry<T>* row = pairs + (size_t)base * 32 + lane;
+    __shared__ T2 red[SPMV_P][32];
+    const int sl = blockIdx.x, lane = threadIdx.x & 31, part = threadIdx.x >> 5;
+    const int t = sl * 32 + lane;
     T ax = 0, ay = 0;
-    int k = 0;
-    for (; k + U <= len; k += U) {
-        PairEntry<T> e[U];
-        T2 m[U];
+    if (t < N) {  // the slice's rows past N have no entries
+        const int base = slice_start[sl], len = slice_start[sl + 1] - base;
+        const PairEntry<T>* row = pairs + (size_t)base * 32 + lane;
+        int k = part;
+        for (; k + (U - 1) * SPMV_P < len; k += U * SPMV_P) {
+            PairEntry<T> e[U];
+            T2 m[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) e[u] = ld_entry(row + (size_t)(k + u) * 32);
+            for (int u = 0; u < U; ++u) e[u] = ld_entry(row + (size_t)(k + u * SPMV_P) * 32);
 #pragma unroll
-        for (int u = 0; u < U; ++u) m[u] = __ldg(mu_s + e[u].src);
+            for (int u = 0; u < U; ++u) m[u] = __ldg(mu_s + e[u].src);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            ax = fma(e[u].xx, m[u].x, fma(e[u].xy, m[u].y, ax));
-            ay = fma(e[u].xy, m[u].x, fma(e[u].yy, m[u].y, ay));
+            for (int u = 0; u < U; ++u) {
+                ax = fma(e[u].xx, m[u].x, fma(e[u].xy, m[u].y, ax));
+                ay = fma(e[u].xy, m[u].x, fma(e[u].yy, m[u].y, ay));
+            }
+        }
+        for (; k < len; k += SPMV_P) {
+            const PairEntry<T> e = ld_entry(row + (size_t)k * 32);
+            const T2 m = __ldg(mu_s + e.src);
+            ax = fma(e.xx, m.x, fma(e.xy, m.y, ax));
+            ay = fma(e.xy, m.x, fma(e.yy, m.y, ay));
         }
     }
-    for (; k < len; ++k) {
-        const PairEntry<T> e = ld_entry(row + (size_t)k * 32);
-        const T2 m = __ldg(mu_s + e.src);
-        ax = fma(e.xx, m.x, fma(e.xy, m.y, ax));
-        ay = fma(e.xy, m.x, fma(e.yy, m.y, ay));
+    red[part][lane].x = ax;
+    red[part][lane].y = ay;
+    __syncthreads();
+    if (part == 0 && t < N) {
+        T sx = red[0][lane].x, sy = red[0][lane].y;
+#pragma unroll
+        for (int p = 1; p < SPMV_P; ++p) {
+            sx += red[p][lane].x;
+            sy += red[p][lane].y;
+        }
+        v_s[t].x = sx;
+        v_s[t].y = sy;
     }
-    v_s[t].x = ax;
-    v_s[t].y = ay;
 }
 
 // The FP64 real-space product of an FP32 handle on its float-float list: products
@@ -746,8 +761,8 @@ static void pair_product(cudaStream_t st, int N, EwaldBuffers<T>& e, bool df) {
         k_pair_spmv_df<<<(N + 63) / 64, 64, 0, st>>>(N, e.slice_start, (const PairEntryDF*)e.pairs, e.mu_df,
                                                      (double2*)e.v_s);
     else
-        k_pair_spmv<T><<<(N + 63) / 64, 64, 0, st>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
-                                                     (const T2*)e.mu_s, (T2*)e.v_s);
+        k_pair_spmv<T><<<(N + 31) / 32, 32 * SPMV_P, 0, st>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
+                                                              (const T2*)e.mu_s, (T2*)e.v_s);
 }
 
 template <typename T>
