@@ -74,3 +74,31 @@ def test_invalid_arguments_are_rejected(fb):
         fb.choose_ewald(1.0, 0.6, 1e-8)      # r_c > L/3
     with pytest.raises(fb.FbimError):
         fb.choose_ewald(1.0, 0.2, 2.0)       # tol >= 1
+
+
+def test_ctypes_structs_match_the_header_layout(fb, tmp_path):
+    """Every field of the binding's ctypes structs sits at the offset, and every struct
+    has the size, that a C compiler gives the header's structs."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"fbim_params": fb.Params, "fbim_info": fb.Info, "fbim_batch_info": fb.BatchInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "fbim.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'    printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
