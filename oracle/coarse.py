@@ -23,8 +23,10 @@ two bodies alone (Sec. 3.1, Eq. discreteParticleVelocity, applied to the pair).
 Parity: the pair list and features are plain definitions, checked by brute
 force and by invariance under a common translation and a periodic shift; the
 two-body target is pinned by the symmetry of N_pair and by the decay of C_ab
-with separation (the bodies decouple).  The network's accuracy for C is
-unpinned (only the solve it preconditions is checked).
+with separation (the bodies decouple); ``coarse_velocity`` with the exact pair
+correction reproduces the mobility of the two bodies from an independent dense
+solve.  The network's accuracy for C is unpinned (only the solve it
+preconditions is checked).
 """
 from __future__ import annotations
 

@@ -9,8 +9,10 @@ The first two terms come from one saddle solve with right-hand side
 [slip; F] where slip = sqrt(2kT/dt) M^1/2 W; the drift from two solves with
 force W~ and no slip at the displaced configurations.
 
-Parity: unpinned beyond its parts (it only combines the pinned solves); the
-paper's free-diffusion statistics are out of reach of a unit test.
+Parity: pinned by what Sec. 4.4 fixes about the step: the RFD term's expectation
+over W~ equals dt kT (d/dQ . N) (checked against central differences of this
+package's N), at fixed W~ it tends to dt kT (D_W~ N) W~ as delta -> 0 at second
+order, and the deterministic part is dt N F.
 """
 from __future__ import annotations
 
