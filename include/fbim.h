@@ -145,7 +145,9 @@ fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const double* ref_nod
                        const double* Q_host, double L, double r_c, double xi, double tol,
                        const fbim_params* opt);
 
-/* Move the bodies: Q_dev double [n_b][3] (device).  Rebuilds node positions and cells. */
+/* Move the bodies: Q_dev double [n_b][3] (device).  Rebuilds node positions, cells and
+ * pair lists, and synchronises the stream to report FBIM_ERR_NONFINITE (non-finite
+ * coordinates) or FBIM_ERR_OVERLAP (two nodes coincide). */
 fbim_status fbim_update_config(fbim_handle h, const double* Q_dev);
 
 /* v = M mu with M = M(t) + M(a)_sym + M(w) (Sec. 3.2).  mu_dev, v_dev: double [N][2]. */
@@ -338,12 +340,18 @@ fbim_status fbim_coarse_stats(fbim_handle h, int* n_pairs, int* n_rejected);
  * allocating any device memory (the paper has no counterpart: this is a library
  * service).  It is for callers that must not allocate once running, such as a host
  * that gives all device memory to its own pool at start-up or a time-critical loop.
- * Works in FP64 on the handle's cell list, with its scratch in a fixed device array
- * of the library (4 MiB per device, held until exit); the handle may have at most
- * 131072 nodes, larger handles get FBIM_ERR_INVALID_ARG.  The first call on each
- * device looks up that array's address (make it before any stream capture).  All
- * calls share the array: calls whose work overlaps on the GPU race and must be
- * serialised by the caller.  mu_dev, v_dev: double [N][2], 16-byte aligned. */
+ * Works in FP64 on the handle's cell list (FBIM_FP32 and FBIM_FP64 handles alike:
+ * fbim_setup builds the FP64 cell offsets of every handle), with its scratch in a
+ * fixed device array of the library (4 MiB per device, held until exit); the handle
+ * may have at most 131072 nodes, larger handles get FBIM_ERR_INVALID_ARG.
+ * fbim_setup does this entry point's set-up on the handle's device: it looks up the
+ * array's address and loads the entry point's kernels (under CUDA's lazy module
+ * loading that load would otherwise allocate at the first call), so the call itself
+ * neither loads code nor allocates.  All calls share the array and it keeps the last
+ * call's contents: calls whose work overlaps on the GPU race and must be serialised
+ * by the caller.  Coincident nodes contribute nothing (fbim_setup and
+ * fbim_update_config report them as FBIM_ERR_OVERLAP).
+ * mu_dev, v_dev: double [N][2], 16-byte aligned. */
 fbim_status fbim_apply_real_noalloc(fbim_handle h, const double* mu_dev, double* v_dev);
 
 /* v = M mu with the handle's FP64 operator whatever its precision: the operator of the

@@ -259,7 +259,19 @@ class FBIM:
         return v
 
     def apply_real_noalloc(self, mu, out):
-        """Real-space operator into the caller's ``out``; allocates no device memory."""
+        """Real-space operator into the caller's ``out``; allocates no device memory.
+
+        ``mu`` and ``out`` must be float64, contiguous, shaped (n, 2) and on the
+        handle's device: the library receives bare pointers and cannot check them.
+        """
+        for name, t in (("mu", mu), ("out", out)):
+            if isinstance(t, int):
+                continue
+            import torch
+            if (t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != (self.n, 2)
+                    or t.device.type != "cuda" or t.device.index not in (None, self.device)):
+                raise FbimError(1, f"apply_real_noalloc: {name} must be a contiguous float64 ({self.n}, 2) "
+                                   f"tensor on cuda:{self.device}, got {t.dtype} {tuple(t.shape)} on {t.device}")
         _check(_lib.fbim_apply_real_noalloc(self._h, _ptr(mu), _ptr(out)), self._h)
         return out
 

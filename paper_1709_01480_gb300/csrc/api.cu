@@ -278,6 +278,7 @@ static fbim_status setup_one(fbim_handle* out, int n_b, int n_p, const double* r
         FBIM_TRY(fbim::build_geometry(h));
         if (h->precision == FBIM_FP32) FBIM_TRY(fbim::ensure_ewald<float>(h));
         FBIM_TRY(fbim::ensure_ewald<double>(h));
+        FBIM_TRY(fbim::noalloc_prepare(h));
         return check_flags(h);
     });
     if (st != FBIM_OK) {
@@ -378,7 +379,8 @@ extern "C" fbim_status fbim_update_config(fbim_handle h, const double* Q_dev) {
     if (!h || !Q_dev) return FBIM_ERR_INVALID_ARG;
     return guarded(h, [&]() -> fbim_status {
         FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
-        return fbim::update_positions(h, Q_dev);
+        FBIM_TRY(fbim::update_positions(h, Q_dev));
+        return check_flags(h);
     });
 }
 

@@ -195,7 +195,11 @@ struct fbim_handle_s {
     long long launches = 0;      // kernels this library has launched on the handle (counted at launch sites)
     unsigned long long layout_version = 0;  // bumped when a buffer that launches take by pointer is reallocated
     unsigned long long geom_version = 0;    // bumped by every geometry rebuild
-    struct Coarse* coarse = nullptr;        // learned coarse level (coarse.cu), NULL when off
+    struct Coarse* coarse = nullptr;        // allocation-free real-space entry point (noalloc.cu): run by fbim_setup on the
+// handle's device so that the entry point's first call loads and allocates nothing
+fbim_status noalloc_prepare(fbim_handle_s* h);
+
+// learned coarse level (coarse.cu), NULL when off
 
     int n_cell() const { return n_box * n_box; }
     void fail(const std::string& m) { err = m; }
@@ -241,6 +245,10 @@ fbim_status solver_precondition(fbim_handle_s* h, const double* in, double* out,
 fbim_status solver_saddle(fbim_handle_s* h, const double* x, double* y, bool fp32);
 // point every launch of the handle (kernels, cuFFT plans, cuBLAS) at stream s
 void bind_stream(fbim_handle_s* h, cudaStream_t s);
+
+// allocation-free real-space entry point (noalloc.cu): run by fbim_setup on the
+// handle's device so that the entry point's first call loads and allocates nothing
+fbim_status noalloc_prepare(fbim_handle_s* h);
 
 // learned coarse level (coarse.cu)
 void free_coarse(fbim_handle_s* h);

@@ -181,6 +181,8 @@ size_t scan_storage(int n) { return (size_t)n + 2 + 2 * (size_t)((n + 1023) / 10
 fbim_status build_geometry(fbim_handle_s* h) {
     const int N = h->N, nc = h->n_cell(), nt = h->n_tile * h->n_tile;
     ++h->geom_version;
+    // flags 0 (non-finite coordinates) and 1 (coincident nodes) describe this geometry
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(h->flags, 0, 2 * sizeof(int), h->stream));
     FBIM_CUDA_TRY(h, cudaMemsetAsync(h->cell_fill, 0, sizeof(int) * nc, h->stream));
     FBIM_CUDA_TRY(h, cudaMemsetAsync(h->tile_fill, 0, sizeof(int) * nt, h->stream));
     const int tb = 256;

@@ -15,6 +15,13 @@
 // written by the same call, so nothing needs clearing.  Calls whose work
 // overlaps on the GPU (different streams, or different handles on one device)
 // race on the array and must be serialised by the caller.
+//
+// Under CUDA's lazy module loading a module, and each kernel in it, is loaded
+// (and its device memory allocated) when it is first used.  fbim_setup therefore
+// runs noalloc_prepare on the handle's device: it looks up the array's address and
+// launches each kernel of this file once on an empty range, so that the module,
+// the kernels' code and their local memory are in place before the entry point is
+// first called; the entry point itself then neither loads nor allocates.
 #include <mutex>
 
 #include "ewald_types.cuh"
@@ -38,16 +45,21 @@ __global__ void k_na_gather(int N, const int* __restrict__ perm, const double2* 
     if (s < N) mu_s[s] = mu[perm[s]];
 }
 
+// Coincident nodes (r = 0) contribute nothing and raise flags[1], as in the pair-list
+// build; fbim_setup and fbim_update_config report that flag as FBIM_ERR_OVERLAP.
 __global__ void __launch_bounds__(128) k_na_pairs(int N, int n_box, double r_c, double rc2, double xi2, double pref,
                                                  fbim::ChebE1<double> ce, const int* __restrict__ perm,
                                                  const int* __restrict__ cell, const int* __restrict__ start,
                                                  const double2* __restrict__ off, const double2* __restrict__ mu_s,
-                                                 double2* __restrict__ v_s) {
+                                                 double2* __restrict__ v_s, int* __restrict__ flags) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
     double ax = 0, ay = 0;
     fbim::for_each_pair<double>(t, n_box, r_c, rc2, perm, cell, start, off, [&](int s, double rx, double ry, double r2) {
-        if (r2 == 0.0) return;
+        if (r2 == 0.0) {
+            atomicOr(&flags[1], 1);
+            return;
+        }
         double z = xi2 * r2;
         double a = fbim::kernel_a<double>(ce, z);
         double b = exp(-z) / r2;
@@ -83,7 +95,7 @@ __global__ void k_na_finish(int N, int n_p, int band, const int* __restrict__ sl
 }
 
 // Set-up, once per device, with that device current: look up the device address
-// of the scratch array.  Runs inside the first call on each device.
+// of the scratch array (noalloc_prepare runs it from fbim_setup).
 fbim_status scratch_on_device(fbim_handle h, double2** out) {
     int dev = h->device;
     if (dev < 0 || dev >= FBIM_NOALLOC_MAX_DEVICES) {
@@ -105,6 +117,27 @@ fbim_status scratch_on_device(fbim_handle h, double2** out) {
 }
 
 }  // namespace
+
+namespace fbim {
+
+// Run by fbim_setup with the handle's device current (see the file header): the
+// scratch address, then one launch of each kernel on an empty range (N = 0: every
+// thread returns before touching memory), which loads the kernels and sizes their
+// local memory.
+fbim_status noalloc_prepare(fbim_handle_s* h) {
+    double2* scratch = nullptr;
+    FBIM_TRY(scratch_on_device(h, &scratch));
+    k_na_gather<<<1, 32, 0, h->stream>>>(0, h->perm, scratch, scratch);
+    k_na_pairs<<<1, 32, 0, h->stream>>>(0, h->n_box, h->r_c, h->r_c * h->r_c, h->xi * h->xi, 0.0, h->cheb64,
+                                        h->perm, h->cell, h->cell_start, scratch, scratch, scratch, h->flags);
+    k_na_finish<<<1, 32, 0, h->stream>>>(0, h->n_p, h->band, h->slot, scratch, h->rot, h->band_dev, scratch,
+                                         scratch);
+    h->launches += 3;
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    return FBIM_OK;
+}
+
+}  // namespace fbim
 
 extern "C" fbim_status fbim_apply_real_noalloc(fbim_handle h, const double* mu_dev, double* v_dev) {
     if (!h || !mu_dev || !v_dev) return FBIM_ERR_INVALID_ARG;
@@ -131,9 +164,11 @@ extern "C" fbim_status fbim_apply_real_noalloc(fbim_handle h, const double* mu_d
     k_na_gather<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->perm, (const double2*)mu_dev, mu_s);
     k_na_pairs<<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, h->r_c, h->r_c * h->r_c, h->xi * h->xi,
                                                         1.0 / (4.0 * M_PI * h->eta), h->cheb64, h->perm, h->cell,
-                                                        h->cell_start, (const double2*)h->e64.off, mu_s, v_s);
+                                                        h->cell_start, (const double2*)h->e64.off, mu_s, v_s,
+                                                        h->flags);
     k_na_finish<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, h->slot, v_s, h->rot, h->band_dev,
                                                          (const double2*)mu_dev, (double2*)v_dev);
+    h->launches += 3;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;
 }

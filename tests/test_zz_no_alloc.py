@@ -7,9 +7,19 @@ library; this test calls it twice in a row through the C ABI, with different
 forces each time, and compares each result with the ordinary entry point at the
 FP64 tolerance of the other GPU tests.  The file sorts last so that a run that
 stops at its first failure has run every other test already.
+
+Under CUDA's lazy module loading a kernel's module is loaded, and device memory
+allocated for it, at its first use; fbim_setup therefore loads the entry point's
+kernels ahead of time.  A child process with CUDA_MODULE_LOADING=LAZY checks that
+the device's free memory is the same before and after the entry point's first two
+calls.
 """
 import ctypes
+import json
 import math
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -57,4 +67,63 @@ def test_noalloc_rejects_handles_above_its_limit():
     with pytest.raises(fb.FbimError) as e:
         op.apply_real_noalloc(mu, out)
     assert e.value.status == 1 and "at most 131072" in str(e.value)
+    op.close()
+
+
+_FREE_MEMORY_PROBE = r"""
+import ctypes, json, math, sys
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import torch
+import fbim_synth
+import paper_1709_01480_gb300 as fb
+w = fbim_synth.workload("starfish4_np64_L4")
+xi = math.sqrt(math.log(100.0 / 1e-13)) / (w.L / 6)
+op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=1e-13, r_c=w.L / 6, xi=xi, precision="fp32")
+mu = torch.tensor(np.random.default_rng(3).standard_normal((w.n, 2)), device="cuda")
+out = torch.empty_like(mu)
+ref = op.apply_real(mu).clone()
+torch.cuda.synchronize()
+lib = fb.lib()
+free0 = torch.cuda.mem_get_info()[0]
+codes = [lib.fbim_apply_real_noalloc(op.handle, ctypes.c_void_p(mu.data_ptr()), ctypes.c_void_p(out.data_ptr()))
+         for _ in range(2)]
+torch.cuda.synchronize()
+free1 = torch.cuda.mem_get_info()[0]
+print(json.dumps({"codes": codes, "free_before": free0, "free_after": free1,
+                  "rel_diff_fp32_handle": float((out - ref).abs().max() / ref.abs().max())}))
+op.close()
+"""
+
+
+def test_noalloc_first_calls_allocate_nothing_under_lazy_loading():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, CUDA_MODULE_LOADING="LAZY")
+    r = subprocess.run([sys.executable, "-c", _FREE_MEMORY_PROBE, root], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    print(d)
+    assert d["codes"] == [0, 0]
+    assert d["free_after"] == d["free_before"], d
+    # an FP32 handle's real-space operator is FP32: agreement to its rounding
+    assert d["rel_diff_fp32_handle"] < 1e-5
+
+
+def test_noalloc_wrapper_rejects_tensors_it_cannot_use():
+    import torch
+    import paper_1709_01480_gb300 as fb
+    w = fbim_synth.workload("starfish4_np64_L4")
+    op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=1e-10, r_c=w.L / 6, precision="fp64")
+    good = torch.zeros((w.n, 2), dtype=torch.float64, device="cuda")
+    bad = [torch.zeros((w.n, 2), dtype=torch.float32, device="cuda"),        # wrong dtype
+           torch.zeros((w.n - 1, 2), dtype=torch.float64, device="cuda"),    # wrong shape
+           torch.zeros((2, w.n), dtype=torch.float64, device="cuda").t(),    # not contiguous
+           torch.zeros((w.n, 2), dtype=torch.float64)]                       # host memory
+    for b in bad:
+        for args in ((b, good), (good, b)):
+            with pytest.raises(fb.FbimError) as e:
+                op.apply_real_noalloc(*args)
+            assert e.value.status == 1
+    op.apply_real_noalloc(good, torch.empty_like(good))
     op.close()
