@@ -55,12 +55,42 @@ BATCH_RC = 0.504
 # GMRES iterations per solve of the chosen form on this workload (measured); the
 # CPU baseline prices a solve as this many oracle matvecs plus one residual check
 ITERS_PER_SOLVE_REF = 24
-# DRAM bytes (read + write) per launch of each FP32 operator stage, from the ncu
-# capture summarised in profiles/ewald_matvec_dram_starfish1024.md (cutoff L/91 and
-# grid 1296^2, the split and grid tuners' choice); valid for the kernels and the
-# configuration as they are now.
-MEASURED_DRAM_BYTES = {"pairs": 163.23e6, "spread": 14.77e6, "interp": 14.72e6, "finish": 5.25e6,
-                       "scale": 13.45e6, "gather": 3.17e6}
+# ncu DRAM bytes per launch of the FP32 operator's kernels, as written by the profiling
+# run of this workload: "key value" lines (config, source hash, bytes per kernel)
+DRAM_RECORD = os.path.join(ROOT, "profiles", "dram_bytes_fp32_matvec_starfish1024.txt")
+PAIR_KERNEL_SOURCE = os.path.join(ROOT, "paper_1709_01480_gb300", "csrc", "ewald_ops.cu")
+
+
+def source_sha16(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_dram_bytes(pair_entries, grid, r_c):
+    """Per-launch DRAM bytes of the pair SpMV from the committed ncu record, or (None, why).
+
+    The record counts for the configuration and kernel source it was taken on; when the
+    run's pair list differs in size (another cutoff) the bytes are scaled by the stored
+    entries, the unit the kernel streams; when the kernel source changed they are void.
+    """
+    if not os.path.exists(DRAM_RECORD):
+        return None, "no ncu record"
+    rec = {}
+    with open(DRAM_RECORD) as f:
+        for ln in f:
+            ln = ln.strip()
+            if ln and not ln.startswith("#"):
+                k, v = ln.split(None, 1)
+                rec[k] = v.strip()
+    if rec.get("source_sha16") != source_sha16(PAIR_KERNEL_SOURCE):
+        return None, "kernel source changed since the ncu record"
+    b = float(rec["k_pair_spmv"])
+    n_rec = int(rec["pair_entries"])
+    if n_rec == pair_entries:
+        return b, f"ncu record (grid {rec.get('grid')}, r_c {rec.get('r_c')})"
+    return b * pair_entries / n_rec, (f"ncu record at {n_rec} stored entries scaled to {pair_entries} "
+                                      f"(the list grows in proportion)")
 
 
 def load_peaks():
@@ -407,8 +437,28 @@ def run_gpu(args):
         stage[p] = {k: ms / max(c, 1) for k, (ms, c) in op.stage_times().items()}
         op.set_timing(False)
 
+    # ---- Brownian slip alone (increments per second) -------------------------------
+    slip_it = []
+
+    def slip_call(i):
+        _, it = ops["fp32"].brownian_slip(kT=KT, dt=DT, seed=77 + rank, counter=i, tol=SOLVE_TOL)
+        slip_it.append(it)
+    ops["fp32"].update_config(Q0)
+    slip_call(0)
+    slip_ms = float(np.mean(timed(torch, stream, flush, slip_call, max(3, args.steps // 2))))
+
+    # ---- true FP64 residuals of one more RFD step (outside the timed region) ---------
+    ops["fp32"].set_residual_audit(True)
+    Qa = Q0.clone()
+    ops["fp32"].rfd_step(F, Qa, DT, KT, delta, seed=1234 + rank, step=args.steps + 1, tol=SOLVE_TOL, max_iter=600)
+    rep, mea = ops["fp32"].residual_audit()
+    ops["fp32"].set_residual_audit(False)
+    audit = {"solves": len(mea), "reported": rep, "measured": mea, "max_measured": max(mea) if mea else None,
+             "what": "one RFD step after the timed ones: each solve's reported residual (the refinement's "
+                     "estimate) beside its true |b - A x| / |b| from the FP64 operator"}
+
     M, N = info["grid"], w.n
-    n_pairs = pair_count(positions(w), w.L, info["r_c"])
+    n_pairs = pair_count(positions(w), w.L, info["r_c"])    # unordered pairs within r_c
     n_entries = info["pair_entries"]
     # minimum DRAM bytes per launch of each stage of the FP32 operator (grids: 2 components
     # x 4 B; half spectrum 2 x M (M/2 + 1) complex x 8 B; node vectors 8 B per node)
@@ -419,23 +469,34 @@ def run_gpu(args):
         "fft_fwd": 8 * M * M + spec_b,
         "scale": 2 * spec_b,
         "fft_inv": spec_b + 8 * M * M,
-        "pairs": 16 * n_entries + 8 * N + 8 * N,        # pair list streamed once, mu_s, v_s
+        "pairs": 16 * 2 * n_pairs + 8 * N + 8 * N,      # 16 B per ordered pair within r_c, mu_s, v_s
         "interp": 8 * M * M + 24 * N + 8 * N,
         "finish": N * (4 + 4 + 8 + 8 + 16 + 16) + 16 * N,
     }
     st32 = stage["fp32"]
-    # the roofline kernel: the pair SpMV, the top kernel of the RFD step's launch list
-    # (profiles/launches_rfd_step_starfish1024.md) and the operator's HBM-bound stage; the
-    # longest stage timer (now the spread, bound by its L2 reductions) is reported beside it
+    # the roofline kernel: the pair SpMV, the top kernel of the RFD step's launch list and
+    # the operator's HBM-bound stage; the longest stage timer is reported beside it
     dom = "pairs"
     dom_ms = st32[dom]
     longest = max(algo_bytes, key=lambda k: st32.get(k, 0.0))
     achieved = algo_bytes[dom] / (dom_ms * 1e-3) / 1e9
+    traffic, traffic_src = measured_dram_bytes(n_entries, M, info["r_c"])
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": MEASURED_DRAM_BYTES.get(dom),
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "traffic_source": traffic_src,
                 "peak_kind": peak_kind + " (HBM copy, burst)", "algorithmic_bytes": algo_bytes[dom],
+                "algorithmic_unit": "16 B per ordered pair within r_c (2 x %d) + 16 B per node" % n_pairs,
+                "stored_bytes": 16 * n_entries + 16 * N, "stored_entries": n_entries,
                 "launch_ms": dom_ms, "scope": "pair SpMV of the FP32 Ewald matvec (top kernel of the step)",
                 "longest_stage": {"stage": longest, "launch_ms": st32[longest]}}
+    # the whole FP32 matvec against the same peak: the wave space's 64 M^2 + 40 N bytes
+    # (spread write, both transforms, scale, interpolation read, node data) plus the real
+    # space's algorithmic bytes, over the whole operator application
+    mv_bytes = 64 * M * M + 40 * N + algo_bytes["pairs"]
+    mv_gbs = mv_bytes / (mv["fp32"] * 1e-3) / 1e9
+    roofline_matvec = {"bound": "hbm", "achieved": mv_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                       "frac": mv_gbs / peaks["hbm_gbs"], "algorithmic_bytes": mv_bytes,
+                       "launch_ms": mv["fp32"], "scope": "one FP32 Ewald matvec (all stages, both streams)"}
 
     # ---- end to end through the public API with host buffers -------------------------
     F_h = torch.empty((w.n_b, 3), dtype=torch.float64, pin_memory=True)
@@ -490,6 +551,11 @@ def run_gpu(args):
                        "fp64_node_matvecs_per_s": world * N / (mv["fp64"] * 1e-3)},
             "stage_ms": {"fp32": st32, "fp64": stage["fp64"]},
             "roofline": roofline,
+            "roofline_matvec": roofline_matvec,
+            "brownian_slip": {"value": 1e3 / slip_ms, "unit": "Brownian increments/s", "ms_per_slip": slip_ms,
+                              "lanczos_iters": float(np.mean(slip_it)),
+                              "what": "fbim_brownian_slip: Lanczos near field + Fourier far field, tol 1e-6"},
+            "residual_audit": audit,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": int(launches),

@@ -166,14 +166,34 @@ fbim_status fbim_apply_wave(fbim_handle h, const double* mu_dev, double* v_dev);
  * iterative refinement (FP64 residual b - A x, FP32-operator corrections).
  *   F_dev:    double [n_b][3] forces and torques (device).
  *   slip_dev: double [N][2] random slip, or NULL for none.
- *   tol:      relative residual |b - A x| / |b| to reach (measured with the FP64 operator).
+ *   tol:      relative residual |b - A x| / |b| to reach.
  *   max_iter: cap on GMRES iterations (all refinement steps together).
  *   U_dev:    double [n_b][3] output velocities (device).  mu_dev: NULL or double [N][2].
  *   iters, rel_residual: NULL or outputs.  Synchronises the stream.
+ * The returned residual: an FBIM_FP64 handle measures it with the FP64 operator at exit.
+ * An FBIM_FP32 handle measures it with the FP64 operator after each correction taken
+ * from a residual above max(1e-3, 5e4 tol), and afterwards ESTIMATES it: the residual is
+ * advanced by r - A_32 d and the last correction's inner GMRES estimate (the FP32
+ * operator's error on the small correction d is ~3e-7 |d|), which saves one FP64 operator
+ * application per solve.  fbim_set_residual_audit makes every solve also measure its
+ * final residual with the FP64 operator, for checking that estimate.
  * Returns FBIM_ERR_NOT_CONVERGED (with the partial result written) if the cap is hit. */
 fbim_status fbim_mobility_solve(fbim_handle h, const double* F_dev, const double* slip_dev, double tol,
                                 int max_iter, double* U_dev, double* mu_dev, int* iters,
                                 double* rel_residual);
+
+/* Residual audit (tracing; the paper has no counterpart).  With on = 1 every mobility
+ * solve of the handle -- also the three inside fbim_rfd_step -- ends with one more
+ * FP64 operator application that measures its true relative residual |b - A x| / |b|
+ * of the returned [mu; U], and records it beside the residual the solve reports
+ * (fbim_mobility_solve: measured or estimated).  The solve's iterates and results are
+ * unchanged.  Turning the audit on or off clears the records. */
+fbim_status fbim_set_residual_audit(fbim_handle h, int on);
+
+/* The last min(n, kept) audit records, oldest first, into the host arrays reported[n]
+ * and measured[n]; *count (NULL allowed) = the number written.  The handle keeps the
+ * last 64 records. */
+fbim_status fbim_residual_audit(fbim_handle h, int n, double* reported, double* measured, int* count);
 
 /* Random slip v = M^1/2 W with <v v^T> = (2 kT / dt) M by the positive split (Sec. 3.3,
  * Eq. sqrtM-split): sqrt(2 kT/dt) [G^+ (G M(r) G^T)^1/2 W(r) + (M(w))^1/2 W(w)], the
@@ -243,12 +263,14 @@ fbim_status fbim_batch_create(fbim_batch* out, int n_handles, const fbim_handle*
 /* Solve every system of the batch.
  *   F_dev:    double, the systems' [n_b][3] force blocks stacked in system order (device).
  *   slip_dev: NULL or double, the systems' [N][2] slip blocks stacked the same way.
- *   tol:      relative residual each system must reach, measured with its FP64 operator
+ *   tol:      relative residual each system must reach (its FP64 operator defines the residual)
  *             (FP32 handles refine: FP64 residuals, FP32-operator corrections).
  *   max_iter: cap on each system's GMRES iterations (all refinement steps together).
  *   U_dev:    double output, the systems' [n_b][3] velocity blocks stacked like F_dev.
- *   iters, rel_residual: NULL or host arrays [n_systems] (iterations and the final FP64
- *             relative residual of every system).
+ *   iters, rel_residual: NULL or host arrays [n_systems] (iterations and the final
+ *             relative residual of every system: measured with the FP64 operators for
+ *             FBIM_FP64 handles, estimated after the last small correction for FBIM_FP32
+ *             handles, as in fbim_mobility_solve).
  * Synchronises the stream.  FBIM_ERR_NOT_CONVERGED (results written) when a system
  * misses tol within max_iter. */
 fbim_status fbim_batch_solve(fbim_batch b, const double* F_dev, const double* slip_dev, double tol, int max_iter,

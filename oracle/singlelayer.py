@@ -163,21 +163,26 @@ def apply_real_rows(X: np.ndarray, mu: np.ndarray, rows, L: float, xi: float, et
 
 
 def apply_wave_rows(Xf: np.ndarray, mu: np.ndarray, rows, L: float, xi: float, eta: float = 1.0,
-                    cut: float = ewald.WAVE_CUT) -> np.ndarray:
+                    cut: float = ewald.WAVE_CUT, chunk: int = 8192) -> np.ndarray:
     """M(w) mu at listed rows by the direct non-uniform Fourier sum (sources: nonzero mu only).
 
     The lattice sum over kappa in [-K, K]^2 with k^2/(4 xi^2) <= cut uses the
     separability e^{-i k.x} = e^{-i k_x x} e^{-i k_y y}: the source transform
-    S(kappa) = sum_n mu_n e^{-i k.x_n} is the matrix product Ex^T diag(mu) Ey.
+    S(kappa) = sum_n mu_n e^{-i k.x_n} is the matrix product Ex^T diag(mu) Ey,
+    summed over blocks of ``chunk`` sources so that Ex and Ey stay small.
     """
     kmax = 2.0 * xi * np.sqrt(cut)
     K = int(np.ceil(kmax * L / (2.0 * np.pi)))
     kap = np.arange(-K, K + 1) * (2.0 * np.pi / L)
     src = np.nonzero(np.any(mu != 0.0, axis=1))[0]
-    Ex = np.exp(-1j * np.outer(Xf[src, 0], kap))            # [S, 2K+1]
-    Ey = np.exp(-1j * np.outer(Xf[src, 1], kap))
-    Sx = Ex.T @ (mu[src, 0:1] * Ey)                          # [kx, ky]
-    Sy = Ex.T @ (mu[src, 1:2] * Ey)
+    Sx = np.zeros((kap.size, kap.size), dtype=np.complex128)   # [kx, ky]
+    Sy = np.zeros_like(Sx)
+    for c0 in range(0, src.size, chunk):
+        s = src[c0:c0 + chunk]
+        Ex = np.exp(-1j * np.outer(Xf[s, 0], kap))            # [S, 2K+1]
+        Ey = np.exp(-1j * np.outer(Xf[s, 1], kap))
+        Sx += Ex.T @ (mu[s, 0:1] * Ey)
+        Sy += Ex.T @ (mu[s, 1:2] * Ey)
     kx, ky = np.meshgrid(kap, kap, indexing="ij")
     k2 = kx * kx + ky * ky
     keep = (k2 > 0) & (k2 / (4.0 * xi * xi) <= cut)

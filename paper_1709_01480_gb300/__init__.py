@@ -42,6 +42,7 @@ EXPORTS = [
     "fbim_mlp_set_params", "fbim_mlp_get_params", "fbim_mlp_set_normalization", "fbim_mlp_forward",
     "fbim_mlp_gradient", "fbim_mlp_adam_step", "fbim_mlp_launches", "fbim_coarse_pairs",
     "fbim_coarse_enable", "fbim_coarse_stats", "fbim_apply_stokeslet_fp64",
+    "fbim_set_residual_audit", "fbim_residual_audit",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -148,6 +149,8 @@ _lib.fbim_mlp_launches.restype = ctypes.c_longlong
 _lib.fbim_coarse_pairs.argtypes = [_P, _D, _I, _P, _P, _IP]
 _lib.fbim_coarse_enable.argtypes = [_P, _P, _D]
 _lib.fbim_coarse_stats.argtypes = [_P, _IP, _IP]
+_lib.fbim_set_residual_audit.argtypes = [_P, _I]
+_lib.fbim_residual_audit.argtypes = [_P, _I, _DP, _DP, _IP]
 
 
 def lib():
@@ -351,6 +354,18 @@ class FBIM:
         n, r = ctypes.c_int(0), ctypes.c_int(0)
         _check(_lib.fbim_coarse_stats(self._h, ctypes.byref(n), ctypes.byref(r)), self._h)
         return n.value, r.value
+
+    def set_residual_audit(self, on: bool):
+        """Make every mobility solve also measure its true FP64 residual (clears the records)."""
+        _check(_lib.fbim_set_residual_audit(self._h, 1 if on else 0), self._h)
+
+    def residual_audit(self, n=64):
+        """The last audit records, oldest first: (reported residuals, measured residuals)."""
+        rep = np.zeros(n)
+        mea = np.zeros(n)
+        k = ctypes.c_int(0)
+        _check(_lib.fbim_residual_audit(self._h, int(n), _dptr(rep), _dptr(mea), ctypes.byref(k)), self._h)
+        return rep[:k.value].tolist(), mea[:k.value].tolist()
 
     def update_config(self, Q_dev):
         _check(_lib.fbim_update_config(self._h, _ptr(Q_dev)), self._h)

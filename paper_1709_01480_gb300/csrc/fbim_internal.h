@@ -192,6 +192,12 @@ struct fbim_handle_s {
     void mark_begin();             // record the opening event of a timed operator call
     void collect();                // synchronise and accumulate the recorded intervals
 
+    // residual audit (fbim_set_residual_audit): every mobility solve also measures its true
+    // FP64 residual; the last kAuditKeep (reported, measured) pairs are kept, oldest first
+    static constexpr int kAuditKeep = 64;
+    bool audit = false;
+    std::vector<double> audit_reported, audit_measured;
+
     long long launches = 0;      // kernels this library has launched on the handle (counted at launch sites)
     unsigned long long layout_version = 0;  // bumped when a buffer that launches take by pointer is reallocated
     unsigned long long geom_version = 0;    // bumped by every geometry rebuild

@@ -21,6 +21,7 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -965,6 +966,17 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
         FBIM_TRY(st);
     }
     S->have_x = std::isfinite(rel);
+    if (h->audit) {
+        // measure the true FP64 residual of the returned [mu; U] beside the reported one
+        double rn_true = 0.0, rel_true = 0.0;
+        FBIM_TRY(true_residual(h, S->t, S->d, S->r, bn, rn_true, rel_true));
+        h->audit_reported.push_back(rel);
+        h->audit_measured.push_back(rel_true);
+        if ((int)h->audit_reported.size() > fbim_handle_s::kAuditKeep) {
+            h->audit_reported.erase(h->audit_reported.begin());
+            h->audit_measured.erase(h->audit_measured.begin());
+        }
+    }
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(U, S->d + N2, sizeof(double) * 3 * h->n_b, cudaMemcpyDeviceToDevice,
                                      h->stream));
     if (mu_out)
@@ -980,6 +992,13 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
         h->fail("GMRES reached the iteration cap before the tolerance");
         return FBIM_ERR_NOT_CONVERGED;
     }
+    return FBIM_OK;
+}
+
+fbim_status set_residual_audit(fbim_handle_s* h, int on) {
+    h->audit = on != 0;
+    h->audit_reported.clear();
+    h->audit_measured.clear();
     return FBIM_OK;
 }
 
@@ -1006,6 +1025,23 @@ void bind_stream(fbim_handle_s* h, cudaStream_t s) {
 }
 
 }  // namespace fbim
+
+extern "C" fbim_status fbim_set_residual_audit(fbim_handle h, int on) {
+    if (!h) return FBIM_ERR_INVALID_ARG;
+    return fbim::set_residual_audit(h, on);
+}
+
+extern "C" fbim_status fbim_residual_audit(fbim_handle h, int n, double* reported, double* measured, int* count) {
+    if (!h || n < 0 || (n > 0 && (!reported || !measured))) return FBIM_ERR_INVALID_ARG;
+    const int have = (int)h->audit_reported.size();
+    const int k = std::min(n, have);
+    for (int i = 0; i < k; ++i) {
+        reported[i] = h->audit_reported[have - k + i];
+        measured[i] = h->audit_measured[have - k + i];
+    }
+    if (count) *count = k;
+    return FBIM_OK;
+}
 
 extern "C" fbim_status fbim_mobility_solve(fbim_handle h, const double* F_dev, const double* slip_dev, double tol,
                                            int max_iter, double* U_dev, double* mu_dev, int* iters,

@@ -223,3 +223,31 @@ def test_mixed_precision_errors_vs_oracle(torch, fb, tiny):
     assert e_trans < 2e-5 and e_rot < 2e-5
     assert e_brown < 5e-5
     op.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_residual_audit_measures_what_the_oracle_measures(torch, fb, tiny, precision):
+    """The audit's measured residual of each solve equals the oracle's |b - A x| / |b| for
+    the returned [mu; U] (an FP64 handle reports that same measured value)."""
+    w, M, K = tiny["w"], tiny["M"], tiny["K"]
+    op = _op(fb, tiny, precision)
+    rng = np.random.default_rng(12)
+    F = rng.standard_normal((w.n_b, 3))
+    slip = rng.standard_normal((w.n, 2))
+    op.set_residual_audit(True)
+    U, mu, it, rel = op.mobility_solve(torch.tensor(F, device="cuda"), torch.tensor(slip, device="cuda"),
+                                       tol=1e-6, max_iter=300, want_mu=True)
+    rep, mea = op.residual_audit()
+    A = saddle.saddle_matrix(M, K)
+    x = np.concatenate([mu.cpu().numpy().reshape(-1), U.cpu().numpy().reshape(-1)])
+    b = -np.concatenate([slip.reshape(-1), F.reshape(-1)])
+    oracle_rel = float(np.linalg.norm(b - A @ x) / np.linalg.norm(b))
+    print(f"{precision}: reported {rep}, measured {mea}, oracle {oracle_rel:.3e}")
+    assert len(rep) == 1 and rep[0] == rel
+    assert abs(mea[0] - oracle_rel) <= 1e-3 * oracle_rel + 1e-12
+    assert mea[0] <= 1.1e-6
+    if precision == "fp64":
+        assert abs(rep[0] - mea[0]) <= 1e-9 * mea[0]
+    op.set_residual_audit(False)
+    assert op.residual_audit() == ([], [])
+    op.close()
