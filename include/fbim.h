@@ -173,10 +173,13 @@ fbim_status fbim_apply_wave(fbim_handle h, const double* mu_dev, double* v_dev);
  * The returned residual: an FBIM_FP64 handle measures it with the FP64 operator at exit.
  * An FBIM_FP32 handle measures it with the FP64 operator after each correction taken
  * from a residual above max(1e-3, 5e4 tol), and afterwards ESTIMATES it: the residual is
- * advanced by r - A_32 d and the last correction's inner GMRES estimate (the FP32
- * operator's error on the small correction d is ~3e-7 |d|), which saves one FP64 operator
- * application per solve.  fbim_set_residual_audit makes every solve also measure its
- * final residual with the FP64 operator, for checking that estimate.
+ * advanced by r - A_32 d and the last correction's inner GMRES estimate, which saves one
+ * FP64 operator application per solve.  That estimate misses (A_64 - A_32) d; the solve
+ * bounds it by 3 e32 |d| summed over the estimated corrections (e32 = |(A_32 - A_64) v| /
+ * |v|, measured once per handle on a probe vector) and accepts convergence on the
+ * estimate only when estimate + bound <= tol, measuring the residual otherwise.
+ * fbim_set_residual_audit makes every solve also measure its final residual with the
+ * FP64 operator, for checking the estimate.
  * Returns FBIM_ERR_NOT_CONVERGED (with the partial result written) if the cap is hit. */
 fbim_status fbim_mobility_solve(fbim_handle h, const double* F_dev, const double* slip_dev, double tol,
                                 int max_iter, double* U_dev, double* mu_dev, int* iters,

@@ -185,6 +185,20 @@ __global__ void k_neg_rhs(int n_mu, int n_U, const double* __restrict__ slip, co
         b[i] = -F[i - n_mu];
 }
 
+// A deterministic vector of uniform values in [-1, 1) (a 32-bit integer hash of the
+// index): the probe vector of the FP32 operator's error estimate.
+__global__ void k_probe_vector(int n, double* __restrict__ v) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    unsigned x = (unsigned)i * 2654435761u + 0x9e3779b9u;
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    v[i] = (double)x * (2.0 / 4294967296.0) - 1.0;
+}
+
 __global__ void k_check_finite(int n, const double* __restrict__ x, int* __restrict__ flag) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n && !isfinite(x[i])) atomicOr(flag, 1);
@@ -892,6 +906,23 @@ static fbim_status true_residual(fbim_handle_s* h, const double* b, const double
     return FBIM_OK;
 }
 
+// e32 = |(A_32 - A_64) v| / |v| for the probe vector v (FP32 handles; once per handle).
+static fbim_status measure_e32(fbim_handle_s* h) {
+    Solver* S = h->solver;
+    if (S->e32 >= 0.0) return FBIM_OK;
+    const int n = S->n;
+    k_probe_vector<<<(n + 255) / 256, 256, 0, h->stream>>>(n, S->corr);
+    h->launches += 2;
+    FBIM_TRY(saddle_apply<float>(h, S->corr, S->w));
+    FBIM_TRY(saddle_apply<double>(h, S->corr, S->r));
+    k_axpby<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0, S->r, -1.0, S->w);  // w = A_64 v - A_32 v
+    double en = 0.0, vn = 0.0;
+    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->w, &en));
+    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->corr, &vn));
+    S->e32 = vn > 0.0 ? en / vn : 0.0;
+    return FBIM_OK;
+}
+
 // warm: start from the solution [mu; U] of the previous solve on this handle (kept in
 // the solver's workspace) instead of zero, e.g. for a nearby configuration.
 fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip, double tol, int max_iter,
@@ -922,6 +953,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
         // error on d): one FP64 matvec per solve instead of one per correction.
         double* corr = S->corr;
         fbim_status st = FBIM_OK;
+        FBIM_TRY(measure_e32(h));  // uses corr, w and r as scratch: before r is set
         if (warm) {
             FBIM_TRY(true_residual(h, S->t, S->d, S->r, bn, rn, rel));
         } else {
@@ -932,6 +964,14 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
         // The residual advanced with the FP32 operator errs by ~1e-6 rel_prev |b| (FP32
         // operator error with margin); it stays below 0.05 tol |b| while rel_prev <= 5e4 tol.
         const double recompute_above = std::max(1e-3, 5e4 * tol);
+        // A residual advanced by r - A_32 d differs from the true b - A_64 x by (A_64 - A_32) d,
+        // at most about e32 |d| (the FP32 operator's measured error per unit vector, with a
+        // margin of 3).  That is small relative to |b| unless x, and so d, carries large
+        // components the operator nearly annihilates (the first-kind system's near-null
+        // normal modes).  drift accumulates the bound over the corrections since the last
+        // FP64 residual; an estimate within tol of convergence only counts once estimate +
+        // drift <= tol, else the residual is measured.
+        double drift = 0.0;
         for (int outer = 0; outer < 40 && rel > tol && iters < max_iter; ++outer) {
             // Each correction solves A d = r with the FP32 operator to a relative 1e-4
             // (or tighter when that already meets tol), within one restart cycle: the
@@ -950,9 +990,20 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
             if (rel > recompute_above) {
                 st = true_residual(h, S->t, S->d, S->r, bn, rn, rel);
                 if (st != FBIM_OK) break;
+                drift = 0.0;
             } else {
                 const double rel_prev = rel;
                 rel = est * rel_prev;
+                double dn = 0.0;
+                FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, corr, &dn));
+                drift += 3.0 * S->e32 * dn / (bn > 0 ? bn : 1.0);
+                if (rel <= tol && rel + drift > tol) {
+                    // the estimate cannot vouch for convergence: measure
+                    st = true_residual(h, S->t, S->d, S->r, bn, rn, rel);
+                    if (st != FBIM_OK) break;
+                    drift = 0.0;
+                    continue;
+                }
                 if (rel > tol && iters < max_iter) {
                     // another correction follows: r <- r - A_32 d
                     FBIM_TRY(saddle_apply<float>(h, corr, S->w));

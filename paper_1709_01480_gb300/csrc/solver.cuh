@@ -61,4 +61,7 @@ struct Solver {
     long long op_kernels[2] = {0, 0};
     cudaStream_t cap = nullptr;  // capture origin (the handle's stream may be the legacy default)
     double* rfd = nullptr;      // [2N + 6 * 3 n_b] workspace of the random-finite-difference step
+    // FP32 handles: |(A_32 - A_64) v| / |v| for a random v, measured on the first solve; it
+    // bounds the error of a residual advanced with the FP32 operator (r - A_32 d)
+    double e32 = -1.0;
 };

@@ -155,7 +155,8 @@ def test_full_size_mixed_precision_solve_meets_its_residual(torch, fb, workload)
           f"recomputed {indep:.3e}")
     assert rep[-1] == rel and rel <= 1e-6
     assert abs(mea[-1] - indep) <= 1e-3 * indep
-    assert indep <= 1.1e-6
+    # the solve only accepts an estimated residual whose error bound keeps it below tol
+    assert indep <= 1e-6
     op.close()
 
 
@@ -169,5 +170,5 @@ def test_full_size_rfd_step_solves_meet_their_residual(torch, fb, workload):
     rep, mea = op.residual_audit()
     print(f"RFD step solves: reported {rep}, measured {mea}")
     assert len(mea) == 3
-    assert max(rep) <= 1e-6 and max(mea) <= 1.1e-6
+    assert max(rep) <= 1e-6 and max(mea) <= 1e-6
     op.close()
