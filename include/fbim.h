@@ -79,6 +79,11 @@ typedef struct {
                              e^{-pi P/2} <= max(tol, 1e-7) -- the FP32 operator's own rounding is
                              ~3e-7, and its refinement corrections need ~1e-4.  Grid, xi and tiles
                              stay those of the FP64 operator.                                    */
+    int    tensor_cores;  /* FBIM_FP32 handles: 1 (default) apply the block-diagonal body operators
+                             (the preconditioner's M_ref^+ block with its body solve, the square
+                             root's G_ref and G_ref^+ blocks) as one tcgen05 tensor-core kernel
+                             each, in three-term TF32 (FP32 accuracy), for 2 n_p <= 256; 0 the
+                             library GEMM between rotation and body-solve kernels              */
 } fbim_params;
 
 /* Ewald parameters the library settled on (fbim_get_info). */
@@ -184,6 +189,18 @@ fbim_status fbim_apply_wave(fbim_handle h, const double* mu_dev, double* v_dev);
 fbim_status fbim_mobility_solve(fbim_handle h, const double* F_dev, const double* slip_dev, double tol,
                                 int max_iter, double* U_dev, double* mu_dev, int* iters,
                                 double* rel_residual);
+
+/* One application of the block-diagonal preconditioner of Sec. 3.4 (Eqs.
+ * preconditionerGMRES, approximate-body-mobility, M-block-inverse), the one
+ * fbim_mobility_solve applies at every GMRES step: per body b, the system
+ * [[M~_bb, -K_b], [-K_b^T, 0]] [mu_b; U_b] = [r_mu,b; r_U,b] with M~_bb^+ = R_b M_ref^+ R_b^T
+ * (M_ref: the reference body alone in the box), through N~_b = (K_b^T M~_bb^+ K_b)^-1.
+ *   in_dev:  double [2N + 3 n_b] = [r_mu (N x 2, body-major); r_U (n_b x 3)] (device).
+ *   out_dev: double [2N + 3 n_b] = [mu; U] (device).  Both 16-byte aligned.
+ * The handle's precision and kernels, as in the solve (FBIM_FP32 handles: FP32 block
+ * operator, on the tensor cores unless fbim_params.tensor_cores = 0; the learned coarse
+ * level when it is on).  For a user's own Krylov solver or for tests.  Synchronises. */
+fbim_status fbim_precondition(fbim_handle h, const double* in_dev, double* out_dev);
 
 /* Residual audit (tracing; the paper has no counterpart).  With on = 1 every mobility
  * solve of the handle -- also the three inside fbim_rfd_step -- ends with one more

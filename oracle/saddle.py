@@ -11,10 +11,19 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 * ``n_half``     N^1/2 = N K^T M^+ M^1/2                                   (Sec. 3.1, Eq. discreteParticleVelocity)
 * ``gmres``      plain restarted GMRES (Arnoldi with modified Gram-Schmidt, Givens
                  rotations), unpreconditioned, for the iteration-count comparison
+* ``block_preconditioner``  one application of the block-diagonal preconditioner P
+                 (Sec. 3.4, Eqs. preconditionerGMRES, approximate-body-mobility,
+                 M-block-inverse): per body, [[M~_bb, -K_b], [-K_b^T, 0]] [mu; U] = [r_mu; r_U]
+                 with M~_bb^+ = R_b M_ref^+ R_b^T, solved through the Schur complement
+                 N~_b = (K_b^T M~_bb^+ K_b)^-1 with K_b from the body's actual nodes
 
 Parity: pinned by the symmetry and positive-definiteness of N (Sec. 2, the
 mobility is SPD), by the exact identity N^1/2 (N^1/2)^T = N (Sec. 3.1,
 Eq. discreteFDB) and by the disk-array drag (Sec. 4.2, Eq. DiluteTheory).
+``block_preconditioner`` is pinned by the case where it is the exact inverse: one
+body at theta = 0 alone in the box (then M~ = M and P^-1 = A^-1 exactly), and by
+the same body turned by a quarter turn (the square lattice is invariant under it,
+so Eq. M-block-inverse is exact and P^-1 = A^-1 again).
 """
 from __future__ import annotations
 
@@ -137,3 +146,32 @@ def gmres(apply_A, b: np.ndarray, tol: float = 1e-10, restart: int = 200, max_it
                 break
         y = sla.solve_triangular(H[:k_used, :k_used], g[:k_used])
         x = x + y @ Z[:k_used]
+
+
+def block_preconditioner(r_mu: np.ndarray, r_U: np.ndarray, Q: np.ndarray, ref_nodes: np.ndarray, L: float,
+                         xi: float, eta: float = 1.0, order: int = 4):
+    """P^-1 [r_mu; r_U] for bodies Q [N_b, 3]: returns (mu [N, 2], U [N_b, 3]).
+
+    M_ref is the single-layer matrix of the reference body alone in the box (theta = 0),
+    M_ref^+ its pseudo-inverse (|lambda| <= 1e-12 max |lambda| dropped), rotated to each
+    body as R_b M_ref^+ R_b^T (Eq. M-block-inverse).  Per body b the 2 x 2 block system
+    gives U_b = -N~_b (r_U,b + K_b^T M~_b^+ r_mu,b) and mu_b = M~_b^+ (r_mu,b + K_b U_b).
+    """
+    from . import singlelayer
+    n_b, n_p = Q.shape[0], ref_nodes.shape[0]
+    Xr = singlelayer.node_positions(np.array([[0.5 * L, 0.5 * L, 0.0]]), ref_nodes)
+    Mp_ref = pinv_sym(singlelayer.single_layer(Xr, L, xi, eta, order))
+    X = singlelayer.node_positions(Q, ref_nodes)
+    r_mu = np.asarray(r_mu, dtype=np.float64).reshape(n_b, 2 * n_p)
+    r_U = np.asarray(r_U, dtype=np.float64).reshape(n_b, 3)
+    mu = np.zeros((n_b, 2 * n_p))
+    U = np.zeros((n_b, 3))
+    for b in range(n_b):
+        c, s = np.cos(Q[b, 2]), np.sin(Q[b, 2])
+        R = np.kron(np.eye(n_p), np.array([[c, -s], [s, c]]))
+        Mp = R @ Mp_ref @ R.T
+        Kb = k_matrix(X[b:b + 1], Q[b:b + 1])
+        Nt = np.linalg.inv(Kb.T @ Mp @ Kb)
+        U[b] = -Nt @ (r_U[b] + Kb.T @ Mp @ r_mu[b])
+        mu[b] = Mp @ (r_mu[b] + Kb @ U[b])
+    return mu.reshape(-1, 2), U

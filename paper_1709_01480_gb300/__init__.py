@@ -42,7 +42,7 @@ EXPORTS = [
     "fbim_mlp_set_params", "fbim_mlp_get_params", "fbim_mlp_set_normalization", "fbim_mlp_forward",
     "fbim_mlp_gradient", "fbim_mlp_adam_step", "fbim_mlp_launches", "fbim_coarse_pairs",
     "fbim_coarse_enable", "fbim_coarse_stats", "fbim_apply_stokeslet_fp64",
-    "fbim_set_residual_audit", "fbim_residual_audit",
+    "fbim_set_residual_audit", "fbim_residual_audit", "fbim_precondition",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -57,7 +57,8 @@ class Params(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("alpert_order", ctypes.c_int), ("grid", ctypes.c_int),
                 ("support", ctypes.c_int), ("eta", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("restart", ctypes.c_int), ("autotune", ctypes.c_int),
-                ("grid_tune", ctypes.c_int), ("split_tune", ctypes.c_int), ("fp32_support", ctypes.c_int)]
+                ("grid_tune", ctypes.c_int), ("split_tune", ctypes.c_int), ("fp32_support", ctypes.c_int),
+                ("tensor_cores", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -150,6 +151,7 @@ _lib.fbim_coarse_pairs.argtypes = [_P, _D, _I, _P, _P, _IP]
 _lib.fbim_coarse_enable.argtypes = [_P, _P, _D]
 _lib.fbim_coarse_stats.argtypes = [_P, _IP, _IP]
 _lib.fbim_set_residual_audit.argtypes = [_P, _I]
+_lib.fbim_precondition.argtypes = [_P, _P, _P]
 _lib.fbim_residual_audit.argtypes = [_P, _I, _DP, _DP, _IP]
 
 
@@ -198,7 +200,7 @@ class FBIM:
 
     def __init__(self, ref_nodes, Q, L, *, tol=1e-8, r_c=0.0, xi=0.0, precision="fp64", order=4,
                  grid=0, support=0, eta=1.0, stream=None, device=0, restart=60, wave="auto", grid_tune=True,
-                 split_tune=False, fp32_support=0):
+                 split_tune=False, fp32_support=0, tensor_cores=True):
         ref = np.ascontiguousarray(ref_nodes, dtype=np.float64)
         Qh = np.ascontiguousarray(Q, dtype=np.float64)
         self.n_p = ref.shape[0]
@@ -216,6 +218,7 @@ class FBIM:
         p.grid_tune = 1 if grid_tune else 0
         p.split_tune = 1 if split_tune else 0
         p.fp32_support = fp32_support
+        p.tensor_cores = 1 if tensor_cores else 0
         if stream is None:
             import torch
             stream = torch.cuda.current_stream(device).cuda_stream
@@ -354,6 +357,12 @@ class FBIM:
         n, r = ctypes.c_int(0), ctypes.c_int(0)
         _check(_lib.fbim_coarse_stats(self._h, ctypes.byref(n), ctypes.byref(r)), self._h)
         return n.value, r.value
+
+    def precondition(self, r, out=None):
+        """One application of the block-diagonal preconditioner to r = [r_mu; r_U] (2N + 3 n_b)."""
+        o = out if out is not None else self._out(r, (2 * self.n + 3 * self.n_b,))
+        _check(_lib.fbim_precondition(self._h, _ptr(r), _ptr(o)), self._h)
+        return o
 
     def set_residual_audit(self, on: bool):
         """Make every mobility solve also measure its true FP64 residual (clears the records)."""

@@ -86,6 +86,7 @@ extern "C" fbim_status fbim_default_params(fbim_params* p) {
     p->grid_tune = 1;
     p->split_tune = 0;
     p->fp32_support = 0;
+    p->tensor_cores = 1;
     return FBIM_OK;
 }
 
@@ -122,6 +123,7 @@ static fbim_status setup_one(fbim_handle* out, int n_b, int n_p, const double* r
         h->device = p.device;
         h->restart = p.restart > 0 ? p.restart : 60;
         h->autotune = p.autotune;
+        h->tensor_cores = p.tensor_cores;
         h->stream = (cudaStream_t)p.stream;
         FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
         FBIM_CUDA_TRY(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));

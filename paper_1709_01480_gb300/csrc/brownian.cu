@@ -88,6 +88,10 @@ template <typename T>
 fbim_status block_apply(fbim_handle_s* h, const T* Bref, const double* in, double* out) {
     Solver* S = h->solver;
     const int N = h->N;
+    if (std::is_same<T, float>::value && S->tc_G.ready) {  // the FP32 blocks on the tensor cores
+        const TcBlock& tb = (const float*)Bref == S->G32 ? S->tc_G : S->tc_Gd;
+        return tc_apply(h, tb, 0, in, out, nullptr, nullptr, nullptr, nullptr, S->tc_err);
+    }
     T* z = (T*)S->zbuf;
     T* g = (T*)S->gbuf;
     k_rot_in2<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, h->n_p, h->rot, in, z);
@@ -283,6 +287,7 @@ fbim_status brownian_slip(fbim_handle_s* h, unsigned long long seed, unsigned lo
     k_combine<<<(n + 255) / 256, 256, 0, h->stream>>>(n, sc, near, sc, far, slip);
     h->launches += 1;
     FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    FBIM_TRY(tc_check(h));
     if (lanczos_iters) *lanczos_iters = it;
     return FBIM_OK;
 }

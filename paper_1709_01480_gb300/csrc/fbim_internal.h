@@ -164,6 +164,7 @@ struct fbim_handle_s {
     int* tile_tmp = nullptr;     // [N] tile id of each node (scratch of the sort)
     int TS = 0, n_tile = 0;      // tile side (divides M) and tiles per side
     int autotune = 1;            // time the wave-space kernel variants at setup
+    int tensor_cores = 1;        // FP32 block operators (preconditioner, Lanczos G) on tcgen05
     int M_min = 0;               // the grid rule's smallest side
     double grid_tune_ms = 0;     // cost of the tuned FFT pair (0: not tuned)
     int split_candidates = 0;    // cutoffs timed by the split tuner (0: not tuned)

@@ -56,24 +56,29 @@ __global__ void k_rot_in(int N, int n_p, const double* __restrict__ rot, const d
     }
 }
 
-// One block per body: U' = -N~ (R^T r_U + K_ref^T g), mu = R (g + H U').
+// One block per body: U' = -N~ (R^T r_U + K_ref^T g), mu = R (g + H U'), with K_ref^T g
+// formed as H^T z (z = R^T r_mu, g = M_ref^+ z; M_ref^+ symmetric): g carries large
+// components along the near-null normal modes that K_ref^T cancels, z and H do not.
 template <typename T>
 __global__ void k_body_solve(int n_p, const double* __restrict__ ref, const double* __restrict__ rot,
-                             const T* __restrict__ g, const T* __restrict__ H, const double* __restrict__ rU,
-                             double nt0, double nt1, double nt2, double nt3, double nt4, double nt5, double nt6,
-                             double nt7, double nt8, double* __restrict__ out_mu, double* __restrict__ out_U) {
+                             const T* __restrict__ z, const T* __restrict__ g, const T* __restrict__ H,
+                             const double* __restrict__ rU, double nt0, double nt1, double nt2, double nt3,
+                             double nt4, double nt5, double nt6, double nt7, double nt8, double* __restrict__ out_mu,
+                             double* __restrict__ out_U) {
     const int b = blockIdx.x;
     const int n2 = 2 * n_p;
     const T* gb = g + (size_t)b * n2;
+    const T* zb = z + (size_t)b * n2;
     // sums over the body's nodes in T (an FP32 preconditioner stays off the FP64 pipe),
     // the 3x3 solve in FP64
     T sx = 0, sy = 0, st = 0;
-    for (int j = threadIdx.x; j < n_p; j += blockDim.x) {
-        const T gx = gb[2 * j], gy = gb[2 * j + 1];
-        sx += gx;
-        sy += gy;
-        st += (T)ref[2 * j] * gy - (T)ref[2 * j + 1] * gx;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const T zi = zb[i];
+        sx += H[i] * zi;
+        sy += H[n2 + i] * zi;
+        st += H[2 * n2 + i] * zi;
     }
+    (void)ref;
     __shared__ T red[3][32];
     __shared__ double Up[3];
     for (int o = 16; o > 0; o >>= 1) {
@@ -545,6 +550,11 @@ fbim_status setup_solver(fbim_handle_s* h) {
     N[6] = (KH[3] * KH[7] - KH[4] * KH[6]) / det;
     N[7] = (KH[1] * KH[6] - KH[0] * KH[7]) / det;
     N[8] = (KH[0] * KH[4] - KH[1] * KH[3]) / det;
+    if (h->tensor_cores && h->precision == FBIM_FP32) {
+        FBIM_CUDA_TRY(h, cudaMalloc(&S->tc_err, sizeof(int)));
+        FBIM_CUDA_TRY(h, cudaMemsetAsync(S->tc_err, 0, sizeof(int), h->stream));
+        FBIM_TRY(tc_prepare(h, Mp, n2, S->tc_Mp));
+    }
     FBIM_TRY(upload(h, &S->Mpinv64, Mp));
     FBIM_TRY(upload(h, &S->Mpinv32, Mp));
     FBIM_TRY(upload(h, &S->H64, Hm));
@@ -554,6 +564,10 @@ fbim_status setup_solver(fbim_handle_s* h) {
     FBIM_TRY(eig_sym(h, Mr, n2, lr, Vr));
     std::vector<double> G = matrix_function(lr, Vr, n2, 1e-12, [](double l) { return 1.0 / std::sqrt(l); }, false);
     std::vector<double> Gd = matrix_function(lr, Vr, n2, 1e-12, [](double l) { return std::sqrt(l); }, false);
+    if (S->tc_err) {
+        FBIM_TRY(tc_prepare(h, G, n2, S->tc_G));
+        FBIM_TRY(tc_prepare(h, Gd, n2, S->tc_Gd));
+    }
     FBIM_TRY(upload(h, &S->G64, G));
     FBIM_TRY(upload(h, &S->Gd64, Gd));
     FBIM_TRY(upload(h, &S->G32, G));
@@ -613,6 +627,10 @@ void free_solver(fbim_handle_s* h) {
                     (void*)S->gw, (void*)S->cg_part, (void*)S->kd, (void*)S->hist, (void*)S->cg_count})
         cudaFree(p);
     if (S->hist_host) cudaFreeHost(S->hist_host);
+    tc_free(S->tc_Mp);
+    tc_free(S->tc_G);
+    tc_free(S->tc_Gd);
+    cudaFree(S->tc_err);
     for (cudaEvent_t ev : S->ev_step)
         if (ev) cudaEventDestroy(ev);
     for (cudaGraphExec_t g : S->op_graph)
@@ -660,6 +678,16 @@ static fbim_status precondition(fbim_handle_s* h, const double* in, double* out)
     const int N = h->N, N2 = 2 * N;
     T* z = (T*)S->zbuf;
     T* g = (T*)S->gbuf;
+    if (std::is_same<T, float>::value && S->tc_Mp.ready) {
+        // rotation, M_ref^+ contraction and body solve in one tensor-core kernel
+        fbim_status cst = FBIM_OK;
+        if (coarse_active(h, &cst)) {
+            FBIM_TRY(tc_apply(h, S->tc_Mp, 1, in, nullptr, nullptr, (float*)g, nullptr, nullptr, S->tc_err));
+            return coarse_body_solve<T>(h, g, (const T*)S->H32, in + N2, out, out + N2);
+        }
+        FBIM_TRY(cst);
+        return tc_apply(h, S->tc_Mp, 2, in, out, out + N2, nullptr, S->H32, S->Nt, S->tc_err);
+    }
     k_rot_in<T><<<(N + 255) / 256, 256, 0, h->stream>>>(N, h->n_p, h->rot, in, z);
     const T* Mp = std::is_same<T, float>::value ? (const T*)S->Mpinv32 : (const T*)S->Mpinv64;
     const T* Hm = std::is_same<T, float>::value ? (const T*)S->H32 : (const T*)S->H64;
@@ -673,8 +701,8 @@ static fbim_status precondition(fbim_handle_s* h, const double* in, double* out)
     }
     FBIM_TRY(cst);
     const double* Nt = S->Nt;
-    k_body_solve<T><<<h->n_b, 128, 0, h->stream>>>(h->n_p, h->ref, h->rot, g, Hm, in + N2, Nt[0], Nt[1], Nt[2],
-                                                   Nt[3], Nt[4], Nt[5], Nt[6], Nt[7], Nt[8], out, out + N2);
+    k_body_solve<T><<<h->n_b, 128, 0, h->stream>>>(h->n_p, h->ref, h->rot, z, g, Hm, in + N2, Nt[0], Nt[1],
+                                                   Nt[2], Nt[3], Nt[4], Nt[5], Nt[6], Nt[7], Nt[8], out, out + N2);
     h->launches += 2;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;
@@ -1033,6 +1061,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
     if (mu_out)
         FBIM_CUDA_TRY(h, cudaMemcpyAsync(mu_out, S->d, sizeof(double) * N2, cudaMemcpyDeviceToDevice, h->stream));
     FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    FBIM_TRY(tc_check(h));
     if (iters_out) *iters_out = iters;
     if (res_out) *res_out = rel;
     if (!std::isfinite(rel)) {
@@ -1076,6 +1105,24 @@ void bind_stream(fbim_handle_s* h, cudaStream_t s) {
 }
 
 }  // namespace fbim
+
+extern "C" fbim_status fbim_precondition(fbim_handle h, const double* in_dev, double* out_dev) {
+    if (!h || !in_dev || !out_dev) return FBIM_ERR_INVALID_ARG;
+    if ((((uintptr_t)in_dev) | ((uintptr_t)out_dev)) & 15) {
+        h->fail("fbim_precondition: in and out must be 16-byte aligned");
+        return FBIM_ERR_INVALID_ARG;
+    }
+    try {
+        if (cudaSetDevice(h->device) != cudaSuccess) return FBIM_ERR_CUDA;
+        FBIM_TRY(fbim::ensure_solver(h));
+        FBIM_TRY(fbim::solver_precondition(h, in_dev, out_dev, h->precision == FBIM_FP32));
+        FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        return fbim::tc_check(h);
+    } catch (...) {
+        h->fail("unexpected host exception in fbim_precondition");
+        return FBIM_ERR_SETUP;
+    }
+}
 
 extern "C" fbim_status fbim_set_residual_audit(fbim_handle h, int on) {
     if (!h) return FBIM_ERR_INVALID_ARG;

@@ -3,6 +3,7 @@
 #include <cublas_v2.h>
 
 #include <cmath>
+#include <vector>
 
 // Euclidean norm through a dot product (one reduction kernel; the library's nrm2
 // routine uses a slower overflow-safe scaling that these vectors do not need).
@@ -12,6 +13,14 @@ inline cublasStatus_t fbim_norm2(cublasHandle_t b, int n, const double* x, doubl
     *out = std::sqrt(d);
     return st;
 }
+
+// A reference block B_ref laid out for the tensor-core block operator (block_tc.cu):
+// TF32 high and low parts in chunks of 32 K-columns and M-tiles of 128 rows.
+struct TcBlock {
+    float* A = nullptr;
+    int n2 = 0, KP = 0, MT = 0, KC = 0;
+    bool ready = false;  // false: 2 n_p > 256, the library GEMM serves this block
+};
 
 struct Solver {
     int n2 = 0;                 // 2 n_p
@@ -64,4 +73,19 @@ struct Solver {
     // FP32 handles: |(A_32 - A_64) v| / |v| for a random v, measured on the first solve; it
     // bounds the error of a residual advanced with the FP32 operator (r - A_32 d)
     double e32 = -1.0;
+    // tensor-core block operators of FBIM_FP32 handles: M_ref^+ (preconditioner), G_ref and
+    // G_ref^+ (near-field square root); tc_err = device flag of a timed-out wait
+    TcBlock tc_Mp, tc_G, tc_Gd;
+    int* tc_err = nullptr;
 };
+
+namespace fbim {
+fbim_status tc_prepare(fbim_handle_s* h, const std::vector<double>& Bref, int n2, TcBlock& out);
+void tc_free(TcBlock& b);
+// mode 0: out_b = R_b B_ref R_b^T in_b; 1: out_g = B_ref R_b^T in_b (FP32, body frame);
+// 2: the preconditioner's body solve (out = mu, out_U = U) with H and N~ (row-major)
+fbim_status tc_apply(fbim_handle_s* h, const TcBlock& B, int mode, const double* in, double* out, double* out_U,
+                     float* out_g, const float* H, const double* Nt, int* err);
+// FBIM_ERR_TIMEOUT when a tensor-core block kernel gave up a wait (host-synchronising)
+fbim_status tc_check(fbim_handle_s* h);
+}  // namespace fbim

@@ -120,3 +120,41 @@ def test_gmres_agrees_with_direct_solve(tiny_system):
     x, it, res = saddle.gmres(lambda v: A @ v, b, tol=1e-11, restart=600, max_iter=600)
     assert res <= 1e-11
     assert np.linalg.norm(x[M.shape[0]:] - U) <= 1e-8 * np.linalg.norm(U)
+
+
+def test_block_preconditioner_is_the_exact_inverse_for_one_unrotated_body():
+    # Sec. 3.4: P neglects only inter-body interactions; one body at theta = 0 alone in
+    # the box has M~ = M, so applying P^-1 to A x returns x
+    ref = fbim_synth.starfish_ref_nodes(32)
+    L = 3.0
+    xi = math.sqrt(math.log(100.0 / 1e-12)) / (L / 4)
+    Q = np.array([[1.1, 1.7, 0.0]])
+    X = singlelayer.node_positions(Q, ref)
+    M = singlelayer.single_layer(X, L, xi)
+    K = saddle.k_matrix(X, Q)
+    A = saddle.saddle_matrix(M, K)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(A.shape[0])
+    r = A @ x
+    mu, U = saddle.block_preconditioner(r[:64], r[64:], Q, ref, L, xi)
+    got = A @ np.concatenate([mu.reshape(-1), U.reshape(-1)])
+    assert np.max(np.abs(got - r)) < 1e-9 * np.max(np.abs(r))
+    assert np.max(np.abs(U.reshape(-1) - x[64:])) < 1e-8 * np.max(np.abs(x[64:]))
+
+
+def test_block_preconditioner_rotates_the_reference_block_exactly_by_a_quarter_turn():
+    # the square periodic lattice is invariant under a quarter turn, so for one body at
+    # theta = pi/2 the rotated reference block of Eq. M-block-inverse is its exact block
+    # and P^-1 is again the exact inverse; a wrong rotation (R^T for R, or none) breaks it
+    ref = fbim_synth.starfish_ref_nodes(32)
+    L = 3.0
+    xi = math.sqrt(math.log(100.0 / 1e-12)) / (L / 4)
+    Q = np.array([[1.1, 1.7, 0.5 * math.pi]])
+    X = singlelayer.node_positions(Q, ref)
+    A = saddle.saddle_matrix(singlelayer.single_layer(X, L, xi), saddle.k_matrix(X, Q))
+    x = np.random.default_rng(7).standard_normal(A.shape[0])
+    r = A @ x
+    mu, U = saddle.block_preconditioner(r[:64], r[64:], Q, ref, L, xi)
+    got = A @ np.concatenate([mu.reshape(-1), U.reshape(-1)])
+    assert np.max(np.abs(got - r)) < 1e-9 * np.max(np.abs(r))
+    assert np.max(np.abs(U.reshape(-1) - x[64:])) < 1e-8 * np.max(np.abs(x[64:]))
