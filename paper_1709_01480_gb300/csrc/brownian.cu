@@ -4,12 +4,14 @@
 // preconditioned-real-part, Gprecond-decomp, Gprecond-precompute).
 //
 // Near field: Lanczos iteration for f(A) w, f = sqrt, A = G M(r) G^T (the real-
-// space operator in the handle's precision, G as one GEMM over all bodies), with
-// full FP64 reorthogonalisation; after k steps y_k = |w| V_k f(T_k) e_1 and the
-// iteration stops when |y_k - y_{k-1}| <= tol |y_k|, which needs only the small
-// coefficient vectors because V_k is orthonormal.  Ritz values below zero (from
-// the small negative eigenvalues the symmetrised Alpert block can leave) are
-// clipped to zero.
+// space operator in the handle's precision, G as one block operator over all bodies:
+// on the tensor cores for FP32 handles), with full FP64 reorthogonalisation by the
+// solver's fused classical Gram-Schmidt sweeps; each step runs on the device and the
+// next is queued before the host reads the last one's alpha and beta.  After k steps
+// y_k = |w| V_k f(T_k) e_1 and the iteration stops when |y_k - y_{k-1}| <= tol |y_k|,
+// which needs only the small coefficient vectors because V_k is orthonormal.  Ritz
+// values below zero (from the small negative eigenvalues the symmetrised Alpert block
+// can leave) are clipped to zero.
 // Far field: the wave-space noise pipeline (ewald_ops.cu).
 #include <cublas_v2.h>
 
@@ -73,15 +75,6 @@ __global__ void k_combine(int n, double a, const double* __restrict__ x, double 
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a * x[i] + b * y[i];
 }
-
-#define FBIM_CUBLAS_TRY2(h, expr)                                                       \
-    do {                                                                                \
-        cublasStatus_t s__ = (expr);                                                    \
-        if (s__ != CUBLAS_STATUS_SUCCESS) {                                             \
-            (h)->fail(std::string(#expr) + ": cublas error " + std::to_string((int)s__)); \
-            return FBIM_ERR_CUDA;                                                       \
-        }                                                                               \
-    } while (0)
 
 // out_b = R_b B_ref R_b^T in_b for every body (B_ref = G_ref or G_ref^+), precision T.
 template <typename T>
@@ -180,80 +173,86 @@ template <typename T>
 fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_iter, double* y, int& iters) {
     Solver* S = h->solver;
     const int n = 2 * h->N;
-    if (S->lanczos_max < max_iter + 1) {
+    // basis rows V_0 .. V_{max_iter + 1} (a step queued past the last one writes one more)
+    if (S->lanczos_max < max_iter + 2) {
         cudaFree(S->lz);
-        cudaFree(S->lh);
-        S->lz = nullptr;
-        S->lh = nullptr;
+        cudaFree(S->lan_in);
+        cudaFree(S->lan_w);
+        cudaFree(S->lan_c);
+        S->lz = S->lan_in = S->lan_w = S->lan_c = nullptr;
         S->lanczos_max = 0;
-        FBIM_CUDA_TRY(h, cudaMalloc(&S->lz, sizeof(double) * (size_t)n * (max_iter + 1)));
-        FBIM_CUDA_TRY(h, cudaMalloc(&S->lh, sizeof(double) * 2 * (size_t)(max_iter + 1)));
-        S->lanczos_max = max_iter + 1;
+        FBIM_CUDA_TRY(h, cudaMalloc(&S->lz, sizeof(double) * (size_t)n * (max_iter + 2)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&S->lan_in, sizeof(double) * n));
+        FBIM_CUDA_TRY(h, cudaMalloc(&S->lan_w, sizeof(double) * n));
+        FBIM_CUDA_TRY(h, cudaMalloc(&S->lan_c, sizeof(double) * (max_iter + 1)));
+        FBIM_TRY(cgs_alloc(h, S->lan, n, n, max_iter + 1));
+        S->lanczos_max = max_iter + 2;
     }
+    CgsState& c = S->lan;
     const T* G = std::is_same<T, float>::value ? (const T*)S->G32 : (const T*)S->G64;
     const T* Gd = std::is_same<T, float>::value ? (const T*)S->Gd32 : (const T*)S->Gd64;
-    cublasHandle_t B = S->blas;
     double wn = 0;
-    FBIM_CUBLAS_TRY2(h, fbim_norm2(B, n, W, &wn));
+    FBIM_TRY(dev_norm2(h, n, W, wn));
     iters = 0;
     if (wn == 0) {
         FBIM_CUDA_TRY(h, cudaMemsetAsync(y, 0, sizeof(double) * n, h->stream));
         return FBIM_OK;
     }
     double* Vl = S->lz;
-    double* tmp = S->w;   // [>= n] scratch from the GMRES workspace
-    double* tmp2 = S->r;
-    FBIM_CUDA_TRY(h, cudaMemcpyAsync(Vl, W, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-    double inv = 1.0 / wn;
-    FBIM_CUBLAS_TRY2(h, cublasDscal(B, n, &inv, Vl, 1));
-    std::vector<double> alpha, beta, cprev, c;
-    const double one = 1.0, mone = -1.0, zero = 0.0;
-    std::vector<double> hc(2 * (max_iter + 1));
+    double* t1 = S->w;  // [>= n] scratch from the GMRES workspace
+    double* t2 = S->r;
+    cgs_start(h, c, 1.0 / wn, W, Vl, S->lan_in);
+    // One step on the device: w = G M(r) G^T v_k (v_k in lan_in), full reorthogonalisation
+    // against V_0..V_k (classical Gram-Schmidt, two passes, FP64), V_{k+1} = w / |w| into
+    // the basis and lan_in.  The host reads alpha_k and beta_k from the step's history row.
+    auto enqueue = [&](int k) -> fbim_status {
+        FBIM_TRY(block_apply<T>(h, G, S->lan_in, t1));
+        FBIM_TRY(apply_operator<T>(h, t1, t2, 1));
+        FBIM_TRY(block_apply<T>(h, G, t2, S->lan_w));
+        cgs_step(h, c, Vl, S->lan_w, true, S->lan_in);
+        FBIM_CUDA_TRY(h, cudaGetLastError());
+        FBIM_CUDA_TRY(h, cudaEventRecord(S->ev_step[k & 1], h->stream));
+        return FBIM_OK;
+    };
+    const int hs = cgs_hist_stride(c.m), m = c.m;
+    std::vector<double> alpha, beta, cprev, coef;
+    double d_last = -1.0, d_prev = -1.0;  // the last two step-to-step changes of the iterate
+    FBIM_TRY(enqueue(0));
     for (int k = 0; k < max_iter; ++k) {
-        double* vk = Vl + (size_t)k * n;
-        // w = G M(r) G^T v_k
-        FBIM_TRY(block_apply<T>(h, G, vk, tmp));
-        FBIM_TRY(apply_operator<T>(h, tmp, tmp2, 1));
-        FBIM_TRY(block_apply<T>(h, G, tmp2, tmp));
-        // alpha_k and full reorthogonalisation (classical Gram-Schmidt, twice)
-        FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, Vl, n, tmp, 1, &zero, S->lh, 1));
-        FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, Vl, n, S->lh, 1, &one, tmp, 1));
-        FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_T, n, k + 1, &one, Vl, n, tmp, 1, &zero,
-                                        S->lh + (max_iter + 1), 1));
-        FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_N, n, k + 1, &mone, Vl, n, S->lh + (max_iter + 1), 1, &one,
-                                        tmp, 1));
-        FBIM_CUDA_TRY(h, cudaMemcpyAsync(hc.data(), S->lh, sizeof(double) * 2 * (max_iter + 1),
-                                         cudaMemcpyDeviceToHost, h->stream));
-        double bn = 0;
-        FBIM_CUBLAS_TRY2(h, fbim_norm2(B, n, tmp, &bn));
-        FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-        alpha.push_back(hc[k] + hc[(max_iter + 1) + k]);
+        // queue the next step before reading this one, unless this one is predicted to
+        // converge (the last change, shrunk by the last ratio of changes, within tol)
+        bool ahead = k + 1 < max_iter;
+        if (ahead && d_last >= 0.0 && d_prev > 0.0) ahead = d_last * std::min(d_last / d_prev, 1.0) > tol;
+        if (ahead) FBIM_TRY(enqueue(k + 1));
+        FBIM_CUDA_TRY(h, cudaEventSynchronize(S->ev_step[k & 1]));
+        const double* row = c.hist_host + (size_t)k * hs;
+        const double bn = std::sqrt(std::max(row[2 * (m + 1)], 0.0));
+        alpha.push_back(row[k] + row[(m + 1) + k]);
         beta.push_back(bn);
         ++iters;
-        c = lanczos_coeffs(alpha, beta, k + 1, wn);
+        coef = lanczos_coeffs(alpha, beta, k + 1, wn);
         double dn = 0, cn = 0;
         for (int i = 0; i <= k; ++i) {
-            double prev = i < (int)cprev.size() ? cprev[i] : 0.0;
-            dn += (c[i] - prev) * (c[i] - prev);
-            cn += c[i] * c[i];
+            const double prev = i < (int)cprev.size() ? cprev[i] : 0.0;
+            dn += (coef[i] - prev) * (coef[i] - prev);
+            cn += coef[i] * coef[i];
         }
-        cprev = c;
+        cprev = coef;
         if (!std::isfinite(bn) || !std::isfinite(cn)) {
             h->fail("Lanczos iterate is not finite");
             return FBIM_ERR_NONFINITE;
         }
-        bool converged = (k > 0 && std::sqrt(dn) <= tol * std::sqrt(cn)) || bn <= 1e-14 * wn;
+        d_prev = d_last;
+        d_last = cn > 0.0 ? std::sqrt(dn / cn) : 0.0;
+        const bool converged = (k > 0 && std::sqrt(dn) <= tol * std::sqrt(cn)) || bn <= 1e-14 * wn;
         if (converged || k + 1 == max_iter) break;
-        double ib = 1.0 / bn;
-        double* vn = Vl + (size_t)(k + 1) * n;
-        FBIM_CUDA_TRY(h, cudaMemcpyAsync(vn, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-        FBIM_CUBLAS_TRY2(h, cublasDscal(B, n, &ib, vn, 1));
+        if (!ahead) FBIM_TRY(enqueue(k + 1));
     }
-    // y = G^+ V c
-    const int k = (int)c.size();
-    FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->lh, c.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
-    FBIM_CUBLAS_TRY2(h, cublasDgemv(B, CUBLAS_OP_N, n, k, &one, Vl, n, S->lh, 1, &zero, tmp, 1));
-    FBIM_TRY(block_apply<T>(h, Gd, tmp, y));
+    // y = G^+ V c; a step queued past the last one read is complete before the combination
+    const int k = (int)coef.size();
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->lan_c, coef.data(), sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+    dev_combine(h, n, k, Vl, n, S->lan_c, 0.0, t1);
+    FBIM_TRY(block_apply<T>(h, Gd, t1, y));
     return FBIM_OK;
 }
 

@@ -291,7 +291,7 @@ __device__ __forceinline__ void cgs_sum_partials(int K, int nb, const double* pa
 }
 
 // first pass: partial dots of w with V_0..V_k; also stores the step's preconditioned
-// vector z as Z_k
+// vector z as Z_k (Z non-null)
 __global__ void __launch_bounds__(CG_TB) k_cgs_dots(int n, const int* __restrict__ kd, const double* __restrict__ V,
                                                     int ld, const double* __restrict__ w, const double* __restrict__ z,
                                                     double* __restrict__ Z, int nb, double* __restrict__ part,
@@ -306,10 +306,12 @@ __global__ void __launch_bounds__(CG_TB) k_cgs_dots(int n, const int* __restrict
         wv[e] = i < n ? w[i] : 0.0;
     }
     cgs_block_dots(n, k + 1, V, ld, wv, nb, part, red);
+    if (Z) {  // (the Lanczos iteration keeps no preconditioned basis)
 #pragma unroll
-    for (int e = 0; e < CG_EPT; ++e) {
-        const int i = i0 + e * CG_TB;
-        if (i < n) Z[(size_t)k * ld + i] = z[i];
+        for (int e = 0; e < CG_EPT; ++e) {
+            const int i = i0 + e * CG_TB;
+            if (i < n) Z[(size_t)k * ld + i] = z[i];
+        }
     }
     if (cgs_last_block(count)) {  // the first pass's coefficients into history row k
         cgs_sum_partials(k + 1, nb, part, hist + (size_t)k * hist_stride(m));
@@ -397,6 +399,133 @@ __global__ void k_start(int n, double a, const double* __restrict__ w, double* _
     V[i] = v;
     y2[i] = v;
 }
+
+// <x, y> over n entries: per-block partials, the last block to finish sums them in a
+// fixed order (the result does not depend on scheduling) into *out (mapped host memory)
+__global__ void __launch_bounds__(CG_TB) k_dot(int n, const double* __restrict__ x, const double* __restrict__ y,
+                                               double* __restrict__ part, unsigned* __restrict__ count,
+                                               double* __restrict__ out) {
+    __shared__ double red[CG_TB / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double sacc = 0.0;
+#pragma unroll
+    for (int e = 0; e < CG_EPT; ++e) {
+        const int i = blockIdx.x * CG_CHUNK + threadIdx.x + e * CG_TB;
+        if (i < n) sacc = fma(x[i], y[i], sacc);
+    }
+    sacc = warp_sum(sacc);
+    if (lane == 0) red[warp] = sacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < CG_TB / 32; ++q) t += red[q];
+        part[blockIdx.x] = t;
+    }
+    if (!cgs_last_block(count)) return;
+    if (threadIdx.x < 32) {
+        double t = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + b);
+        t = warp_sum(t);
+        if (lane == 0) {
+            *out = t;
+            *count = 0u;
+        }
+    }
+}
+
+// y = beta y + sum_{j < k} c_j V_j (a basis combination; c on the device)
+__global__ void k_combine_basis(int n, int k, const double* __restrict__ V, int ld, const double* __restrict__ c,
+                                double beta, double* __restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = beta == 0.0 ? 0.0 : beta * y[i];
+    for (int j = 0; j < k; ++j) acc = fma(c[j], V[(size_t)j * ld + i], acc);
+    y[i] = acc;
+}
+
+}  // namespace
+
+// <x, y> for vectors of n <= the solver's length, on the handle's stream (host-synchronising)
+fbim_status dev_dot(fbim_handle_s* h, int n, const double* x, const double* y, double& out) {
+    Solver* S = h->solver;
+    const int nb = (n + CG_CHUNK - 1) / CG_CHUNK;
+    k_dot<<<nb, CG_TB, 0, h->stream>>>(n, x, y, S->dot_part, S->dot_count, S->dot_map);
+    h->launches += 1;
+    FBIM_CUDA_TRY(h, cudaGetLastError());
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    out = *(volatile double*)S->dot_host;
+    return FBIM_OK;
+}
+
+fbim_status dev_norm2(fbim_handle_s* h, int n, const double* x, double& out) {
+    double d = 0.0;
+    FBIM_TRY(dev_dot(h, n, x, x, d));
+    out = std::sqrt(std::max(d, 0.0));
+    return FBIM_OK;
+}
+
+void dev_combine(fbim_handle_s* h, int n, int k, const double* V, int ld, const double* c, double beta, double* y) {
+    k_combine_basis<<<(n + 255) / 256, 256, 0, h->stream>>>(n, k, V, ld, c, beta, y);
+    h->launches += 1;
+}
+
+// Device-driven classical Gram-Schmidt on a basis of rows V_j (stride ld): see k_cgs_dots.
+fbim_status cgs_alloc(fbim_handle_s* h, CgsState& c, int n, int ld, int m) {
+    cgs_free(c);
+    c.n = n;
+    c.ld = ld;
+    c.m = m;
+    c.nb = (n + CG_CHUNK - 1) / CG_CHUNK;
+    const size_t hist_bytes = sizeof(double) * (m + 1) * hist_stride(m);
+    FBIM_CUDA_TRY(h, cudaMalloc(&c.kd, sizeof(int)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&c.count, sizeof(unsigned)));
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(c.count, 0, sizeof(unsigned), h->stream));
+    FBIM_CUDA_TRY(h, cudaMalloc(&c.hist, hist_bytes));
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(c.hist, 0, hist_bytes, h->stream));
+    FBIM_CUDA_TRY(h, cudaMalloc(&c.part, sizeof(double) * (m + 1) * c.nb));
+    FBIM_CUDA_TRY(h, cudaHostAlloc(&c.hist_host, hist_bytes, cudaHostAllocMapped));
+    memset(c.hist_host, 0, hist_bytes);
+    FBIM_CUDA_TRY(h, cudaHostGetDevicePointer(&c.hist_map, c.hist_host, 0));
+    return FBIM_OK;
+}
+
+void cgs_free(CgsState& c) {
+    cudaFree(c.kd);
+    cudaFree(c.count);
+    cudaFree(c.hist);
+    cudaFree(c.part);
+    if (c.hist_host) cudaFreeHost(c.hist_host);
+    c = CgsState();
+}
+
+int cgs_hist_stride(int m) { return hist_stride(m); }
+
+// V_0 = a w (also into next_in), step index 0
+void cgs_start(fbim_handle_s* h, CgsState& c, double a, const double* w, double* V, double* next_in) {
+    k_start<<<(c.n + 255) / 256, 256, 0, h->stream>>>(c.n, a, w, V, next_in, c.kd);
+    h->launches += 1;
+}
+
+// Orthonormalise w against V_0..V_k (k = the device's step index) by classical Gram-Schmidt
+// (two passes or one), record the coefficients, |w|^2 and 1/|w| in history row k (and its
+// mapped host copy), then V_{k+1} = w / |w|, also into next_in; the step index advances.
+void cgs_step(fbim_handle_s* h, CgsState& c, double* V, double* w, bool two_pass, double* next_in) {
+    const cudaStream_t st = h->stream;
+    k_cgs_dots<<<c.nb, CG_TB, 0, st>>>(c.n, c.kd, V, c.ld, w, nullptr, nullptr, c.nb, c.part, c.hist, c.m, c.count);
+    if (two_pass) {
+        k_cgs_update<<<c.nb, CG_TB, 0, st>>>(c.n, c.kd, V, c.ld, c.hist, c.m, 0, w, 1, c.nb, c.part, c.hist_map,
+                                             c.count);
+        k_cgs_update<<<c.nb, CG_TB, 0, st>>>(c.n, c.kd, V, c.ld, c.hist, c.m, c.m + 1, w, 0, c.nb, c.part,
+                                             c.hist_map, c.count);
+    } else {
+        k_cgs_update<<<c.nb, CG_TB, 0, st>>>(c.n, c.kd, V, c.ld, c.hist, c.m, 0, w, 0, c.nb, c.part, c.hist_map,
+                                             c.count);
+    }
+    k_normalize<<<(c.n + 255) / 256, 256, 0, st>>>(c.n, c.kd, c.hist, c.m, w, V, c.ld, next_in);
+    h->launches += two_pass ? 4 : 3;
+}
+
+namespace {
 
 // ---------------------------------------------------------------------------
 // host helpers
@@ -596,6 +725,11 @@ fbim_status setup_solver(fbim_handle_s* h) {
     memset(S->hist_host, 0, hist_bytes + sizeof(double) * (m + 1));
     FBIM_CUDA_TRY(h, cudaHostGetDevicePointer(&S->hist_map, S->hist_host, 0));
     for (cudaEvent_t& ev : S->ev_step) FBIM_CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->dot_part, sizeof(double) * ((n + CG_CHUNK - 1) / CG_CHUNK)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&S->dot_count, sizeof(unsigned)));
+    FBIM_CUDA_TRY(h, cudaMemsetAsync(S->dot_count, 0, sizeof(unsigned), h->stream));
+    FBIM_CUDA_TRY(h, cudaHostAlloc(&S->dot_host, sizeof(double), cudaHostAllocMapped));
+    FBIM_CUDA_TRY(h, cudaHostGetDevicePointer(&S->dot_map, S->dot_host, 0));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gz, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMalloc(&S->gw, sizeof(double) * n));
     FBIM_CUDA_TRY(h, cudaMemsetAsync(S->gin, 0, sizeof(double) * n, h->stream));
@@ -627,6 +761,13 @@ void free_solver(fbim_handle_s* h) {
                     (void*)S->gw, (void*)S->cg_part, (void*)S->kd, (void*)S->hist, (void*)S->cg_count})
         cudaFree(p);
     if (S->hist_host) cudaFreeHost(S->hist_host);
+    if (S->dot_host) cudaFreeHost(S->dot_host);
+    cudaFree(S->dot_part);
+    cudaFree(S->dot_count);
+    cgs_free(S->lan);
+    cudaFree(S->lan_in);
+    cudaFree(S->lan_w);
+    cudaFree(S->lan_c);
     tc_free(S->tc_Mp);
     tc_free(S->tc_G);
     tc_free(S->tc_Gd);
@@ -807,9 +948,8 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
                           double bnorm_in = 0.0) {
     Solver* S = h->solver;
     const int n = S->n, m = S->restart, ld = S->ld, hs = hist_stride(m);
-    cublasHandle_t B = S->blas;
     double bnorm = bnorm_in;
-    if (!(bnorm > 0.0)) FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, b, &bnorm));
+    if (!(bnorm > 0.0)) FBIM_TRY(dev_norm2(h, n, b, bnorm));
     iters = 0;
     rel_est = 0;
     if (bnorm == 0) {
@@ -834,7 +974,6 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
         FBIM_CUDA_TRY(h, cudaEventRecord(S->ev_step[k & 1], h->stream));
         return FBIM_OK;
     };
-    const double one = 1.0;
     const int tb = 256, nb = (n + tb - 1) / tb;
     bool first = true;
     while (true) {
@@ -847,7 +986,7 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
             FBIM_TRY(saddle_apply<T>(h, x, S->w));
             k_axpby<<<nb, tb, 0, h->stream>>>(n, 1.0, b, -1.0, S->w);  // w = b - w
             h->launches += 1;
-            FBIM_CUBLAS_TRY(h, fbim_norm2(B, n, S->w, &beta));
+            FBIM_TRY(dev_norm2(h, n, S->w, beta));
         }
         first = false;
         rel_est = beta / bnorm;
@@ -908,7 +1047,7 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
             y[i] = acc / Hh[(size_t)i * (m + 1) + i];
         }
         FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->hcol, y, sizeof(double) * k_used, cudaMemcpyHostToDevice, h->stream));
-        FBIM_CUBLAS_TRY(h, cublasDgemv(B, CUBLAS_OP_N, n, k_used, &one, S->Z, ld, S->hcol, 1, &one, x, 1));
+        dev_combine(h, n, k_used, S->Z, ld, S->hcol, 1.0, x);
         // A correction of iterative refinement stops on the cycle's own estimate: the
         // outer loop measures the true FP64 residual anyway, and a restart started only
         // because the FP32 residual lands just above the inner tolerance costs a cycle.
@@ -929,7 +1068,7 @@ static fbim_status true_residual(fbim_handle_s* h, const double* b, const double
     k_axpby<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0, b, -1.0, r);
     h->launches += 1;
     rn = 0;
-    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, r, &rn));
+    FBIM_TRY(dev_norm2(h, n, r, rn));
     rel = bn > 0 ? rn / bn : 0.0;
     return FBIM_OK;
 }
@@ -945,8 +1084,8 @@ static fbim_status measure_e32(fbim_handle_s* h) {
     FBIM_TRY(saddle_apply<double>(h, S->corr, S->r));
     k_axpby<<<(n + 255) / 256, 256, 0, h->stream>>>(n, 1.0, S->r, -1.0, S->w);  // w = A_64 v - A_32 v
     double en = 0.0, vn = 0.0;
-    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->w, &en));
-    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->corr, &vn));
+    FBIM_TRY(dev_norm2(h, n, S->w, en));
+    FBIM_TRY(dev_norm2(h, n, S->corr, vn));
     S->e32 = vn > 0.0 ? en / vn : 0.0;
     return FBIM_OK;
 }
@@ -966,7 +1105,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
     if (!warm) FBIM_CUDA_TRY(h, cudaMemsetAsync(S->d, 0, sizeof(double) * n, h->stream));
     int iters = 0;
     double rel = 1.0, bn = 0.0, rn = 0.0;  // |r| / |b|, |b|, |r|
-    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->t, &bn));
+    FBIM_TRY(dev_norm2(h, n, S->t, bn));
     if (h->precision == FBIM_FP64) {
         double est = 0;
         FBIM_TRY(fgmres<double>(h, S->t, S->d, tol, max_iter, iters, est, !warm, false, bn));
@@ -1023,7 +1162,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
                 const double rel_prev = rel;
                 rel = est * rel_prev;
                 double dn = 0.0;
-                FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, corr, &dn));
+                FBIM_TRY(dev_norm2(h, n, corr, dn));
                 drift += 3.0 * S->e32 * dn / (bn > 0 ? bn : 1.0);
                 if (rel <= tol && rel + drift > tol) {
                     // the estimate cannot vouch for convergence: measure
@@ -1037,7 +1176,7 @@ fbim_status mobility_solve(fbim_handle_s* h, const double* F, const double* slip
                     FBIM_TRY(saddle_apply<float>(h, corr, S->w));
                     k_axpby<<<nb, tb, 0, h->stream>>>(n, -1.0, S->w, 1.0, S->r);
                     h->launches += 1;
-                    FBIM_CUBLAS_TRY(h, fbim_norm2(S->blas, n, S->r, &rn));
+                    FBIM_TRY(dev_norm2(h, n, S->r, rn));
                     rel = bn > 0 ? rn / bn : 0.0;
                 }
             }

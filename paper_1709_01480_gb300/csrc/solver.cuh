@@ -5,14 +5,22 @@
 #include <cmath>
 #include <vector>
 
-// Euclidean norm through a dot product (one reduction kernel; the library's nrm2
-// routine uses a slower overflow-safe scaling that these vectors do not need).
-inline cublasStatus_t fbim_norm2(cublasHandle_t b, int n, const double* x, double* out) {
-    double d = 0.0;
-    cublasStatus_t st = cublasDdot(b, n, x, 1, x, 1, &d);
-    *out = std::sqrt(d);
-    return st;
-}
+struct fbim_handle_s;
+
+// Device-driven classical Gram-Schmidt state of a Krylov basis (the Lanczos iteration of
+// the near-field square root; solver.cu): the index of the newest basis vector on the
+// device, the step history (two passes of coefficients, |w|^2, 1/|w| per row) with its
+// mapped host copy, and the block partials of the fused sweeps.
+struct CgsState {
+    int m = 0;                   // history rows m + 1
+    int n = 0, ld = 0, nb = 0;   // vector length, basis row stride, sweep blocks
+    int* kd = nullptr;
+    unsigned* count = nullptr;
+    double* hist = nullptr;
+    double* hist_host = nullptr;
+    double* hist_map = nullptr;
+    double* part = nullptr;
+};
 
 // A reference block B_ref laid out for the tensor-core block operator (block_tc.cu):
 // TF32 high and low parts in chunks of 32 K-columns and M-tiles of 128 rows.
@@ -77,6 +85,17 @@ struct Solver {
     // G_ref^+ (near-field square root); tc_err = device flag of a timed-out wait
     TcBlock tc_Mp, tc_G, tc_Gd;
     int* tc_err = nullptr;
+    // dot products: block partials, finished-block count, and the result's mapped host slot
+    double* dot_part = nullptr;
+    unsigned* dot_count = nullptr;
+    double* dot_host = nullptr;
+    double* dot_map = nullptr;
+    // Lanczos (brownian.cu): Gram-Schmidt state over the basis lz, the step input, the
+    // orthogonalised vector and the coefficients of the final combination
+    CgsState lan;
+    double* lan_in = nullptr;
+    double* lan_w = nullptr;
+    double* lan_c = nullptr;
 };
 
 namespace fbim {
@@ -88,4 +107,14 @@ fbim_status tc_apply(fbim_handle_s* h, const TcBlock& B, int mode, const double*
                      float* out_g, const float* H, const double* Nt, int* err);
 // FBIM_ERR_TIMEOUT when a tensor-core block kernel gave up a wait (host-synchronising)
 fbim_status tc_check(fbim_handle_s* h);
+// vector kernels of the solvers (solver.cu): <x, y> and |x| (host-synchronising), and
+// y = beta y + sum_{j < k} c_j V_j with c on the device
+fbim_status dev_dot(fbim_handle_s* h, int n, const double* x, const double* y, double& out);
+fbim_status dev_norm2(fbim_handle_s* h, int n, const double* x, double& out);
+void dev_combine(fbim_handle_s* h, int n, int k, const double* V, int ld, const double* c, double beta, double* y);
+fbim_status cgs_alloc(fbim_handle_s* h, CgsState& c, int n, int ld, int m);
+void cgs_free(CgsState& c);
+int cgs_hist_stride(int m);
+void cgs_start(fbim_handle_s* h, CgsState& c, double a, const double* w, double* V, double* next_in);
+void cgs_step(fbim_handle_s* h, CgsState& c, double* V, double* w, bool two_pass, double* next_in);
 }  // namespace fbim
