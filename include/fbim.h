@@ -7,7 +7,8 @@
  * split Ewald sum (Sec. 3.2), solves the first-kind mobility problem (Sec. 3.1,
  * Eq. discreteSaddlePoint) with block-diagonal preconditioned GMRES (Sec. 3.4),
  * draws the random slip M^1/2 W (Sec. 3.3) and advances Brownian rigid bodies
- * with the Euler-Maruyama random-finite-difference step (Sec. 4.4, Eq. EM-RFD).
+ * with the Euler-Maruyama and Adams-Bashforth random-finite-difference steps (Sec. 4.4,
+ * Eqs. EM-RFD, AB2-RFD).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -242,6 +243,25 @@ fbim_status fbim_brownian_slip(fbim_handle h, uint64_t seed, uint64_t counter, d
 fbim_status fbim_rfd_step(fbim_handle h, const double* F_dev, double dt, double kT, double delta, uint64_t seed,
                           uint64_t step, const double* W_r_dev, const double* Z_w_dev, const double* W_t_dev,
                           double tol, int max_iter, double* Q_dev, int* iters);
+
+/* Brownian dynamics step schemes of Sec. 4.4 (fbim_bd_step). */
+typedef enum { FBIM_EM = 0, FBIM_AB2 = 1 } fbim_scheme;
+
+/* One Brownian dynamics step with a random finite difference (Sec. 4.4):
+ *   FBIM_EM  (Eq. EM-RFD): as fbim_rfd_step, three solves.
+ *   FBIM_AB2 (Eq. AB2-RFD): Q <- Q + dt (3/2 N F - 1/2 N_prev F_prev) + sqrt(2 kT dt) N^1/2 W
+ *            + dt kT/delta [N(Q + delta/2 W~) - N(Q - delta/2 W~)] W~, four solves (N F, the
+ *            slip's velocity with force zero, the RFD pair).
+ * The RFD pair is solved to tol_rfd, the other solves to tol (Sec. 4.4.2 uses 1e-3 and
+ * 1e-6; tol_rfd = tol reproduces fbim_rfd_step for FBIM_EM).  NF_dev (double [n_b][3],
+ * device; FBIM_AB2 only, NULL allowed for FBIM_EM): on entry N_prev F_prev of the previous
+ * step when have_prev != 0 (have_prev = 0: the first step, dt N F for the deterministic
+ * part), on exit N F of this step.  Noise arguments, Q_dev and iters as in fbim_rfd_step
+ * (the slip's Philox counter is 3 step, W~'s counter step).  Synchronises the stream. */
+fbim_status fbim_bd_step(fbim_handle h, int scheme, const double* F_dev, double dt, double kT, double delta,
+                         uint64_t seed, uint64_t step, const double* W_r_dev, const double* Z_w_dev,
+                         const double* W_t_dev, double tol, double tol_rfd, int max_iter, double* NF_dev,
+                         int have_prev, double* Q_dev, int* iters);
 
 /* n standard normals of (seed, stream, counter) from Philox4x32-10 and Box-Muller:
  * normal i is element i mod 2 of block i / 2, counter block = (i/2 low, i/2 high,

@@ -42,7 +42,7 @@ EXPORTS = [
     "fbim_mlp_set_params", "fbim_mlp_get_params", "fbim_mlp_set_normalization", "fbim_mlp_forward",
     "fbim_mlp_gradient", "fbim_mlp_adam_step", "fbim_mlp_launches", "fbim_coarse_pairs",
     "fbim_coarse_enable", "fbim_coarse_stats", "fbim_apply_stokeslet_fp64",
-    "fbim_set_residual_audit", "fbim_residual_audit", "fbim_precondition",
+    "fbim_set_residual_audit", "fbim_residual_audit", "fbim_precondition", "fbim_bd_step",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -152,6 +152,8 @@ _lib.fbim_coarse_enable.argtypes = [_P, _P, _D]
 _lib.fbim_coarse_stats.argtypes = [_P, _IP, _IP]
 _lib.fbim_set_residual_audit.argtypes = [_P, _I]
 _lib.fbim_precondition.argtypes = [_P, _P, _P]
+_lib.fbim_bd_step.argtypes = [_P, _I, _P, _D, _D, _D, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P, _D, _D, _I, _P,
+                              _I, _P, _IP]
 _lib.fbim_residual_audit.argtypes = [_P, _I, _DP, _DP, _IP]
 
 
@@ -319,6 +321,19 @@ class FBIM:
         _check(_lib.fbim_rfd_step(self._h, _ptr(F), float(dt), float(kT), float(delta), int(seed), int(step),
                                   opt(W_r), opt(Z_w), opt(W_t), float(tol), int(max_iter), _ptr(Q),
                                   ctypes.byref(it)), self._h)
+        return it.value
+
+    def bd_step(self, F, Q, dt, kT=1.0, delta=1e-3, scheme="em", seed=0, step=0, W_r=None, Z_w=None, W_t=None,
+                tol=1e-6, tol_rfd=None, NF=None, have_prev=False, max_iter=500):
+        """One Brownian dynamics step (scheme "em" or "ab2"); Q is updated in place.  For "ab2",
+        NF (device [n_b, 3]) carries N F between steps (read when have_prev, written always).
+        Returns the GMRES iterations of the step's solves."""
+        it = ctypes.c_int(0)
+        opt = lambda t: None if t is None else _ptr(t)
+        sch = {"em": 0, "ab2": 1}[scheme]
+        _check(_lib.fbim_bd_step(self._h, sch, _ptr(F), float(dt), float(kT), float(delta), int(seed), int(step),
+                                 opt(W_r), opt(Z_w), opt(W_t), float(tol), float(tol if tol_rfd is None else tol_rfd),
+                                 int(max_iter), opt(NF), 1 if have_prev else 0, _ptr(Q), ctypes.byref(it)), self._h)
         return it.value
 
     def philox_normals(self, n, seed=0, stream=0, counter=0):

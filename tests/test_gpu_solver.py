@@ -192,6 +192,60 @@ def test_fp64_rfd_step_matches_oracle(torch, fb, tiny):
     op.close()
 
 
+def test_fp64_ab2_steps_match_oracle(torch, fb, tiny):
+    """Two AB2-RFD steps (Sec. 4.4, Eq. AB2-RFD) with given noise: the first takes the Euler
+    deterministic part, the second the carried N^{n-1} F^{n-1}; displacements and the
+    carried N F against the oracle's."""
+    from oracle import rfd
+    w, xi, grid = tiny["w"], tiny["xi"], tiny["grid"]
+    op = _op(fb, tiny)
+    rng = np.random.default_rng(56)
+    dt, kT, delta = 1e-3, 1.0, 1e-2
+    Q = torch.tensor(w.Q, device="cuda")
+    NF = torch.zeros((w.n_b, 3), dtype=torch.float64, device="cuda")
+    Qh, NF_or = w.Q.copy(), None
+    for k in range(2):
+        W_r = rng.standard_normal((w.n, 2))
+        Z = rng.standard_normal((grid, grid, 2, 2))
+        Wt = rng.standard_normal((w.n_b, 3))
+        F = w.F * (1.0 + 0.5 * k)
+        op.bd_step(torch.tensor(F, device="cuda"), Q, dt, kT, delta, scheme="ab2", W_r=torch.tensor(W_r, device="cuda"),
+                   Z_w=torch.tensor(Z, device="cuda"), W_t=torch.tensor(Wt, device="cuda"), tol=1e-12, NF=NF,
+                   have_prev=k > 0)
+        Q_new, NF_or = rfd.ab2_rfd_step(Qh, w.ref_nodes, w.L, xi, F, NF_or, dt, kT, delta, W_r, Z, Wt)
+        err = _rel(Q.cpu().numpy() - Qh, Q_new - Qh)
+        err_nf = _rel(NF.cpu().numpy(), NF_or)
+        print(f"AB2 step {k}: rel err of the displacement {err:.3e}, of N F {err_nf:.3e}")
+        assert err < 1e-8 and err_nf < 1e-9
+        Qh = Q_new
+        # continue both from the oracle's configuration so that the steps are compared alike
+        Q.copy_(torch.tensor(Qh, device="cuda"))
+    op.close()
+
+
+def test_split_tolerance_em_step(torch, fb, tiny):
+    """EM-RFD with the RFD pair solved at 1e-3 and the velocity at 1e-8 (Sec. 4.4.2): its
+    displacement differs from the all-1e-8 step by no more than the pair's tolerance allows
+    (dt kT/delta times ~1e-3 of the pair's velocities)."""
+    w = tiny["w"]
+    rng = np.random.default_rng(57)
+    Wt = torch.tensor(rng.standard_normal((w.n_b, 3)), device="cuda")
+    F = torch.tensor(w.F, device="cuda")
+    dQ = {}
+    its = {}
+    for tol_rfd in (1e-8, 1e-3):
+        op = _op(fb, tiny, "fp32")
+        Q = torch.tensor(w.Q, device="cuda")
+        its[tol_rfd] = op.bd_step(F, Q, 1e-3, 1.0, 1e-2, scheme="em", seed=9, step=0, W_t=Wt, tol=1e-8,
+                                  tol_rfd=tol_rfd)
+        dQ[tol_rfd] = Q.cpu().numpy() - w.Q
+        op.close()
+    rel = _rel(dQ[1e-3], dQ[1e-8])
+    print(f"split tolerances: iterations {its[1e-8]} -> {its[1e-3]}, displacement change {rel:.2e}")
+    assert its[1e-3] < its[1e-8]
+    assert rel < 5e-3  # measured 2.7e-4 (48 -> 28 iterations)
+
+
 def test_mixed_precision_errors_vs_oracle(torch, fb, tiny):
     """The mixed form's error against the FP64 oracle, reported apart for body velocities,
     rotations and Brownian displacements (FP32 operator, FP64 refinement; solves and the

@@ -1,4 +1,4 @@
-"""Pins for the oracle's Euler-Maruyama random-finite-difference step (Sec. 4.4, Eq. EM-RFD).
+"""Pins for the oracle's random-finite-difference steps (Sec. 4.4, Eqs. EM-RFD, AB2-RFD).
 
 What the paper fixes about the step:
 
@@ -10,6 +10,8 @@ What the paper fixes about the step:
   to O(delta^2), the quadratic form W~ -> (D_W~ N) W~, its expectation is the sum of
   that form over the unit vectors e_j: sum_j (d_j N)[:, j], the divergence.
 * At fixed W~, the term tends to dt kT (D_W~ N) W~ as delta -> 0.
+* The Adams-Bashforth step's deterministic part, dt (3/2 N^n F^n - 1/2 N^{n-1} F^{n-1}),
+  is second-order accurate where the Euler step's dt N F is first-order.
 
 The expected values come from central differences (with Richardson extrapolation)
 of the oracle's mobility N, computed column by column from dense saddle solves at
@@ -109,3 +111,46 @@ def test_deterministic_part_is_dt_N_F():
     got = _step(Q, ref, F, dt, 1.0, 1e-3, np.zeros(Q.size))
     expect = Q + dt * (_mobility(Q, ref) @ F.reshape(-1)).reshape(-1, 3)
     assert np.max(np.abs(got - expect)) < 1e-12 * np.max(np.abs(Q))
+
+
+def _spring_force(Q):
+    """Forces and torques of a spring between the two tracking points (rest length 1.5,
+    stiffness 40) and angular springs to pi/4 and pi/2 (stiffness 2): F = -dU/dQ."""
+    d = Q[1, :2] - Q[0, :2]
+    r = np.linalg.norm(d)
+    f = 40.0 * (r - 1.5) * d / r
+    F = np.zeros_like(Q)
+    F[0, :2] = f
+    F[1, :2] = -f
+    F[0, 2] = -2.0 * (Q[0, 2] - 0.25 * math.pi)
+    F[1, 2] = -2.0 * (Q[1, 2] - 0.5 * math.pi)
+    return F
+
+
+def _trajectory(scheme, dt, T, ref):
+    Q = np.array([[1.0, 1.2, 0.3], [2.25, 1.55, 1.7]])
+    W_r, Z = _zero_noise(Q.shape[0] * ref.shape[0], M=8)
+    zero = np.zeros(Q.size)
+    NF = None
+    for _ in range(int(round(T / dt))):
+        F = _spring_force(Q)
+        if scheme == "ab2":
+            Q, NF = rfd.ab2_rfd_step(Q, ref, L, XI, F, NF, dt, 0.0, 1e-3, W_r, Z, zero)
+        else:
+            Q = rfd.em_rfd_step(Q, ref, L, XI, F, dt, 0.0, 1e-3, W_r, Z, zero)
+    return Q
+
+
+def test_ab2_deterministic_part_converges_at_second_order():
+    # Sec. 4.4, Eq. AB2-RFD: 3/2 N^n F^n - 1/2 N^{n-1} F^{n-1} is the second-order
+    # Adams-Bashforth step; at kT = 0 (no noise, no drift) the trajectory's successive
+    # differences under halving dt shrink by ~4 (second order) against ~2 for Euler
+    ref = fbim_synth.starfish_ref_nodes(12)
+    T = 0.4
+    ratios = {}
+    for scheme in ("ab2", "em"):
+        q = [_trajectory(scheme, dt, T, ref) for dt in (0.1, 0.05, 0.025)]
+        ratios[scheme] = np.linalg.norm(q[0] - q[1]) / np.linalg.norm(q[1] - q[2])
+    print(f"successive-difference ratios: AB2 {ratios['ab2']:.2f}, EM {ratios['em']:.2f}")
+    assert 3.0 < ratios["ab2"] < 5.5
+    assert 1.5 < ratios["em"] < 2.6
