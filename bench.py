@@ -328,7 +328,10 @@ def learned_leg(torch, fb, fbim_synth, stream, flush, reps):
         res[mode] = {"ms_per_solve": float(np.mean(ms)), "gmres_iters": its[-1][0], "residual": its[-1][1],
                      "solves_per_s": 1e3 / float(np.mean(ms))}
     n_pairs, n_rej = op.coarse_stats()
-    res["learned_coarse"].update({"pairs": n_pairs, "pairs_dropped": n_rej, "setup_s": setup_s})
+    res["learned_coarse"].update({"pairs": n_pairs, "pairs_dropped": n_rej, "setup_s": setup_s,
+                                  "stagnation_fallbacks": op.info["coarse_fallbacks"],
+                                  "note": "a GMRES cycle without a tenfold residual drop in 20 steps falls back "
+                                          "to the block-diagonal preconditioner for the configuration"})
     op.coarse_enable(None, 1.0)
     op.close()
     model.close()

@@ -116,6 +116,10 @@ typedef struct {
     int    fp64_fft;         /* transforms and Fourier scale of the FP64 operator: 1 float-
                                 float kernels (FP32 handles with an even 5-smooth grid),
                                 -1 cuFFT double, 0 not yet set up (first FP64 use)      */
+    int    coarse_fallbacks; /* GMRES cycles in which the learned coarse level stagnated
+                                (no tenfold residual drop in 20 steps), after which the
+                                solve went on with the block-diagonal preconditioner and
+                                the coarse level stayed off until the next move          */
 } fbim_info;
 
 /* Fill *p with defaults: FP64, order 4, automatic grid and support, eta = 1,
@@ -391,8 +395,11 @@ fbim_status fbim_coarse_pairs(fbim_handle h, double g_c, int max_pairs, int* pai
  * recomputes the body's traction from that U (the body solve of Sec. 3.4 with the
  * mobility N~ + sum C).  C comes from the network at every new configuration; a
  * pair's correction is dropped when blockdiag(N~_p, N~_q) + C_pq is not positive
- * definite or not finite.  The model must outlive its use by the handle and is
- * evaluated on the handle's stream. */
+ * definite or not finite.  A GMRES cycle that does not cut its residual tenfold within
+ * 20 steps with the coarse level on falls back to the block-diagonal preconditioner for
+ * the rest of the solve and the current configuration (fbim_info.coarse_fallbacks counts
+ * these).  The model must outlive its use by the handle and is evaluated on the handle's
+ * stream. */
 fbim_status fbim_coarse_enable(fbim_handle h, fbim_mlp model, double g_c);
 
 /* Pairs in use and pairs dropped at the last coarse-level setup (NULL allowed). */

@@ -19,6 +19,11 @@ two bodies alone (Sec. 3.1, Eq. discreteParticleVelocity, applied to the pair).
 * ``to_lab``          T(theta_a) C T(theta_a)^T, T(t) = blockdiag(R(t) + 1, R(t) + 1)
 * ``coarse_velocity`` U = N~ a + sum over pairs of C_lab a_pair, the coarse-level body
                       velocities for effective body forces a
+* ``coarse_preconditioner`` one application of the block preconditioner of Sec. 3.4
+                      with the coarse level: per body g = M~_b^+ r_mu,b and a_b = r_U,b +
+                      K_b^T g_b, then U = -coarse_velocity(N~, pairs, C, a) and
+                      mu_b = M~_b^+ (r_mu,b + K_b U_b), with M~_b^+ = R_b M_ref^+ R_b^T and
+                      N~_b = R_b N~_ref R_b^T (the reference body alone in the box)
 
 Parity: the pair list and features are plain definitions, checked by brute
 force and by invariance under a common translation and a periodic shift; the
@@ -110,3 +115,28 @@ def coarse_velocity(N_tilde: np.ndarray, pairs: np.ndarray, C_lab: np.ndarray, a
         U[p] += du[:3]
         U[q] += du[3:]
     return U
+
+
+def coarse_preconditioner(r_mu, r_U, Q, ref_nodes, L, xi, pairs, C_lab, eta=1.0, order=4):
+    """P^-1 [r_mu; r_U] with the coarse level: returns (mu [N, 2], U [N_b, 3])."""
+    n_b, n_p = Q.shape[0], ref_nodes.shape[0]
+    Xr = singlelayer.node_positions(np.array([[0.5 * L, 0.5 * L, 0.0]]), ref_nodes)
+    Mp_ref = saddle.pinv_sym(singlelayer.single_layer(Xr, L, xi, eta, order))
+    K_ref = saddle.k_matrix(Xr, np.array([[0.5 * L, 0.5 * L, 0.0]]))
+    N_ref = np.linalg.inv(K_ref.T @ Mp_ref @ K_ref)
+    X = singlelayer.node_positions(Q, ref_nodes)
+    r_mu = np.asarray(r_mu, dtype=np.float64).reshape(n_b, 2 * n_p)
+    r_U = np.asarray(r_U, dtype=np.float64).reshape(n_b, 3)
+    Mp, Kb, a, N_t = [], [], np.zeros((n_b, 3)), np.zeros((n_b, 3, 3))
+    for b in range(n_b):
+        c, s = np.cos(Q[b, 2]), np.sin(Q[b, 2])
+        R = np.kron(np.eye(n_p), np.array([[c, -s], [s, c]]))
+        T3 = np.eye(3)
+        T3[:2, :2] = [[c, -s], [s, c]]
+        Mp.append(R @ Mp_ref @ R.T)
+        Kb.append(saddle.k_matrix(X[b:b + 1], Q[b:b + 1]))
+        a[b] = r_U[b] + Kb[b].T @ Mp[b] @ r_mu[b]
+        N_t[b] = T3 @ N_ref @ T3.T
+    U = -coarse_velocity(N_t, pairs, C_lab, a)
+    mu = np.stack([Mp[b] @ (r_mu[b] + Kb[b] @ U[b]) for b in range(n_b)])
+    return mu.reshape(-1, 2), U

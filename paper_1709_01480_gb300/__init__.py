@@ -73,7 +73,8 @@ class Info(ctypes.Structure):
                 ("launches", ctypes.c_longlong), ("grid_min", ctypes.c_int), ("grid_tune_ms", ctypes.c_double),
                 ("split_candidates", ctypes.c_int), ("split_cost_ms", ctypes.c_double),
                 ("interp_variant", ctypes.c_int), ("interp_ms", ctypes.c_double * 2),
-                ("support32", ctypes.c_int), ("eta_s32", ctypes.c_double), ("fp64_fft", ctypes.c_int)]
+                ("support32", ctypes.c_int), ("eta_s32", ctypes.c_double), ("fp64_fft", ctypes.c_int),
+                ("coarse_fallbacks", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

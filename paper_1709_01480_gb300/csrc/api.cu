@@ -451,6 +451,7 @@ extern "C" fbim_status fbim_get_info(fbim_handle h, fbim_info* info) {
     info->split_candidates = h->split_candidates;
     info->split_cost_ms = h->split_cost_ms;
     info->fp64_fft = h->precision == FBIM_FP32 ? h->fft64.state : -1;
+    info->coarse_fallbacks = h->coarse_fallbacks;
     return FBIM_OK;
 }
 

@@ -535,7 +535,7 @@ fbim_status coarse_refresh(fbim_handle_s* h) {
 }
 
 bool coarse_active(fbim_handle_s* h, fbim_status* st) {
-    if (!h->coarse) return false;
+    if (!h->coarse || h->coarse_suspended_geom == h->geom_version) return false;
     *st = coarse_refresh(h);
     return *st == FBIM_OK;
 }

@@ -202,11 +202,11 @@ struct fbim_handle_s {
     long long launches = 0;      // kernels this library has launched on the handle (counted at launch sites)
     unsigned long long layout_version = 0;  // bumped when a buffer that launches take by pointer is reallocated
     unsigned long long geom_version = 0;    // bumped by every geometry rebuild
-    struct Coarse* coarse = nullptr;        // allocation-free real-space entry point (noalloc.cu): run by fbim_setup on the
-// handle's device so that the entry point's first call loads and allocates nothing
-fbim_status noalloc_prepare(fbim_handle_s* h);
-
-// learned coarse level (coarse.cu), NULL when off
+    struct Coarse* coarse = nullptr;        // learned coarse level (coarse.cu), NULL when off
+    // the stagnation guard of GMRES suspends the coarse level for the geometry it
+    // stagnated on (block-diagonal preconditioner until the next move)
+    unsigned long long coarse_suspended_geom = ~0ull;
+    int coarse_fallbacks = 0;
 
     int n_cell() const { return n_box * n_box; }
     void fail(const std::string& m) { err = m; }

@@ -975,8 +975,10 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
         return FBIM_OK;
     };
     const int tb = 256, nb = (n + tb - 1) / tb;
-    bool first = true;
+    bool first = true, recapture = false;
     while (true) {
+        if (recapture && use_graph) FBIM_TRY(op_graph<T>(h));
+        recapture = false;
         // r = b - A x (just b when the initial guess is zero)
         double beta = 0;
         if (first && x_is_zero) {
@@ -1001,6 +1003,12 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
         gvec[0] = beta;
         int k_used = 0;
         double res1 = rel_est, res2 = 0.0;  // residual estimates after the last two steps
+        const double res_start = rel_est;
+        // stagnation guard of the learned coarse level: a cycle that has not cut the
+        // residual tenfold in kGuardSteps steps ends here, and the solve goes on with the
+        // block-diagonal preconditioner (the coarse level stays off for this geometry)
+        constexpr int kGuardSteps = 20;
+        bool stagnated = false;
         FBIM_TRY(enqueue(0));
         for (int k = 0; k < m; ++k) {
             bool ahead = k + 1 < m && iters + 1 < max_iter;
@@ -1036,6 +1044,11 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
             res2 = res1;
             res1 = std::fabs(gvec[k + 1]) / bnorm;
             if (res1 <= tol || iters >= max_iter || hn == 0) break;
+            if (k + 1 == kGuardSteps && res1 > 0.1 * res_start && h->coarse &&
+                h->coarse_suspended_geom != h->geom_version) {
+                stagnated = true;
+                break;
+            }
             if (!ahead && k + 1 < m) FBIM_TRY(enqueue(k + 1));
         }
         // y = R^-1 g (upper triangular), x += Z y; y is staged in pinned memory after the
@@ -1048,6 +1061,13 @@ static fbim_status fgmres(fbim_handle_s* h, const double* b, double* x, double t
         }
         FBIM_CUDA_TRY(h, cudaMemcpyAsync(S->hcol, y, sizeof(double) * k_used, cudaMemcpyHostToDevice, h->stream));
         dev_combine(h, n, k_used, S->Z, ld, S->hcol, 1.0, x);
+        if (stagnated) {
+            h->coarse_suspended_geom = h->geom_version;
+            ++h->coarse_fallbacks;
+            ++h->layout_version;  // the captured step holds the coarse level: recapture
+            recapture = true;
+            continue;             // a new cycle from the true residual of the updated x
+        }
         // A correction of iterative refinement stops on the cycle's own estimate: the
         // outer loop measures the true FP64 residual anyway, and a restart started only
         // because the FP32 residual lands just above the inner tolerance costs a cycle.

@@ -152,3 +152,81 @@ def test_coarse_level_solve(torch, fb):
     op.close()
     model.close()
     bad.close()
+
+
+def test_coarse_stagnation_guard_falls_back_to_the_block_preconditioner(torch, fb):
+    """A coarse level that passes the positive-definiteness check but misleads GMRES (every
+    close pair corrected by C = c I): the stagnation guard ends the cycle after 20 steps
+    without a tenfold residual drop, and the solve reaches its tolerance on the
+    block-diagonal preconditioner with the block solve's solution."""
+    w = _suspension()
+    op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=1e-10, r_c=0.5)
+    F = torch.tensor(w.F, device="cuda")
+    U0, _, it0, _ = op.mobility_solve(F, tol=1e-10, max_iter=500)
+    bad = fb.MLP(max_batch=64)
+    theta = np.zeros(fb.mlp_param_count(), dtype=np.float32)
+    theta[-36:][[0, 7, 14, 21, 28, 35]] = 1.0e4   # output bias: C = 1e4 I, weights zero
+    bad.set_params(theta)
+    bad.set_normalization(np.zeros(6), np.ones(6), np.ones(36))
+    op.coarse_enable(bad, 1.3)
+    n_pairs, n_rej = op.coarse_stats()
+    U1, _, it1, r1 = op.mobility_solve(F, tol=1e-10, max_iter=500, check=False)
+    fallbacks = op.info["coarse_fallbacks"]
+    err = float((U1 - U0).abs().max() / U0.abs().max())
+    print(f"misleading coarse level on {n_pairs} pairs ({n_rej} dropped): {it1} iterations "
+          f"(block-diagonal {it0}), residual {r1:.1e}, fallbacks {fallbacks}, U rel diff {err:.1e}")
+    assert n_pairs > 0 and n_rej < n_pairs
+    assert fallbacks >= 1
+    assert r1 <= 1e-10 and err < 1e-8
+    assert it1 <= it0 + 25
+    op.coarse_enable(None, 1.0)
+    op.close()
+    bad.close()
+
+
+def test_coarse_preconditioner_matches_oracle(torch, fb):
+    """fbim_precondition with the coarse level on (FP64 handle) against the oracle's
+    composition: pair features, the bf16-faithful network, C = T sym(y s) T^T, the coarse
+    velocities U = -(N~ a + sum C a_pair) and the tractions from that U."""
+    w = _suspension()
+    g_c = 1.3
+    xi = math.sqrt(math.log(100.0 / 1e-10)) / 0.5
+    op = fb.FBIM(w.ref_nodes, w.Q, w.L, tol=1e-10, r_c=0.5, precision="fp64")
+    xi = op.info["xi"]
+    theta = _theta(9)
+    shift = np.array([0.0, 0.0, 1.2, 0.0, 0.0, 0.3], dtype=np.float32)
+    scale = np.array([1.0, 1.0, 0.5, 1.0, 1.0, 0.3], dtype=np.float32)
+    out = np.full(36, 2e-3, dtype=np.float32)   # corrections small enough to keep every pair
+    m = fb.MLP(max_batch=64)
+    m.set_params(theta)
+    m.set_normalization(shift, scale, out)
+    op.coarse_enable(m, g_c)
+    n_pairs, n_rej = op.coarse_stats()
+    rng = np.random.default_rng(21)
+    r_mu = rng.standard_normal((w.n, 2))
+    r_U = rng.standard_normal((w.n_b, 3))
+    r = torch.tensor(np.concatenate([r_mu.reshape(-1), r_U.reshape(-1)]), device="cuda")
+    got = op.precondition(r).cpu().numpy()
+    pairs, feats = ocoarse.pair_features(w.Q, w.ref_nodes, w.L, g_c)
+    xn = ((feats - shift.astype(np.float64)) / scale.astype(np.float64)).astype(np.float32).astype(np.float64)
+    y, _ = omlp.forward(theta.astype(np.float64), xn, rounding=True)
+    C_lab = []
+    for p, (a, _) in enumerate(pairs):
+        Cf = (y[p] * out.astype(np.float64)).reshape(6, 6)
+        C_lab.append(ocoarse.to_lab(0.5 * (Cf + Cf.T), w.Q[a, 2]))
+    mu_or, U_or = ocoarse.coarse_preconditioner(r_mu, r_U, w.Q, w.ref_nodes, w.L, xi, pairs, np.array(C_lab))
+    mu = got[:2 * w.n].reshape(-1, 2)
+    U = got[2 * w.n:].reshape(-1, 3)
+    eU = float(np.max(np.abs(U - U_or)) / np.max(np.abs(U_or)))
+    emu = float(np.max(np.abs(mu - mu_or)) / np.max(np.abs(mu_or)))
+    # the pairs' share of U, so that the comparison is not the block solve's alone
+    _, U_bd = ocoarse.coarse_preconditioner(r_mu, r_U, w.Q, w.ref_nodes, w.L, xi, pairs[:0], np.zeros((0, 6, 6)))
+    share = float(np.max(np.abs(U_or - U_bd)) / np.max(np.abs(U_or)))
+    print(f"coarse preconditioner: {n_pairs} pairs ({n_rej} dropped), pair share of U {share:.1e}; "
+          f"U rel err {eU:.2e}, mu rel err {emu:.2e}")
+    assert n_pairs == len(pairs) and n_rej == 0
+    assert share > 1e-3
+    assert eU < 1e-6 and emu < 1e-6
+    op.coarse_enable(None, 1.0)
+    op.close()
+    m.close()
