@@ -17,9 +17,11 @@ with FP64 refinement; the plain form runs everything in FP64.  L2 is flushed
 The matvec alone (node-matvecs/s) and its per-stage times are measured too; the
 roofline object refers to the pair SpMV of the FP32 matvec (the step's top kernel).
 
-Two further measurements ride along (``--legs``): ``batched`` solves 64
+Two further measurements ride along (``--legs``): ``batched`` runs 64
 independent suspensions (16-512 bodies, 96 nodes each, area fractions
-0.1-0.35) with 10 right-hand sides each through the graph-captured batch, and
+0.1-0.35) through the graph-captured batch: 8 batched Brownian slips per
+suspension, solved with forces, and the RFD +- pair (handles moved to
+Q +- delta/2 W~) in the same batched solve; and
 ``learned`` times the mobility solve of a dense 4096-body suspension (area
 fraction 0.40) with and without the learned coarse level.
 
@@ -50,8 +52,9 @@ SOLVE_TOL = 1e-6
 DT, KT = 1e-3, 1.0
 SOLVES_PER_STEP = 3
 BATCH_WORKLOAD = "batch64_starfish_np96"
-BATCH_RHS = 10          # per suspension: 8 random slips + the RFD pair
+BATCH_SLIPS = 8         # per suspension: 8 Brownian slips (with forces), plus the RFD +- pair
 BATCH_RC = 0.504
+BATCH_DELTA = 1e-3      # RFD displacement delta of the batched leg
 # GMRES iterations per solve of the chosen form on this workload (measured); the
 # CPU baseline prices a solve as this many oracle matvecs plus one residual check
 ITERS_PER_SOLVE_REF = 24
@@ -254,51 +257,99 @@ def timed(torch, stream, flush, fn, n):
 
 
 def batched_leg(torch, fb, fbim_synth, stream, flush, reps):
-    """Independent suspensions with several right-hand sides through the graph-captured batch."""
+    """Independent suspensions through the graph-captured batch: per suspension BATCH_SLIPS
+    Brownian slips (batched Lanczos near field + far-field noise) solved with forces, and
+    the RFD +- pair (force W~ at Q +- delta/2 W~) in the same batched solve."""
     ws = fbim_synth.batch(BATCH_WORKLOAD)
-    R = BATCH_RHS
-    ops = [fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=BATCH_RC, precision="fp32") for w in ws]
+    R = BATCH_SLIPS
+    mk = lambda w: fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=BATCH_RC, precision="fp32")
+    q_ops = [mk(w) for w in ws]
+    pm_ops = [mk(w) for w in ws for _ in (0, 1)]            # Q + delta/2 W~, Q - delta/2 W~
+    slip_batch = fb.Batch(q_ops, [R] * len(ws))
+    batch = fb.Batch(q_ops + pm_ops, [R] * len(ws) + [1] * len(pm_ops))
+    n_sys = len(batch.systems)
+    # stacked forces: R random force sets per suspension, then W~ of each +- system
     g = np.random.default_rng(5)
-    # per suspension: random forces, R - 2 random slips, and the two unit-scale RFD solves (force only)
-    F, S = [], []
+    f_q = [g.standard_normal(3 * w.n_b * R) for w in ws]
+    n_fq = sum(x.size for x in f_q)
+    F = torch.zeros(n_fq + sum(6 * w.n_b for w in ws), dtype=torch.float64, device="cuda")
+    F[:n_fq] = torch.tensor(np.concatenate(f_q), device="cuda")
+    wt_off, o = [], n_fq
     for w in ws:
-        for r in range(R):
-            F.append(torch.tensor(g.standard_normal((w.n_b, 3)), device="cuda"))
-            S.append(torch.tensor(g.standard_normal((w.n, 2)) if r < R - 2 else np.zeros((w.n, 2)), device="cuda"))
-    batch = fb.Batch(ops, [R] * len(ops))
-    U, it, res = batch.solve(F, S, tol=SOLVE_TOL, max_iter=400)     # warm-up: captures the graphs
-    k0 = batch.info()["launches"]
-    ms = timed(torch, stream, flush, lambda i: batch.solve(F, S, tol=SOLVE_TOL, max_iter=400), reps)
-    info = batch.info()
-    n_sys = len(it)
-    # sequential single solves of the same systems on a sample, for comparison
+        wt_off.append(o)
+        o += 6 * w.n_b
+    n_sq = sum(2 * w.n * R for w in ws)
+    S = torch.zeros(n_sq + sum(4 * w.n for w in ws), dtype=torch.float64, device="cuda")
+    Qd = [torch.tensor(w.Q, device="cuda") for w in ws]
+    ms_slip, ms_solve = [], []
+    res = {}
+
+    def step(i):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        # W~ (Philox stream 2) straight into the +- systems' force blocks; move the +- handles
+        for k, w in enumerate(ws):
+            n3 = 3 * w.n_b
+            a = F[wt_off[k]:wt_off[k] + n3]
+            for o in (0, n3):     # the same draw for the + and the - system
+                q_ops[k].philox_normals(n3, seed=900 + k, stream=2, counter=i, out=F[wt_off[k] + o:wt_off[k] + o + n3])
+            pm_ops[2 * k].update_config_displaced(Qd[k], 0.5 * BATCH_DELTA, a)
+            pm_ops[2 * k + 1].update_config_displaced(Qd[k], -0.5 * BATCH_DELTA, a)
+        _, res["lanczos"] = slip_batch.slip(1000 + n_sys * i, counter=3 * i, kT=KT, dt=DT, tol=SOLVE_TOL,
+                                            max_iter=200, out=S[:n_sq])
+        ev[1].record(stream)
+        _, res["it"], res["res"] = batch.solve(F, S, tol=SOLVE_TOL, max_iter=400)
+        ev[2].record(stream)
+        ev[2].synchronize()
+        ms_slip.append(ev[0].elapsed_time(ev[1]))
+        ms_solve.append(ev[1].elapsed_time(ev[2]))
+
+    step(10_000)                                  # warm-up: captures the graphs
+    ms_slip.clear()
+    ms_solve.clear()
+    k0 = batch.info()["launches"] + slip_batch.info()["launches"]
+    ms = timed(torch, stream, flush, step, reps)
+    info, sinfo = batch.info(), slip_batch.info()
+    it, rs = res["it"], res["res"]
+    n_slip = len(slip_batch.systems)
+    n_q = n_slip
+    # sequential single solves of a sample of the same systems, for comparison
     n_seq = min(n_sys, 40)
-    idx = np.linspace(0, n_sys - 1, n_seq).astype(int)
-    # one untimed single solve per sampled suspension first (solver workspace, captured
-    # Arnoldi step), as the batch's warm-up solve is untimed
-    for k in sorted(set(int(i) // R for i in idx)):
-        ops[k].mobility_solve(F[k * R], S[k * R], tol=SOLVE_TOL, max_iter=400)
+    idx = np.linspace(0, n_q - 1, n_seq).astype(int)
+    Fl = [F[:n_fq].split([3 * w.n_b * R for w in ws])[k].view(R, -1, 3) for k, w in enumerate(ws)]
+    Sl = [S[:n_sq].split([2 * w.n * R for w in ws])[k].view(R, -1, 2) for k, w in enumerate(ws)]
+    for k in sorted(set(int(j) // R for j in idx)):
+        q_ops[k].mobility_solve(Fl[k][0], Sl[k][0], tol=SOLVE_TOL, max_iter=400)
     torch.cuda.synchronize()
     t0 = time.time()
     seq_it = []
-    for i in idx:
-        k = i // R
-        _, _, its, _ = ops[k].mobility_solve(F[i], S[i], tol=SOLVE_TOL, max_iter=400)
+    for j in idx:
+        k, r = int(j) // R, int(j) % R
+        _, _, its, _ = q_ops[k].mobility_solve(Fl[k][r], Sl[k][r], tol=SOLVE_TOL, max_iter=400)
         seq_it.append(its)
     torch.cuda.synchronize()
     seq_rate = n_seq / (time.time() - t0)
-    out = {"workload": BATCH_WORKLOAD, "suspensions": len(ws), "rhs_per_suspension": R,
-           "systems": n_sys, "nodes": int(sum(w.n for w in ws)),
-           "node_rhs": int(sum(w.n for w in ws) * R), "value": n_sys / (float(np.mean(ms)) * 1e-3),
-           "unit": "mobility solves/s", "ms_per_batch_solve": float(np.mean(ms)), "reps": reps,
+    t_step = float(np.mean(ms)) * 1e-3
+    out = {"workload": BATCH_WORKLOAD, "suspensions": len(ws), "slips_per_suspension": R,
+           "rfd_pair_per_suspension": 2, "systems": n_sys, "nodes": int(sum(w.n for w in ws)),
+           "node_rhs": int(sum(w.n for w in ws) * (R + 2)),
+           "value": n_sys / t_step, "unit": "mobility solves/s (slips and RFD moves included)",
+           "ms_per_batch_step": float(np.mean(ms)), "ms_batch_slip": float(np.mean(ms_slip)),
+           "ms_batch_solve": float(np.mean(ms_solve)),
+           "slips_per_s": n_slip / (float(np.mean(ms_slip)) * 1e-3),
+           "solves_per_s_solve_only": n_sys / (float(np.mean(ms_solve)) * 1e-3), "reps": reps,
+           "lanczos_iters_mean": float(np.mean(res["lanczos"])), "lanczos_iters_max": int(np.max(res["lanczos"])),
            "gmres_iters_mean": float(np.mean(it)), "gmres_iters_max": int(np.max(it)),
-           "worst_residual": float(np.max(res)), "graph_kernels": info["graph_kernels"],
-           "kernels_per_batch_solve": (info["launches"] - k0) / max(reps, 1),
-           "graph_launches": info["graph_launches"], "branches": info["branches"],
+           "gmres_iters_mean_rfd_pair": float(np.mean(it[n_q:])),
+           "worst_residual": float(np.max(rs)), "graph_kernels": info["graph_kernels"],
+           "slip_graph_kernels": sinfo["graph_kernels"],
+           "kernels_per_batch_step": (info["launches"] + sinfo["launches"] - k0) / max(reps, 1),
+           "graph_launches": info["graph_launches"] + sinfo["graph_launches"], "branches": info["branches"],
            "sequential_single_solves_per_s": seq_rate, "sequential_iters_mean": float(np.mean(seq_it)),
-           "precision": "FP32 operators, FP64 residuals and Krylov vectors"}
+           "precision": "FP32 operators, FP64 residuals, Krylov and Lanczos vectors"}
+    slip_batch.close()
     batch.close()
-    for o in ops:
+    for o in q_ops + pm_ops:
         o.close()
     return out
 

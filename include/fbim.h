@@ -160,6 +160,11 @@ fbim_status fbim_setup(fbim_handle* out, int n_b, int n_p, const double* ref_nod
  * coordinates) or FBIM_ERR_OVERLAP (two nodes coincide). */
 fbim_status fbim_update_config(fbim_handle h, const double* Q_dev);
 
+/* Move the bodies to Q + a W (the displaced configurations Q +- delta/2 W~ of the random
+ * finite difference, Sec. 4.4, Eq. EM-RFD): Q_dev, W_dev double [n_b][3] (device), the
+ * sum formed on the device.  Otherwise as fbim_update_config. */
+fbim_status fbim_update_config_displaced(fbim_handle h, const double* Q_dev, double a, const double* W_dev);
+
 /* v = M mu with M = M(t) + M(a)_sym + M(w) (Sec. 3.2).  mu_dev, v_dev: double [N][2]. */
 fbim_status fbim_apply_stokeslet(fbim_handle h, const double* mu_dev, double* v_dev);
 
@@ -287,8 +292,9 @@ typedef struct {
     long long n_unknowns;            /* length of the stacked Krylov vectors                    */
     int       restart;               /* GMRES restart of the batch (smallest of the handles')   */
     int       branches;              /* concurrent branches of the captured graphs              */
-    long long graph_kernels[4];      /* this library's kernels in each graph: precondition +
-                                        saddle FP32, the same FP64, saddle FP32, saddle FP64
+    long long graph_kernels[7];      /* this library's kernels in each graph: precondition +
+                                        saddle FP32, the same FP64, saddle FP32, saddle FP64,
+                                        the slip's G M(r) G^T, G^+ and G^+ G (handles' precision)
                                         (0 until the graph is first captured)                   */
     long long launches;              /* this library's kernels run by the batch so far,
                                         graph nodes included (cuFFT, cuBLAS not counted)        */
@@ -319,6 +325,24 @@ fbim_status fbim_batch_create(fbim_batch* out, int n_handles, const fbim_handle*
  * misses tol within max_iter. */
 fbim_status fbim_batch_solve(fbim_batch b, const double* F_dev, const double* slip_dev, double tol, int max_iter,
                              double* U_dev, int* iters, double* rel_residual);
+
+/* Brownian slip of every system of the batch (Sec. 3.3, Eq. sqrtM-split, with the
+ * Sec. 3.4 block-diagonal G): system i gets the slip fbim_brownian_slip gives its
+ * handle with seed seeds[i] and this counter (Philox normals), up to rounding: the
+ * same Lanczos iteration and stopping test per system, run for all systems at once
+ * (one graph of G M(r) G^T per step, segmented FP64 Gram-Schmidt, each system frozen
+ * once it stops), then a graph of G^+ and each system's far-field noise.
+ *   seeds:    host array [n_systems] (distinct seeds give independent slips).
+ *   counter:  Philox call counter of every system (fbim_rfd_step uses 3 step).
+ *   kT, dt, tol, max_iter: as in fbim_brownian_slip (max_iter <= 1000).
+ *   slip_dev: double output [N][2] blocks stacked in system order (the layout of
+ *             fbim_batch_solve's slip_dev).
+ *   lanczos_iters: NULL or host array [n_systems].
+ * Keeps a Lanczos basis of (max_iter + 2) stacked vectors (grown on demand, freed
+ * with the batch).  Synchronises the stream.  A system that has not met tol after
+ * max_iter steps gets its last iterate, as in fbim_brownian_slip. */
+fbim_status fbim_batch_slip(fbim_batch b, const uint64_t* seeds, uint64_t counter, double kT, double dt, double tol,
+                            int max_iter, double* slip_dev, int* lanczos_iters);
 
 fbim_status fbim_batch_get_info(fbim_batch b, fbim_batch_info* info);
 
@@ -455,6 +479,13 @@ double fbim_host_expint_e1(double z);
 /* Nodes v_k and weights w_k of the library's log-singular end correction (Sec. 3.1) and
  * its window a; v and w must hold order - 1 doubles.  Host only. */
 fbim_status fbim_host_alpert_rule(int order, double* v, double* w, int* a);
+
+/* Coefficients c = wnorm f(T) e_1, f = sqrt with negative Ritz values clipped to zero, of
+ * the Lanczos approximation V c to A^1/2 w (Sec. 3.3) from the k x k symmetric tridiagonal
+ * T (alpha[k] diagonal, beta[k - 1] off-diagonal): the host routine of fbim_brownian_slip
+ * and fbim_batch_slip, exported so that it can be tested without a GPU.  out: double [k].
+ * FBIM_ERR_INVALID_ARG for k < 1 or NULL pointers.  Host only. */
+fbim_status fbim_host_lanczos_sqrt(const double* alpha, const double* beta, int k, double wnorm, double* out);
 
 #ifdef __cplusplus
 }

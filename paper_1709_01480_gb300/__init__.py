@@ -37,7 +37,7 @@ EXPORTS = [
     "fbim_set_timing", "fbim_stage_times", "fbim_mobility_solve", "fbim_brownian_slip",
     "fbim_philox_normals", "fbim_apply_real_noalloc", "fbim_rfd_step",
     "fbim_batch_create", "fbim_batch_solve", "fbim_batch_get_info", "fbim_batch_destroy",
-    "fbim_batch_last_error",
+    "fbim_batch_last_error", "fbim_batch_slip", "fbim_update_config_displaced", "fbim_host_lanczos_sqrt",
     "fbim_mlp_param_count", "fbim_mlp_create", "fbim_mlp_destroy", "fbim_mlp_last_error",
     "fbim_mlp_set_params", "fbim_mlp_get_params", "fbim_mlp_set_normalization", "fbim_mlp_forward",
     "fbim_mlp_gradient", "fbim_mlp_adam_step", "fbim_mlp_launches", "fbim_coarse_pairs",
@@ -85,7 +85,7 @@ class Info(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_handles", ctypes.c_int), ("n_systems", ctypes.c_int), ("n_unknowns", ctypes.c_longlong),
-                ("restart", ctypes.c_int), ("branches", ctypes.c_int), ("graph_kernels", ctypes.c_longlong * 4),
+                ("restart", ctypes.c_int), ("branches", ctypes.c_int), ("graph_kernels", ctypes.c_longlong * 7),
                 ("launches", ctypes.c_longlong), ("graph_launches", ctypes.c_longlong)]
 
     def as_dict(self):
@@ -106,6 +106,7 @@ _lib.fbim_default_params.argtypes = [ctypes.POINTER(Params)]
 _lib.fbim_choose_ewald.argtypes = [_D, _D, _D, _D, _IP, _DP, _DP, _IP, _IP, _DP]
 _lib.fbim_setup.argtypes = [ctypes.POINTER(_P), _I, _I, _DP, _DP, _D, _D, _D, _D, ctypes.POINTER(Params)]
 _lib.fbim_update_config.argtypes = [_P, _P]
+_lib.fbim_update_config_displaced.argtypes = [_P, _P, _D, _P]
 _lib.fbim_apply_stokeslet.argtypes = [_P, _P, _P]
 _lib.fbim_apply_real.argtypes = [_P, _P, _P]
 _lib.fbim_apply_wave.argtypes = [_P, _P, _P]
@@ -120,6 +121,7 @@ _lib.fbim_last_error.restype = ctypes.c_char_p
 _lib.fbim_host_expint_e1.argtypes = [_D]
 _lib.fbim_host_expint_e1.restype = _D
 _lib.fbim_host_alpert_rule.argtypes = [_I, _DP, _DP, _IP]
+_lib.fbim_host_lanczos_sqrt.argtypes = [_DP, _DP, _I, _D, _DP]
 _lib.fbim_set_timing.argtypes = [_P, _I]
 _lib.fbim_mobility_solve.argtypes = [_P, _P, _P, _D, _I, _P, _P, _IP, _DP]
 _lib.fbim_brownian_slip.argtypes = [_P, ctypes.c_uint64, ctypes.c_uint64, _D, _D, _P, _P, _D, _I, _P, _IP]
@@ -128,6 +130,7 @@ _lib.fbim_stage_times.argtypes = [_P, _DP, ctypes.POINTER(ctypes.c_longlong), _I
 _lib.fbim_batch_create.argtypes = [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _IP]
 _lib.fbim_batch_solve.argtypes = [_P, _P, _P, _D, _I, _P, _IP, _DP]
 _lib.fbim_batch_get_info.argtypes = [_P, ctypes.POINTER(BatchInfo)]
+_lib.fbim_batch_slip.argtypes = [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_uint64, _D, _D, _D, _I, _P, _IP]
 _lib.fbim_batch_destroy.argtypes = [_P]
 _lib.fbim_batch_destroy.restype = None
 _lib.fbim_batch_last_error.argtypes = [_P]
@@ -188,6 +191,18 @@ def host_alpert_rule(order: int = 4):
     a = ctypes.c_int(0)
     _check(_lib.fbim_host_alpert_rule(order, _dptr(v), _dptr(w), ctypes.byref(a)))
     return v, w, a.value
+
+
+def host_lanczos_sqrt(alpha, beta, wnorm=1.0):
+    """wnorm sqrt(T) e_1 for the symmetric tridiagonal T = tridiag(beta, alpha, beta) (host routine)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    if b.size + 1 != a.size or a.size < 1:
+        raise ValueError("beta needs len(alpha) - 1 entries")
+    out = np.zeros(a.size)
+    bb = b if b.size else np.zeros(1)
+    _check(_lib.fbim_host_lanczos_sqrt(_dptr(a), _dptr(bb), a.size, float(wnorm), _dptr(out)))
+    return out
 
 
 def choose_ewald(L, r_c, tol, xi=0.0):
@@ -337,9 +352,12 @@ class FBIM:
                                  int(max_iter), opt(NF), 1 if have_prev else 0, _ptr(Q), ctypes.byref(it)), self._h)
         return it.value
 
-    def philox_normals(self, n, seed=0, stream=0, counter=0):
+    def philox_normals(self, n, seed=0, stream=0, counter=0, out=None):
         import torch
-        out = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", self.device))
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", self.device))
+        elif out.numel() < n or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out: contiguous float64 with n entries")
         _check(_lib.fbim_philox_normals(self._h, int(seed), int(stream), int(counter), int(n), _ptr(out)), self._h)
         return out
 
@@ -394,6 +412,10 @@ class FBIM:
 
     def update_config(self, Q_dev):
         _check(_lib.fbim_update_config(self._h, _ptr(Q_dev)), self._h)
+
+    def update_config_displaced(self, Q_dev, a, W_dev):
+        """Move the bodies to Q + a W (device [n_b, 3] tensors)."""
+        _check(_lib.fbim_update_config_displaced(self._h, _ptr(Q_dev), float(a), _ptr(W_dev)), self._h)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -457,6 +479,28 @@ class Batch:
             self._check(st)
         Us = list(torch.split(U, sizes))
         return [u.view(-1, 3) for u in Us], list(it), list(res)
+
+    def slip(self, seeds, counter=0, kT=1.0, dt=1.0, tol=1e-6, max_iter=200, out=None):
+        """Brownian slip of every system: system i with Philox seed seeds[i] (an int gives
+        seeds + i).  Returns the [N, 2] slips as views of one stacked tensor (``out`` if
+        given, a flat float64 tensor of the systems' 2N entries) and the Lanczos steps."""
+        import torch
+        n_sys = len(self.systems)
+        if isinstance(seeds, int):
+            seeds = [seeds + i for i in range(n_sys)]
+        if len(seeds) != n_sys:
+            raise ValueError("one seed per system")
+        sizes = [2 * self.ops[k].n for k, _ in self.systems]
+        if out is None:
+            out = torch.empty(sum(sizes), dtype=torch.float64, device=torch.device("cuda", self.ops[0].device))
+        elif out.numel() < sum(sizes) or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out: contiguous float64 with the systems' 2N entries")
+        sd = (ctypes.c_uint64 * n_sys)(*[int(x) for x in seeds])
+        it = (ctypes.c_int * n_sys)()
+        self._check(_lib.fbim_batch_slip(self._b, sd, int(counter), float(kT), float(dt), float(tol),
+                                         int(max_iter), _ptr(out), it))
+        flat = out.reshape(-1)[:sum(sizes)]
+        return [s.view(-1, 2) for s in torch.split(flat, sizes)], list(it)
 
     def close(self):
         if getattr(self, "_b", None):

@@ -386,6 +386,28 @@ extern "C" fbim_status fbim_update_config(fbim_handle h, const double* Q_dev) {
     });
 }
 
+namespace {
+__global__ void k_displaced(int n, const double* __restrict__ Q, double a, const double* __restrict__ W,
+                            double* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = Q[i] + a * W[i];
+}
+}  // namespace
+
+extern "C" fbim_status fbim_update_config_displaced(fbim_handle h, const double* Q_dev, double a, const double* W_dev) {
+    if (!h || !Q_dev || !W_dev || !std::isfinite(a)) return FBIM_ERR_INVALID_ARG;
+    return guarded(h, [&]() -> fbim_status {
+        FBIM_CUDA_TRY(h, cudaSetDevice(h->device));
+        const int n = 3 * h->n_b;
+        // Q_dev or W_dev may be the handle's own coordinates: the sum is elementwise
+        k_displaced<<<(n + 255) / 256, 256, 0, h->stream>>>(n, Q_dev, a, W_dev, h->Q);
+        h->launches += 1;
+        FBIM_CUDA_TRY(h, cudaGetLastError());
+        FBIM_TRY(fbim::update_positions(h, h->Q));
+        return check_flags(h);
+    });
+}
+
 static fbim_status apply_which(fbim_handle h, const double* mu, double* v, int which, bool fp64 = false) {
     if (!h || !mu || !v) return FBIM_ERR_INVALID_ARG;
     if ((((uintptr_t)mu) | ((uintptr_t)v)) & 15) {

@@ -18,6 +18,15 @@
 // FBIM_FP32 handles refine: FP64 residuals from a graph of FP64 saddle
 // operators and FP32-operator corrections to 1e-4 (one restart cycle each),
 // which is the mixed-precision scheme of the single-system solver.
+//
+// Batched Brownian slip (Sec. 3.3, Eq. sqrtM-split; Sec. 3.4, Eq. Gprecond-decomp):
+// the near field of every system by one Lanczos iteration over the stacked vector
+// (a graph of G M(r) G^T per step, segmented classical Gram-Schmidt twice in FP64,
+// segment norms and normalisation on the device, the next step queued before the
+// host reads the last one's alpha and beta), each system stopping on its own test;
+// then a graph of G^+ and each system's far-field noise on the branch streams.  The
+// iteration starts, as the single slip's does, from G^+ G W(r), W(r)'s projection onto
+// the range of G.
 #include <cublas_v2.h>
 #include <cufft.h>
 
@@ -26,8 +35,12 @@
 #include <new>
 #include <vector>
 
+#include "ewald_types.cuh"
 #include "fbim_internal.h"
+#include "lanczos_host.h"
 #include "solver.cuh"
+
+constexpr int kGraphs = 7;
 
 struct fbim_batch_s {
     int n_h = 0, n_tot = 0;                  // handles, systems
@@ -51,10 +64,23 @@ struct fbim_batch_s {
     long long* d_off = nullptr;              // device copy of off
     long long *d_f_off = nullptr, *d_s_off = nullptr;
     int* d_two_n = nullptr;                  // [n_tot] 2N of each system
-    // graphs: [0] precondition + saddle FP32, [1] same FP64, [2] saddle FP32, [3] saddle FP64
-    cudaGraphExec_t g[4] = {nullptr, nullptr, nullptr, nullptr};
-    long long g_kernels[4] = {0, 0, 0, 0};   // this library's kernels in each graph
-    std::vector<unsigned long long> g_version[4];
+    // graphs: [0] precondition + saddle FP32, [1] same FP64, [2] saddle FP32, [3] saddle FP64,
+    // [4] G M(r) G^T, [5] G^+ and [6] G^+ G in the handles' precision (the Brownian slip)
+    cudaGraphExec_t g[kGraphs] = {};
+    long long g_kernels[kGraphs] = {};       // this library's kernels in each graph
+    std::vector<unsigned long long> g_version[kGraphs];
+    // batched Lanczos workspace (grown on demand)
+    int lz_cap = 0;                          // basis vectors held
+    double* lz_V = nullptr;                  // [lz_cap][ld] basis V_0, V_1, ...
+    double* lz_dots = nullptr;               // [3][n_tot][lz_cap] the two Gram-Schmidt passes, the norm
+    double* lz_coef = nullptr;               // [n_tot][lz_cap] coefficients of the final combination
+    int* lz_cnt = nullptr;                   // [n_tot] basis vectors each combination uses
+    int* lz_active = nullptr;                // [n_tot] 1 while the system's iteration runs
+    double* lz_rec = nullptr;                // mapped host [lz_cap][n_tot][2]: alpha_k, |w_k|^2
+    double* lz_rec_dev = nullptr;            // its device address
+    unsigned long long* d_seeds = nullptr;   // [n_tot]
+    cudaEvent_t lz_ev[2] = {nullptr, nullptr};
+    std::vector<int> lz_active_host;
     long long launches = 0;                  // this library's kernels run by the batch (graphs included)
     long long graph_launches = 0;
     std::string err;
@@ -164,6 +190,79 @@ __global__ void k_batch_u(long long n, const long long* __restrict__ off, int n_
     if (k >= 0 && k < f_off[i + 1] - f_off[i]) U[f_off[i] + k] = x[t];
 }
 
+// Near-field normals W(r) of every system into the stacked vector (zero past 2N):
+// the Philox draws of fbim_brownian_slip with the system's seed (stream 0; FP32
+// transform for FP32 handles).  One thread per pair: segments start even and 2N
+// is even, so a pair never straddles two systems.
+__global__ void k_batch_normals(long long n_pairs, const long long* __restrict__ off, int n_seg,
+                                const int* __restrict__ two_n, const unsigned long long* __restrict__ seeds,
+                                unsigned counter, int f32, double* __restrict__ out) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_pairs) return;
+    const long long t = 2 * p;
+    const int i = seg_of(off, n_seg, t);
+    const long long k = t - off[i];
+    double2 z = make_double2(0.0, 0.0);
+    if (k < two_n[i]) {
+        if (f32) {
+            const float2 zf = fbim::philox_normals_f(seeds[i], 0u, counter, (unsigned long long)(k / 2));
+            z = make_double2(zf.x, zf.y);
+        } else {
+            z = fbim::philox_normals(seeds[i], 0u, counter, (unsigned long long)(k / 2));
+        }
+    }
+    out[t] = z.x;
+    out[t + 1] = z.y;
+}
+
+// V_next = w / |w| per system while it is active (|w|^2 = nrm[i * stride]); exact zeros
+// for a stopped system, so that nothing it leaves behind reaches later steps
+__global__ void k_seg_normalize(long long n_all, const long long* __restrict__ off, int n_seg,
+                                const double* __restrict__ nrm, int stride, const int* __restrict__ active,
+                                const double* __restrict__ w, double* __restrict__ v_next) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_all) return;
+    const int i = seg_of(off, n_seg, t);
+    const double q = nrm[(size_t)i * stride];
+    const bool on = active[i] != 0 && q > 0.0 && isfinite(q);
+    v_next[t] = on ? w[t] * rsqrt(q) : 0.0;
+}
+
+// alpha_k = <v_k, A v_k> (the k-th coefficients of the two Gram-Schmidt passes) and
+// |w_k|^2 of every system into row k of the mapped host record
+__global__ void k_lz_record(int n_seg, int k, int stride, const double* __restrict__ d1,
+                            const double* __restrict__ d2, const double* __restrict__ nrm, double* __restrict__ rec) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_seg) return;
+    rec[2 * i] = d1[(size_t)i * stride + k] + d2[(size_t)i * stride + k];
+    rec[2 * i + 1] = nrm[(size_t)i * stride];
+}
+
+// out = sum_{j < cnt[i]} a[i][j] V_j on system i's segment (terms past a system's own
+// count are never read)
+__global__ void k_seg_combine_cnt(long long n_all, const long long* __restrict__ off, int n_seg,
+                                  const int* __restrict__ cnt, const double* __restrict__ a, int stride,
+                                  const double* __restrict__ V, long long ld, double* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_all) return;
+    const int i = seg_of(off, n_seg, t);
+    double v = 0.0;
+    for (int j = 0; j < cnt[i]; ++j) v += a[(size_t)i * stride + j] * V[(size_t)j * ld + t];
+    out[t] = v;
+}
+
+// slip = sc (near + far) into the caller's stacked [2N] blocks
+__global__ void k_batch_slip_out(long long n_all, const long long* __restrict__ off, int n_seg,
+                                 const int* __restrict__ two_n, const long long* __restrict__ s_off, double sc,
+                                 const double* __restrict__ near, const double* __restrict__ far,
+                                 double* __restrict__ slip) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_all) return;
+    const int i = seg_of(off, n_seg, t);
+    const long long k = t - off[i];
+    if (k < two_n[i]) slip[s_off[i] + k] = sc * (near[t] + far[t]);
+}
+
 fbim_status fail(fbim_batch B, const std::string& m, fbim_status s) {
     B->err = m;
     return s;
@@ -185,13 +284,22 @@ fbim_status fail(fbim_batch B, const std::string& m, fbim_status s) {
 inline unsigned blocks(long long n, int tb) { return (unsigned)((n + tb - 1) / tb); }
 
 // The operator a graph applies to one system: kind 0/1 = precondition then saddle
-// (FP32 / FP64 operator), kind 2/3 = saddle only (FP32 / FP64).
+// (FP32 / FP64 operator), kind 2/3 = saddle only (FP32 / FP64), kind 4 = G M(r) G^T
+// and kind 6 = G^+ G on the first 2N entries (the rest of the segment set to zero),
+// kind 5 = G^+.
 fbim_status system_ops(fbim_batch B, int i, int kind) {
     fbim_handle h = B->hs[B->h_of[i]];
     const bool fp32 = (kind & 1) == 0;
     const double* in = B->vin + B->off[i];
     double* z = B->zout + B->off[i];
     double* y = B->wout + B->off[i];
+    if (kind == 4 || kind == 6) {
+        BSTATUS(kind == 4 ? fbim::lanczos_operator(h, in, y) : fbim::g_project(h, in, y));
+        const long long tail = B->off[i + 1] - B->off[i] - 2LL * h->N;
+        BTRY(cudaMemsetAsync(y + 2LL * h->N, 0, sizeof(double) * tail, h->stream));
+        return FBIM_OK;
+    }
+    if (kind == 5) return fbim::gplus_apply(h, in, y);
     if (kind < 2) {
         BSTATUS(fbim::solver_precondition(h, in, z, fp32));
         return fbim::solver_saddle(h, z, y, fp32);
@@ -551,6 +659,188 @@ fbim_status batch_solve(fbim_batch B, const double* F, const double* slip, doubl
     return FBIM_OK;
 }
 
+// Batched Lanczos workspace for up to cap basis vectors (grown on demand).
+fbim_status ensure_lanczos(fbim_batch B, int cap) {
+    if (B->lz_cap >= cap) return FBIM_OK;
+    cudaFree(B->lz_V);
+    cudaFree(B->lz_dots);
+    cudaFree(B->lz_coef);
+    if (B->lz_rec) cudaFreeHost(B->lz_rec);
+    B->lz_V = B->lz_dots = B->lz_coef = B->lz_rec = B->lz_rec_dev = nullptr;
+    B->lz_cap = 0;
+    const size_t n = B->n_tot;
+    BTRY(cudaMalloc(&B->lz_V, sizeof(double) * (size_t)B->ld * cap));
+    BTRY(cudaMalloc(&B->lz_dots, sizeof(double) * 3 * n * cap));
+    BTRY(cudaMalloc(&B->lz_coef, sizeof(double) * n * cap));
+    BTRY(cudaHostAlloc(&B->lz_rec, sizeof(double) * 2 * n * cap, cudaHostAllocMapped));
+    BTRY(cudaHostGetDevicePointer(&B->lz_rec_dev, B->lz_rec, 0));
+    if (!B->lz_cnt) {
+        BTRY(cudaMalloc(&B->lz_cnt, sizeof(int) * n));
+        BTRY(cudaMalloc(&B->lz_active, sizeof(int) * n));
+        BTRY(cudaMalloc(&B->d_seeds, sizeof(unsigned long long) * n));
+        BTRY(cudaEventCreateWithFlags(&B->lz_ev[0], cudaEventDisableTiming));
+        BTRY(cudaEventCreateWithFlags(&B->lz_ev[1], cudaEventDisableTiming));
+    }
+    B->lz_cap = cap;
+    return FBIM_OK;
+}
+
+template <typename T>
+fbim_status far_fields(fbim_batch B, const unsigned long long* seeds, unsigned counter, double* far) {
+    // each system's (M(w))^1/2 W(w) on its handle's branch; the systems of one handle
+    // share its wave-space buffers and run in turn
+    const int nb = (int)B->side.size();
+    BTRY(cudaEventRecord(B->fork_ev, B->stream));
+    for (int b = 0; b < nb; ++b) BTRY(cudaStreamWaitEvent(B->side[b], B->fork_ev, 0));
+    fbim_status st = FBIM_OK;
+    for (int i = 0; i < B->n_tot && st == FBIM_OK; ++i) {
+        const int k = B->h_of[i];
+        fbim_handle h = B->hs[k];
+        fbim::bind_stream(h, B->side[k % nb]);
+        const long long l0 = h->launches;
+        st = fbim::apply_noise<T>(h, nullptr, seeds[i], counter, far + B->off[i]);
+        B->launches += h->launches - l0;
+        if (st != FBIM_OK) B->err = std::string("batch far field: ") + h->err;
+    }
+    for (fbim_handle h : B->hs) fbim::bind_stream(h, B->stream);
+    for (int b = 0; b < nb; ++b) {
+        BTRY(cudaEventRecord(B->side_ev[b], B->side[b]));
+        BTRY(cudaStreamWaitEvent(B->stream, B->side_ev[b], 0));
+    }
+    return st;
+}
+
+// Brownian slip of every system (see the file comment); system i's slip is that of
+// fbim_brownian_slip on its handle with seed seeds[i] and the same counter.
+fbim_status batch_slip(fbim_batch B, const unsigned long long* seeds, unsigned long long counter, double kT, double dt,
+                       double tol, int max_iter, double* slip, int* iters_out) {
+    const int n = B->n_tot, tb = 256;
+    const long long N = B->n_all, ld = B->ld;
+    cudaStream_t st = B->stream;
+    const bool fp32 = B->hs[0]->precision == FBIM_FP32;
+    const int cap = max_iter + 2;  // V_0 .. V_{max_iter + 1}: a step queued past the last one writes one more
+    const int stride = cap;
+    BSTATUS(ensure_lanczos(B, cap));
+    BSTATUS(capture(B, 4));
+    BSTATUS(capture(B, 5));
+    BSTATUS(capture(B, 6));
+    B->lz_active_host.assign(n, 0);
+    BTRY(cudaMemcpyAsync(B->d_seeds, seeds, sizeof(unsigned long long) * n, cudaMemcpyHostToDevice, st));
+    k_batch_normals<<<blocks(N / 2, tb), tb, 0, st>>>(N / 2, B->d_off, n, B->d_two_n, B->d_seeds,
+                                                      (unsigned)counter, fp32 ? 1 : 0, B->x);
+    B->launches += 1;
+    // start from G^+ G W(r), as the single slip does: the null space of G contributes f(0) = 0
+    BSTATUS(run_graph(B, 6, B->x, nullptr, B->b));
+    std::vector<double> wn2, wn(n), inv(n);
+    BSTATUS(seg_norms2(B, B->b, wn2));
+    for (int i = 0; i < n; ++i) {
+        wn[i] = std::sqrt(wn2[i]);
+        inv[i] = wn[i] > 0 ? 1.0 / wn[i] : 0.0;
+        B->lz_active_host[i] = wn[i] > 0 ? 1 : 0;
+    }
+    BSTATUS(seg_scale(B, inv, B->b, B->lz_V));  // V_0 = W / |W|
+    BTRY(cudaMemcpyAsync(B->lz_active, B->lz_active_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    double* d1 = B->lz_dots;
+    double* d2 = d1 + (size_t)n * stride;
+    double* nr = d2 + (size_t)n * stride;
+    // one step for every system: w = G M(r) G^T v_k, two Gram-Schmidt passes against
+    // V_0..V_k, |w|^2, V_{k+1} = w / |w| while active, alpha_k and |w|^2 to the host record
+    auto enqueue = [&](int k) -> fbim_status {
+        BSTATUS(run_graph(B, 4, B->lz_V + (size_t)k * ld, nullptr, B->w));
+        for (double* dst : {d1, d2}) {
+            k_seg_dots<<<dim3(n, k + 1), 256, 0, st>>>(B->d_off, B->lz_V, ld, B->w, dst, stride);
+            k_seg_update<<<blocks(N, tb), tb, 0, st>>>(N, B->d_off, n, k + 1, B->lz_V, ld, dst, stride, B->w);
+        }
+        k_seg_dots<<<dim3(n, 1), 256, 0, st>>>(B->d_off, B->w, 0, B->w, nr, stride);
+        k_seg_normalize<<<blocks(N, tb), tb, 0, st>>>(N, B->d_off, n, nr, stride, B->lz_active, B->w,
+                                                      B->lz_V + (size_t)(k + 1) * ld);
+        k_lz_record<<<(n + 127) / 128, 128, 0, st>>>(n, k, stride, d1, d2, nr, B->lz_rec_dev + (size_t)2 * n * k);
+        B->launches += 7;
+        BTRY(cudaGetLastError());
+        BTRY(cudaEventRecord(B->lz_ev[k & 1], st));
+        return FBIM_OK;
+    };
+    std::vector<std::vector<double>> alpha(n), beta(n), coef(n);
+    std::vector<double> d_last(n, -1.0), d_prev(n, -1.0);
+    std::vector<int> its(n, 0);
+    int n_active = 0;
+    for (int i = 0; i < n; ++i) n_active += B->lz_active_host[i];
+    if (n_active > 0) BSTATUS(enqueue(0));
+    for (int k = 0; k < max_iter && n_active > 0; ++k) {
+        // queue the next step unless every running system is predicted to stop here
+        bool ahead = false;
+        if (k + 1 < max_iter)
+            for (int i = 0; i < n && !ahead; ++i) {
+                if (!B->lz_active_host[i]) continue;
+                ahead = !(d_last[i] >= 0.0 && d_prev[i] > 0.0) ||
+                        d_last[i] * std::min(d_last[i] / d_prev[i], 1.0) > tol;
+            }
+        if (ahead) BSTATUS(enqueue(k + 1));
+        BTRY(cudaEventSynchronize(B->lz_ev[k & 1]));
+        const double* row = B->lz_rec + (size_t)2 * n * k;
+        bool changed = false;
+        for (int i = 0; i < n; ++i) {
+            if (!B->lz_active_host[i]) continue;
+            const double bn = std::sqrt(std::max(row[2 * i + 1], 0.0));
+            alpha[i].push_back(row[2 * i]);
+            beta[i].push_back(bn);
+            ++its[i];
+            std::vector<double> c = fbim::lanczos_sqrt_coeffs(alpha[i].data(), beta[i].data(), k + 1, wn[i]);
+            double dn = 0, cn = 0;
+            for (int j = 0; j <= k; ++j) {
+                const double prev = j < (int)coef[i].size() ? coef[i][j] : 0.0;
+                dn += (c[j] - prev) * (c[j] - prev);
+                cn += c[j] * c[j];
+            }
+            coef[i].swap(c);
+            if (!std::isfinite(bn) || !std::isfinite(cn))
+                return fail(B, "batched Lanczos iterate is not finite", FBIM_ERR_NONFINITE);
+            d_prev[i] = d_last[i];
+            d_last[i] = cn > 0.0 ? std::sqrt(dn / cn) : 0.0;
+            const bool conv = (k > 0 && std::sqrt(dn) <= tol * std::sqrt(cn)) || bn <= 1e-14 * wn[i];
+            if (conv || k + 1 == max_iter) {
+                B->lz_active_host[i] = 0;
+                --n_active;
+                changed = true;
+            }
+        }
+        if (n_active == 0) break;
+        // stop the finished systems from the next queued step on (ordered after the queued one)
+        if (changed)
+            BTRY(cudaMemcpyAsync(B->lz_active, B->lz_active_host.data(), sizeof(int) * n, cudaMemcpyHostToDevice,
+                                 st));
+        if (!ahead) BSTATUS(enqueue(k + 1));
+    }
+    // near = G^+ V c per system, far = its wave-space noise, slip = sqrt(2 kT / dt) (near + far)
+    std::vector<double> cm((size_t)n * stride, 0.0);
+    std::vector<int> cnt(n);
+    for (int i = 0; i < n; ++i) {
+        cnt[i] = (int)coef[i].size();
+        std::copy(coef[i].begin(), coef[i].end(), cm.begin() + (size_t)i * stride);
+    }
+    BTRY(cudaMemcpyAsync(B->lz_coef, cm.data(), sizeof(double) * cm.size(), cudaMemcpyHostToDevice, st));
+    BTRY(cudaMemcpyAsync(B->lz_cnt, cnt.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    k_seg_combine_cnt<<<blocks(N, tb), tb, 0, st>>>(N, B->d_off, n, B->lz_cnt, B->lz_coef, stride, B->lz_V, ld, B->d);
+    B->launches += 1;
+    BSTATUS(run_graph(B, 5, B->d, nullptr, B->r));
+    if (fp32)
+        BSTATUS(far_fields<float>(B, seeds, (unsigned)counter, B->x));
+    else
+        BSTATUS(far_fields<double>(B, seeds, (unsigned)counter, B->x));
+    k_batch_slip_out<<<blocks(N, tb), tb, 0, st>>>(N, B->d_off, n, B->d_two_n, B->d_s_off, std::sqrt(2.0 * kT / dt),
+                                                   B->r, B->x, slip);
+    B->launches += 1;
+    BTRY(cudaGetLastError());
+    BTRY(cudaStreamSynchronize(st));  // the host vectors above outlive their copies
+    for (fbim_handle h : B->hs) {
+        const fbim_status ts = fbim::tc_check(h);
+        if (ts != FBIM_OK) return fail(B, "batched slip: " + h->err, ts);
+    }
+    if (iters_out)
+        for (int i = 0; i < n; ++i) iters_out[i] = its[i];
+    return FBIM_OK;
+}
+
 }  // namespace
 
 extern "C" void fbim_batch_destroy(fbim_batch B) {
@@ -564,6 +854,13 @@ extern "C" void fbim_batch_destroy(fbim_batch B) {
     cudaFree(B->d_two_n);
     for (cudaGraphExec_t g : B->g)
         if (g) cudaGraphExecDestroy(g);
+    for (double* p : {B->lz_V, B->lz_dots, B->lz_coef}) cudaFree(p);
+    cudaFree(B->lz_cnt);
+    cudaFree(B->lz_active);
+    cudaFree(B->d_seeds);
+    if (B->lz_rec) cudaFreeHost(B->lz_rec);
+    for (cudaEvent_t e : B->lz_ev)
+        if (e) cudaEventDestroy(e);
     for (cudaStream_t s : B->side) cudaStreamDestroy(s);
     for (cudaEvent_t e : B->side_ev) cudaEventDestroy(e);
     if (B->fork_ev) cudaEventDestroy(B->fork_ev);
@@ -711,8 +1008,21 @@ extern "C" fbim_status fbim_batch_get_info(fbim_batch B, fbim_batch_info* info) 
     info->n_unknowns = B->n_all;
     info->restart = B->m;
     info->branches = (int)B->side.size();
-    for (int k = 0; k < 4; ++k) info->graph_kernels[k] = B->g_kernels[k];
+    for (int k = 0; k < kGraphs; ++k) info->graph_kernels[k] = B->g_kernels[k];
     info->launches = B->launches;
     info->graph_launches = B->graph_launches;
     return FBIM_OK;
+}
+
+extern "C" fbim_status fbim_batch_slip(fbim_batch B, const uint64_t* seeds, uint64_t counter, double kT, double dt,
+                                       double tol, int max_iter, double* slip_dev, int* lanczos_iters) {
+    if (!B || !seeds || !slip_dev || !(dt > 0) || !(kT >= 0) || !(tol > 0) || max_iter <= 0 || max_iter > 1000)
+        return FBIM_ERR_INVALID_ARG;
+    try {
+        if (cudaSetDevice(B->device) != cudaSuccess) return FBIM_ERR_CUDA;
+        std::vector<unsigned long long> sd(seeds, seeds + B->n_tot);
+        return batch_slip(B, sd.data(), counter, kT, dt, tol, max_iter, slip_dev, lanczos_iters);
+    } catch (...) {
+        return fail(B, "unexpected host exception in fbim_batch_slip", FBIM_ERR_SETUP);
+    }
 }

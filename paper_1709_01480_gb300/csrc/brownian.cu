@@ -15,13 +15,14 @@
 // Far field: the wave-space noise pipeline (ewald_ops.cu).
 #include <cublas_v2.h>
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
 
 #include "ewald_types.cuh"
 #include "fbim_internal.h"
-
+#include "lanczos_host.h"
 #include "solver.cuh"
 
 namespace fbim {
@@ -109,66 +110,6 @@ fbim_status block_apply(fbim_handle_s* h, const T* Bref, const double* in, doubl
     return FBIM_OK;
 }
 
-// Eigen-decomposition of a small symmetric matrix by cyclic Jacobi rotations
-// (row-major, in place; V gets the eigenvectors as columns).
-void jacobi_eig(std::vector<double>& A, int n, std::vector<double>& V) {
-    V.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
-        if (off < 1e-30) break;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                double apq = A[(size_t)p * n + q];
-                if (std::fabs(apq) < 1e-300) continue;
-                double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-                double theta = (aqq - app) / (2.0 * apq);
-                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < n; ++k) {
-                    double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
-                    A[(size_t)k * n + p] = c * akp - s * akq;
-                    A[(size_t)k * n + q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < n; ++k) {
-                    double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
-                    A[(size_t)p * n + k] = c * apk - s * aqk;
-                    A[(size_t)q * n + k] = s * apk + c * aqk;
-                }
-                for (int k = 0; k < n; ++k) {
-                    double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-                    V[(size_t)k * n + p] = c * vkp - s * vkq;
-                    V[(size_t)k * n + q] = s * vkp + c * vkq;
-                }
-            }
-    }
-}
-
-// coefficients c = |w| sqrt(T) e_1 of the Lanczos approximation (negative Ritz values clipped)
-std::vector<double> lanczos_coeffs(const std::vector<double>& alpha, const std::vector<double>& beta, int k,
-                                   double wnorm) {
-    std::vector<double> A((size_t)k * k, 0.0), V;
-    for (int i = 0; i < k; ++i) {
-        A[(size_t)i * k + i] = alpha[i];
-        if (i + 1 < k) {
-            A[(size_t)i * k + i + 1] = beta[i];
-            A[(size_t)(i + 1) * k + i] = beta[i];
-        }
-    }
-    jacobi_eig(A, k, V);
-    std::vector<double> c(k, 0.0);
-    for (int j = 0; j < k; ++j) {
-        double lam = A[(size_t)j * k + j];
-        double f = lam > 0 ? std::sqrt(lam) : 0.0;
-        double w = f * V[(size_t)0 * k + j];  // e_1^T v_j
-        for (int i = 0; i < k; ++i) c[i] += V[(size_t)i * k + j] * w;
-    }
-    for (auto& x : c) x *= wnorm;
-    return c;
-}
-
 template <typename T>
 fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_iter, double* y, int& iters) {
     Solver* S = h->solver;
@@ -191,6 +132,19 @@ fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_it
     CgsState& c = S->lan;
     const T* G = std::is_same<T, float>::value ? (const T*)S->G32 : (const T*)S->G64;
     const T* Gd = std::is_same<T, float>::value ? (const T*)S->Gd32 : (const T*)S->Gd64;
+    double* t1 = S->w;  // [>= n] scratch from the GMRES workspace
+    double* t2 = S->r;
+    // Start from W's projection G^+ G W onto the range of G: the component in the null
+    // space of G (the near-null modes dropped from M(r)_ref, one normal mode per body at
+    // coarse sampling) has f(0) = 0, and left in it would put a Ritz value at rounding
+    // level under the square root (an error of sqrt(eps) that grows once the iteration
+    // runs past convergence)
+    // (W is first copied into the solver's workspace: the caller's vector need not have
+    // the 16-byte alignment the tensor-core block operator's bulk copies require)
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(t2, W, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+    FBIM_TRY(block_apply<T>(h, G, t2, t1));
+    FBIM_TRY(block_apply<T>(h, Gd, t1, S->lan_w));
+    W = S->lan_w;
     double wn = 0;
     FBIM_TRY(dev_norm2(h, n, W, wn));
     iters = 0;
@@ -199,8 +153,6 @@ fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_it
         return FBIM_OK;
     }
     double* Vl = S->lz;
-    double* t1 = S->w;  // [>= n] scratch from the GMRES workspace
-    double* t2 = S->r;
     cgs_start(h, c, 1.0 / wn, W, Vl, S->lan_in);
     // One step on the device: w = G M(r) G^T v_k (v_k in lan_in), full reorthogonalisation
     // against V_0..V_k (classical Gram-Schmidt, two passes, FP64), V_{k+1} = w / |w| into
@@ -230,7 +182,7 @@ fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_it
         alpha.push_back(row[k] + row[(m + 1) + k]);
         beta.push_back(bn);
         ++iters;
-        coef = lanczos_coeffs(alpha, beta, k + 1, wn);
+        coef = lanczos_sqrt_coeffs(alpha.data(), beta.data(), k + 1, wn);
         double dn = 0, cn = 0;
         for (int i = 0; i <= k; ++i) {
             const double prev = i < (int)cprev.size() ? cprev[i] : 0.0;
@@ -257,6 +209,34 @@ fbim_status near_field(fbim_handle_s* h, const double* W, double tol, int max_it
 }
 
 }  // namespace
+
+fbim_status lanczos_operator(fbim_handle_s* h, const double* in, double* out) {
+    Solver* S = h->solver;
+    if (h->precision == FBIM_FP32) {
+        FBIM_TRY(block_apply<float>(h, S->G32, in, S->w));
+        FBIM_TRY(apply_operator<float>(h, S->w, S->r, 1));
+        return block_apply<float>(h, S->G32, S->r, out);
+    }
+    FBIM_TRY(block_apply<double>(h, S->G64, in, S->w));
+    FBIM_TRY(apply_operator<double>(h, S->w, S->r, 1));
+    return block_apply<double>(h, S->G64, S->r, out);
+}
+
+fbim_status gplus_apply(fbim_handle_s* h, const double* in, double* out) {
+    Solver* S = h->solver;
+    if (h->precision == FBIM_FP32) return block_apply<float>(h, S->Gd32, in, out);
+    return block_apply<double>(h, S->Gd64, in, out);
+}
+
+fbim_status g_project(fbim_handle_s* h, const double* in, double* out) {
+    Solver* S = h->solver;
+    if (h->precision == FBIM_FP32) {
+        FBIM_TRY(block_apply<float>(h, S->G32, in, S->w));
+        return block_apply<float>(h, S->Gd32, S->w, out);
+    }
+    FBIM_TRY(block_apply<double>(h, S->G64, in, S->w));
+    return block_apply<double>(h, S->Gd64, S->w, out);
+}
 
 fbim_status brownian_slip(fbim_handle_s* h, unsigned long long seed, unsigned long long counter, double kT, double dt,
                           const double* W_r, const double* Z_w, double tol, int max_iter, double* slip,
@@ -316,4 +296,16 @@ extern "C" fbim_status fbim_philox_normals(fbim_handle h, uint64_t seed, uint32_
                                                                                     out_dev);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     return FBIM_OK;
+}
+
+extern "C" fbim_status fbim_host_lanczos_sqrt(const double* alpha, const double* beta, int k, double wnorm,
+                                              double* out) {
+    if (!alpha || !out || k < 1 || (k > 1 && !beta)) return FBIM_ERR_INVALID_ARG;
+    try {
+        const std::vector<double> c = fbim::lanczos_sqrt_coeffs(alpha, beta, k, wnorm);
+        std::copy(c.begin(), c.end(), out);
+        return FBIM_OK;
+    } catch (...) {
+        return FBIM_ERR_SETUP;
+    }
 }

@@ -253,6 +253,14 @@ fbim_status solver_saddle(fbim_handle_s* h, const double* x, double* y, bool fp3
 // point every launch of the handle (kernels, cuFFT plans, cuBLAS) at stream s
 void bind_stream(fbim_handle_s* h, cudaStream_t s);
 
+// Brownian slip pieces (brownian.cu), stream-ordered, no host sync, in the handle's
+// precision: out = G M(r) G^T in (the near-field Lanczos operator; uses the solver's
+// w and r vectors as scratch) and out = G^+ in (Sec. 3.4, Eq. Gprecond-decomp)
+fbim_status lanczos_operator(fbim_handle_s* h, const double* in, double* out);
+fbim_status gplus_apply(fbim_handle_s* h, const double* in, double* out);
+// out = G^+ G in, the projection onto the range of G (uses the solver's w as scratch)
+fbim_status g_project(fbim_handle_s* h, const double* in, double* out);
+
 // allocation-free real-space entry point (noalloc.cu): run by fbim_setup on the
 // handle's device so that the entry point's first call loads and allocates nothing
 fbim_status noalloc_prepare(fbim_handle_s* h);
