@@ -454,6 +454,38 @@ fbim_status fbim_apply_real_noalloc(fbim_handle h, const double* mu_dev, double*
  * fbim_apply_stokeslet. */
 fbim_status fbim_apply_stokeslet_fp64(fbim_handle h, const double* mu_dev, double* v_dev);
 
+/* ---------------------------------------------------------------------------
+ * Second-kind reference solver (App. B): the completed double-layer formulation,
+ *     u + omega (x - q)^perp = 1/2 phi + D phi + sum_b [G(x - q_b) f_b + R(x - q_b) tau_b],
+ *     u = (1/|Gamma|) int phi dS,  omega = (1/W) int phi . (x - q)^perp dS,
+ * periodised with the Hasimoto split of the Stokeslet, rotlet and stresslet (App. B),
+ * trapezoidal rule at the handle's nodes (spectrally accurate on smooth, separated
+ * bodies), FP64 throughout, GMRES without preconditioning.  It reuses the handle's
+ * geometry, cells, r_c, xi and FP64 wave grid (M, P, eta_s); the stresslet and rotlet
+ * decay one power of k slower in wave space than the Stokeslet, so a grid somewhat
+ * finer than the first kind's keeps the same tolerance.  Needs n_box >= 3.  The state
+ * (FFT plans, workspace: about (restart + 6) vectors of 2N + 3N_b doubles plus 8 M^2
+ * doubles) is built on first use and freed with the handle.  Readings: S_lm =
+ * phi_l n_m dS with n pointing into the body; the mean-flow term (1/V) sum x_s (phi . n)
+ * dS; the trapezoidal self term -(1/4 pi) 2 kappa (t t^T) phi dS; perp counter-clockwise.
+ * ------------------------------------------------------------------------- */
+
+/* Solve the second-kind mobility problem for forces and torques F_dev [n_b][3]: U_dev
+ * [n_b][3] velocities, phi_dev NULL or [N][2] double-layer density.  iters: GMRES
+ * iterations; rel_residual: the measured |b - A x| / |b|.  FBIM_ERR_NOT_CONVERGED
+ * (results written) when tol is missed within max_iter.  Synchronises the stream. */
+fbim_status fbim_second_kind_solve(fbim_handle h, const double* F_dev, double tol, int max_iter, double* U_dev,
+                                   double* phi_dev, int* iters, double* rel_residual);
+
+/* y = A x for x = [phi (2N); U (3 n_b)] (device, not aliased): node rows
+ * u + omega (x - q)^perp - 1/2 phi - D phi, closure rows |Gamma| u - int phi dS and
+ * W omega - int phi . (x - q)^perp dS.  Synchronises the stream. */
+fbim_status fbim_second_kind_apply(fbim_handle h, const double* x_dev, double* y_dev);
+
+/* b = [C F; 0] (2N + 3 n_b doubles, device): the periodic Stokeslets and rotlets of the
+ * bodies' forces and torques at every node.  Synchronises the stream. */
+fbim_status fbim_second_kind_rhs(fbim_handle h, const double* F_dev, double* b_dev);
+
 /* Information about the handle's parameters. */
 fbim_status fbim_get_info(fbim_handle h, fbim_info* info);
 

@@ -38,6 +38,7 @@ EXPORTS = [
     "fbim_philox_normals", "fbim_apply_real_noalloc", "fbim_rfd_step",
     "fbim_batch_create", "fbim_batch_solve", "fbim_batch_get_info", "fbim_batch_destroy",
     "fbim_batch_last_error", "fbim_batch_slip", "fbim_update_config_displaced", "fbim_host_lanczos_sqrt",
+    "fbim_second_kind_solve", "fbim_second_kind_apply", "fbim_second_kind_rhs",
     "fbim_mlp_param_count", "fbim_mlp_create", "fbim_mlp_destroy", "fbim_mlp_last_error",
     "fbim_mlp_set_params", "fbim_mlp_get_params", "fbim_mlp_set_normalization", "fbim_mlp_forward",
     "fbim_mlp_gradient", "fbim_mlp_adam_step", "fbim_mlp_launches", "fbim_coarse_pairs",
@@ -107,6 +108,9 @@ _lib.fbim_choose_ewald.argtypes = [_D, _D, _D, _D, _IP, _DP, _DP, _IP, _IP, _DP]
 _lib.fbim_setup.argtypes = [ctypes.POINTER(_P), _I, _I, _DP, _DP, _D, _D, _D, _D, ctypes.POINTER(Params)]
 _lib.fbim_update_config.argtypes = [_P, _P]
 _lib.fbim_update_config_displaced.argtypes = [_P, _P, _D, _P]
+_lib.fbim_second_kind_solve.argtypes = [_P, _P, _D, _I, _P, _P, _IP, _DP]
+_lib.fbim_second_kind_apply.argtypes = [_P, _P, _P]
+_lib.fbim_second_kind_rhs.argtypes = [_P, _P, _P]
 _lib.fbim_apply_stokeslet.argtypes = [_P, _P, _P]
 _lib.fbim_apply_real.argtypes = [_P, _P, _P]
 _lib.fbim_apply_wave.argtypes = [_P, _P, _P]
@@ -412,6 +416,34 @@ class FBIM:
 
     def update_config(self, Q_dev):
         _check(_lib.fbim_update_config(self._h, _ptr(Q_dev)), self._h)
+
+    def second_kind_solve(self, F, tol=1e-12, max_iter=500, want_phi=False, check=True):
+        """Second-kind reference solve (App. B): returns (U [n_b, 3], phi or None, iterations,
+        measured relative residual)."""
+        import torch
+        U = torch.empty((self.n_b, 3), dtype=torch.float64, device=F.device)
+        phi = torch.empty((self.n, 2), dtype=torch.float64, device=F.device) if want_phi else None
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        st = _lib.fbim_second_kind_solve(self._h, _ptr(F), float(tol), int(max_iter), _ptr(U),
+                                         None if phi is None else _ptr(phi), ctypes.byref(it), ctypes.byref(res))
+        if check or st not in (0, 6):
+            _check(st, self._h)
+        return U, phi, it.value, res.value
+
+    def second_kind_apply(self, x):
+        """y = A x of the second-kind system, x = [phi (2N); U (3 n_b)] flat float64 (device)."""
+        import torch
+        y = torch.empty_like(x)
+        _check(_lib.fbim_second_kind_apply(self._h, _ptr(x), _ptr(y)), self._h)
+        return y
+
+    def second_kind_rhs(self, F):
+        """b = [C F; 0] of the second-kind system for F [n_b, 3] (device)."""
+        import torch
+        b = torch.empty(2 * self.n + 3 * self.n_b, dtype=torch.float64, device=F.device)
+        _check(_lib.fbim_second_kind_rhs(self._h, _ptr(F), _ptr(b)), self._h)
+        return b
 
     def update_config_displaced(self, Q_dev, a, W_dev):
         """Move the bodies to Q + a W (device [n_b, 3] tensors)."""

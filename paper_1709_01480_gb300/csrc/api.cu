@@ -50,6 +50,7 @@ void release(fbim_handle h) {
     cudaFree(h->tslot);
     cudaFree(h->tile_tmp);
     cudaFree(h->rot);
+    fbim::free_second_kind(h);
     fbim::free_solver(h);
     delete h;
 }

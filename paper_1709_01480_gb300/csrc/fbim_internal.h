@@ -181,6 +181,7 @@ struct fbim_handle_s {
     std::vector<double> host_band;   // symmetrised M(a)_ref band (host copy)
     double* rot = nullptr;           // [n_b][2] (cos theta, sin theta) of each body
     struct Solver* solver = nullptr; // preconditioners and Krylov workspace (solver.cu)
+    struct SecondKind* sk = nullptr; // second-kind reference solver (secondkind.cu), built on first use
 
     // ---- stage timing (fbim_set_timing) ------------------------------------
     bool timing = false;
@@ -246,6 +247,7 @@ fbim_status update_positions_if_moved(fbim_handle_s* h, const double* Q_dev);
 
 // solvers (solver.cu)
 void free_solver(fbim_handle_s* h);
+void free_second_kind(fbim_handle_s* h);  // secondkind.cu
 fbim_status ensure_solver(fbim_handle_s* h);
 // block preconditioner and saddle operator on x = [mu; U] (stream-ordered, no host sync)
 fbim_status solver_precondition(fbim_handle_s* h, const double* in, double* out, bool fp32);
