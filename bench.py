@@ -593,6 +593,7 @@ def run_gpu(args):
                        "support": info["support"], "support32": info["support32"], "n_pairs_within_rc": n_pairs,
                        "pair_entries": n_entries, "tile": info["tile"],
                        "spread_variant": ("tile", "warp")[info["wave_variant"]],
+                       "spread_tuner_ms": dict(zip(("tile", "warp"), info["variant_ms"])),
                        "interp_variant": ("tile", "warp")[info["interp_variant"]],
                        "l2": "flushed (256 MB write) before every timed step",
                        "precision": "FP32 Ewald operator and preconditioner GEMM; FP64 Alpert band, "

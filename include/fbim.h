@@ -253,11 +253,16 @@ fbim_status fbim_rfd_step(fbim_handle h, const double* F_dev, double dt, double 
                           uint64_t step, const double* W_r_dev, const double* Z_w_dev, const double* W_t_dev,
                           double tol, int max_iter, double* Q_dev, int* iters);
 
-/* Brownian dynamics step schemes of Sec. 4.4 (fbim_bd_step). */
-typedef enum { FBIM_EM = 0, FBIM_AB2 = 1 } fbim_scheme;
+/* Brownian dynamics step schemes of Sec. 4.4 (fbim_bd_step).  FBIM_EM_NO_RFD is the
+ * biased Euler-Maruyama scheme of Sec. 4.4.1 (Eq. EM-noRFD) that omits the stochastic
+ * drift; it is there to show what the drift term does (its equilibrium distribution is
+ * Eq. biased-dist instead of the Gibbs-Boltzmann one). */
+typedef enum { FBIM_EM = 0, FBIM_AB2 = 1, FBIM_EM_NO_RFD = 2 } fbim_scheme;
 
 /* One Brownian dynamics step with a random finite difference (Sec. 4.4):
  *   FBIM_EM  (Eq. EM-RFD): as fbim_rfd_step, three solves.
+ *   FBIM_EM_NO_RFD (Eq. EM-noRFD with the force term): Q <- Q + dt N F + sqrt(2 kT dt) N^1/2 W,
+ *            one solve (delta, tol_rfd and W~ unused; W~ is not drawn).
  *   FBIM_AB2 (Eq. AB2-RFD): Q <- Q + dt (3/2 N F - 1/2 N_prev F_prev) + sqrt(2 kT dt) N^1/2 W
  *            + dt kT/delta [N(Q + delta/2 W~) - N(Q - delta/2 W~)] W~, four solves (N F, the
  *            slip's velocity with force zero, the RFD pair).
@@ -271,6 +276,16 @@ fbim_status fbim_bd_step(fbim_handle h, int scheme, const double* F_dev, double 
                          uint64_t seed, uint64_t step, const double* W_r_dev, const double* Z_w_dev,
                          const double* W_t_dev, double tol, double tol_rfd, int max_iter, double* NF_dev,
                          int have_prev, double* Q_dev, int* iters);
+
+/* The position update of Eqs. EM-RFD and EM-noRFD for velocities solved elsewhere (for
+ * instance by fbim_batch_solve for many independent trajectories at once):
+ *   Q[i] += dt U[i] + c (Up[i] - Um[i]),  i < n,   c = dt kT / delta,
+ * or Q[i] += dt U[i] when Up_dev and Um_dev are both NULL.  U_dev: the velocities of the
+ * solve with the slip and the force; Up_dev, Um_dev: those of the solves with force W~
+ * at Q + delta/2 W~ and Q - delta/2 W~.  All device arrays of doubles; asynchronous on
+ * stream (a cudaStream_t, NULL = the legacy default stream) of the current device. */
+fbim_status fbim_bd_update(void* stream, size_t n, double dt, double c, const double* U_dev, const double* Up_dev,
+                           const double* Um_dev, double* Q_dev);
 
 /* n standard normals of (seed, stream, counter) from Philox4x32-10 and Box-Muller:
  * normal i is element i mod 2 of block i / 2, counter block = (i/2 low, i/2 high,

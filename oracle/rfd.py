@@ -49,6 +49,15 @@ def em_rfd_step(Q, ref_nodes, L, xi, F, dt, kT, delta, W_r, Z, W_tilde, eta=1.0,
     return Q + dt * U + dt * kT / delta * (Up - Um)
 
 
+def em_no_rfd_step(Q, ref_nodes, L, xi, F, dt, kT, W_r, Z, eta=1.0, order=4):
+    """The biased step of Sec. 4.4.1 (Eq. EM-noRFD, with the force term kept): Eq. EM-RFD
+    without its random finite difference, Q + dt N F + sqrt(2 kT dt) N^1/2 W from one
+    saddle solve with right-hand side [slip; F]."""
+    X = singlelayer.node_positions(Q, ref_nodes)
+    sl = brownian.slip(X, Q, ref_nodes, L, xi, kT, dt, W_r, Z, eta, order)
+    return Q + dt * mobility_velocity(Q, ref_nodes, L, xi, F, sl, eta, order)
+
+
 def ab2_rfd_step(Q, ref_nodes, L, xi, F, NF_prev, dt, kT, delta, W_r, Z, W_tilde, eta=1.0, order=4):
     """One step of Eq. AB2-RFD; returns (Q^{n+1}, N^n F^n).  NF_prev = None: first step."""
     X = singlelayer.node_positions(Q, ref_nodes)

@@ -44,6 +44,7 @@ EXPORTS = [
     "fbim_mlp_gradient", "fbim_mlp_adam_step", "fbim_mlp_launches", "fbim_coarse_pairs",
     "fbim_coarse_enable", "fbim_coarse_stats", "fbim_apply_stokeslet_fp64",
     "fbim_set_residual_audit", "fbim_residual_audit", "fbim_precondition", "fbim_bd_step",
+    "fbim_bd_update",
 ]
 STAGES = ["gather", "spread", "fft_fwd", "scale", "fft_inv", "pairs", "interp", "finish"]
 
@@ -163,10 +164,31 @@ _lib.fbim_precondition.argtypes = [_P, _P, _P]
 _lib.fbim_bd_step.argtypes = [_P, _I, _P, _D, _D, _D, ctypes.c_uint64, ctypes.c_uint64, _P, _P, _P, _D, _D, _I, _P,
                               _I, _P, _IP]
 _lib.fbim_residual_audit.argtypes = [_P, _I, _DP, _DP, _IP]
+_lib.fbim_bd_update.argtypes = [_P, ctypes.c_size_t, _D, _D, _P, _P, _P, _P]
 
 
 def lib():
     return _lib
+
+
+def bd_update(Q, U, dt, c=0.0, Up=None, Um=None, stream=None):
+    """Q += dt U + c (Up - Um) (or Q += dt U without Up, Um) on the device: the position
+    update of the Brownian dynamics steps for velocities from a batched solve."""
+    import torch
+    ts = [t for t in (Q, U, Up, Um) if t is not None]
+    n = Q.numel()
+    for t in ts:
+        if t.dtype != torch.float64 or not t.is_contiguous() or not t.is_cuda or t.numel() != n \
+                or t.device != Q.device:
+            raise ValueError("bd_update: contiguous float64 CUDA tensors of equal size on one device")
+    if (Up is None) != (Um is None):
+        raise ValueError("bd_update: give both Up and Um or neither")
+    if stream is None:
+        stream = torch.cuda.current_stream(Q.device)
+    opt = lambda t: None if t is None else _ptr(t)
+    with torch.cuda.device(Q.device):
+        _check(_lib.fbim_bd_update(ctypes.c_void_p(stream.cuda_stream), n, float(dt), float(c), _ptr(U), opt(Up),
+                                   opt(Um), _ptr(Q)))
 
 
 def _check(status, handle=None):
@@ -345,12 +367,13 @@ class FBIM:
 
     def bd_step(self, F, Q, dt, kT=1.0, delta=1e-3, scheme="em", seed=0, step=0, W_r=None, Z_w=None, W_t=None,
                 tol=1e-6, tol_rfd=None, NF=None, have_prev=False, max_iter=500):
-        """One Brownian dynamics step (scheme "em" or "ab2"); Q is updated in place.  For "ab2",
-        NF (device [n_b, 3]) carries N F between steps (read when have_prev, written always).
-        Returns the GMRES iterations of the step's solves."""
+        """One Brownian dynamics step (scheme "em", "ab2" or "em_no_rfd", the biased scheme
+        without the stochastic drift); Q is updated in place.  For "ab2", NF (device [n_b, 3])
+        carries N F between steps (read when have_prev, written always).  Returns the GMRES
+        iterations of the step's solves."""
         it = ctypes.c_int(0)
         opt = lambda t: None if t is None else _ptr(t)
-        sch = {"em": 0, "ab2": 1}[scheme]
+        sch = {"em": 0, "ab2": 1, "em_no_rfd": 2}[scheme]
         _check(_lib.fbim_bd_step(self._h, sch, _ptr(F), float(dt), float(kT), float(delta), int(seed), int(step),
                                  opt(W_r), opt(Z_w), opt(W_t), float(tol), float(tol if tol_rfd is None else tol_rfd),
                                  int(max_iter), opt(NF), 1 if have_prev else 0, _ptr(Q), ctypes.byref(it)), self._h)
@@ -494,7 +517,8 @@ class Batch:
         self._check(_lib.fbim_batch_get_info(self._b, ctypes.byref(i)))
         return i.as_dict()
 
-    def solve(self, F, slip=None, tol=1e-6, max_iter=500, check=True):
+    def solve(self, F, slip=None, tol=1e-6, max_iter=500, check=True, out=None):
+        """out: optional flat float64 tensor for the stacked velocities (3 n_b per system)."""
         import torch
         Fs = torch.cat([f.reshape(-1) for f in F]) if isinstance(F, (list, tuple)) else F
         Ss = None
@@ -502,7 +526,12 @@ class Batch:
             Ss = torch.cat([s.reshape(-1) for s in slip]) if isinstance(slip, (list, tuple)) else slip
         n_sys = len(self.systems)
         sizes = [3 * self.ops[k].n_b for k, _ in self.systems]
-        U = torch.empty(sum(sizes), dtype=torch.float64, device=Fs.device)
+        if out is None:
+            U = torch.empty(sum(sizes), dtype=torch.float64, device=Fs.device)
+        elif out.numel() != sum(sizes) or out.dtype != torch.float64 or not out.is_contiguous():
+            raise ValueError("out: contiguous float64 with 3 n_b entries per system")
+        else:
+            U = out.view(-1)
         it = (ctypes.c_int * n_sys)()
         res = (ctypes.c_double * n_sys)()
         st = _lib.fbim_batch_solve(self._b, _ptr(Fs), None if Ss is None else _ptr(Ss), float(tol), int(max_iter),

@@ -46,10 +46,12 @@ __global__ void k_displace(int n, const double* __restrict__ Q, double a, const 
     if (i < n) out[i] = Q[i] + a * w[i];
 }
 
-__global__ void k_rfd_update(int n, double* __restrict__ Q, double dt, const double* __restrict__ U, double c,
+// Up, Um null: Q += dt U (no random finite difference)
+__global__ void k_rfd_update(long long n, double* __restrict__ Q, double dt, const double* __restrict__ U, double c,
                              const double* __restrict__ Up, const double* __restrict__ Um) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) Q[i] += dt * U[i] + c * (Up[i] - Um[i]);
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Q[i] += Up ? dt * U[i] + c * (Up[i] - Um[i]) : dt * U[i];
 }
 
 // Q += dt (U_noise + 3/2 Ud - 1/2 NF_prev) + c (Up - Um); NF_prev NULL: dt (U_noise + Ud)
@@ -70,6 +72,7 @@ fbim_status bd_step(fbim_handle_s* h, int scheme, const double* F, double dt, do
                     int* iters_total) {
     const int n3 = 3 * h->n_b, n2 = 2 * h->N, tb = 256;
     const bool ab2 = scheme == FBIM_AB2;
+    const bool no_rfd = scheme == FBIM_EM_NO_RFD;
     // work: slip [2N], W~, Q+-, U, U+, U-, U_det, zero [3 n_b each] (kept in the solver workspace)
     FBIM_TRY(ensure_solver(h));
     Solver* S = h->solver;
@@ -101,6 +104,13 @@ fbim_status bd_step(fbim_handle_s* h, int scheme, const double* F, double dt, do
             s0 = mobility_solve(h, F, nullptr, tol, max_iter, Ud, nullptr, &it, nullptr, false);
             total += it;
             if (s0 != FBIM_OK && s0 != FBIM_ERR_NOT_CONVERGED) return s0;
+        }
+        if (no_rfd) {  // Eq. EM-noRFD: Q += dt (N F + N^1/2 W), no stochastic drift
+            k_rfd_update<<<(n3 + tb - 1) / tb, tb, 0, h->stream>>>(n3, Q, dt, U, 0.0, nullptr, nullptr);
+            h->launches += 1;
+            FBIM_CUDA_TRY(h, cudaGetLastError());
+            FBIM_TRY(update_positions(h, Q));
+            return s1 != FBIM_OK ? FBIM_ERR_NOT_CONVERGED : FBIM_OK;
         }
         // (2) random finite difference of N along W~
         if (W_t) {
@@ -153,7 +163,8 @@ extern "C" fbim_status fbim_bd_step(fbim_handle h, int scheme, const double* F_d
                                     const double* Z_w_dev, const double* W_t_dev, double tol, double tol_rfd,
                                     int max_iter, double* NF_dev, int have_prev, double* Q_dev, int* iters) {
     if (!h || !F_dev || !Q_dev || !(dt > 0) || !(kT >= 0) || !(delta > 0) || !(tol > 0) || !(tol_rfd > 0) ||
-        max_iter <= 0 || (scheme != FBIM_EM && scheme != FBIM_AB2) || (scheme == FBIM_AB2 && !NF_dev))
+        max_iter <= 0 || (scheme != FBIM_EM && scheme != FBIM_AB2 && scheme != FBIM_EM_NO_RFD) ||
+        (scheme == FBIM_AB2 && !NF_dev))
         return FBIM_ERR_INVALID_ARG;
     try {
         if (cudaSetDevice(h->device) != cudaSuccess) return FBIM_ERR_CUDA;
@@ -178,4 +189,16 @@ extern "C" fbim_status fbim_rfd_step(fbim_handle h, const double* F_dev, double 
         h->fail("unexpected host exception in fbim_rfd_step");
         return FBIM_ERR_SETUP;
     }
+}
+
+extern "C" fbim_status fbim_bd_update(void* stream, size_t n, double dt, double c, const double* U_dev,
+                                      const double* Up_dev, const double* Um_dev, double* Q_dev) {
+    if (!U_dev || !Q_dev || (!Up_dev) != (!Um_dev) || !std::isfinite(dt) || !std::isfinite(c) ||
+        n > (size_t)1 << 38)
+        return FBIM_ERR_INVALID_ARG;
+    if (n == 0) return FBIM_OK;
+    const int tb = 256;
+    fbim::k_rfd_update<<<(unsigned)((n + tb - 1) / tb), tb, 0, (cudaStream_t)stream>>>(
+        (long long)n, Q_dev, dt, U_dev, c, Up_dev, Um_dev);
+    return cudaGetLastError() == cudaSuccess ? FBIM_OK : FBIM_ERR_CUDA;
 }

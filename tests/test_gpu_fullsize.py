@@ -84,11 +84,11 @@ def _expect(workload, split):
     return _expect_cache[split]
 
 
-def _handle(fb, w, split, precision):
+def _handle(fb, w, split, precision, wave="auto"):
     s = SPLITS[split]
     xi = _xi(w.L, s["n_box"], w.tol)
     return fb.FBIM(w.ref_nodes, w.Q, w.L, tol=w.tol, r_c=w.L / s["n_box"], xi=xi, precision=precision,
-                   grid=s["grid"])
+                   grid=s["grid"], wave=wave)
 
 
 @pytest.mark.parametrize("split", ["L/115", "L/91"])
@@ -115,6 +115,22 @@ def test_full_size_every_body_forced_matches_oracle(torch, fb, workload, split, 
         e = _rel(v64, exp["all"])
         print(f"full size fp32-handle FP64 operator {split}: rel err {e:.3e}")
         assert e < FP64_BAR
+    op.close()
+
+
+@pytest.mark.parametrize("wave", ["warp", "tile"])
+def test_full_size_fp32_spread_variants_match_oracle(torch, fb, workload, wave):
+    """Each FP32 spread variant at the benchmark's split (grid 1296, support 11), every
+    body forced: the wave part against the oracle's lattice sum at the FP32 bar."""
+    w, X, mu, rows = workload
+    xi, real, wave_exp = _expect(workload, "L/91")
+    op = _handle(fb, w, "L/91", "fp32", wave=wave)
+    assert op.info["wave_variant"] == {"tile": 0, "warp": 1}[wave]
+    mu_d = torch.tensor(mu, device="cuda")
+    for rep in range(2):   # the atomic variants start from a zeroed grid on every call
+        e = _rel(op.apply_wave(mu_d).cpu().numpy()[rows], wave_exp)
+        print(f"full size fp32 spread {wave} (call {rep}): wave part rel err {e:.3e}")
+        assert e < FP32_BAR, e
     op.close()
 
 
