@@ -25,6 +25,10 @@ Q +- delta/2 W~) in the same batched solve; and
 ``learned`` times the mobility solve of a dense 4096-body suspension (area
 fraction 0.40) with and without the learned coarse level.
 
+An opt-in leg (``--legs diffusion``) runs the free diffusion of a four-fold starfish
+in the unit cell (Sec. 4.4.1) as 64 batched trajectories with and without the random
+finite difference and reports the equilibrium statistics.
+
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
 instead, on a bounded sample of the same workload.
 """
@@ -354,6 +358,39 @@ def batched_leg(torch, fb, fbim_synth, stream, flush, reps):
     return out
 
 
+def diffusion_leg(torch, fb, fbim_synth, steps, R=64):
+    """Free diffusion of a four-fold starfish in the unit cell (Sec. 4.4.1): R independent
+    trajectories through the batched path, with (Eq. EM-RFD) and without (Eq. EM-noRFD) the
+    random finite difference; throughput and the equilibrium statistics (mean of cos 4 theta
+    and the one-step mean square displacement over 4 kT dt, with standard errors of the
+    trajectory means)."""
+    from paper_1709_01480_gb300.freediffusion import FreeDiffusion
+    ref = fbim_synth.starfish_ref_nodes(64, r_s=0.45 / 1.3, b=0.3, arms=4)
+    tol, dt, kT = 1e-7, 0.02, 1.0
+    delta = 0.45 * tol ** (1.0 / 3.0)
+    burn = min(50, steps // 4)
+    out = {"workload": "starfish4arm_np64_unitcell (b 0.3, a 0.45, 4th-order Alpert)", "trajectories": R,
+           "steps": steps, "dt": dt, "kT": kT, "tol": tol, "delta": delta, "burn_in_steps": burn}
+    for scheme in ("em", "em_no_rfd"):
+        rng = np.random.default_rng(2024)
+        Q0 = np.column_stack([np.full(R, 0.5), np.full(R, 0.5), rng.uniform(0.0, 0.5 * math.pi, R)])
+        t0 = time.time()
+        fd = FreeDiffusion(ref, 1.0, Q0, scheme=scheme, dt=dt, kT=kT, delta=delta, tol=tol, ewald_tol=tol,
+                           seeds=[7000 + 131 * (scheme == "em") + j for j in range(R)])
+        t1 = time.time()
+        traj = fd.run(steps)
+        t2 = time.time()
+        it = np.array(fd.iters)
+        fd.close()
+        c4 = np.cos(4.0 * traj[burn:, :, 2]).mean(axis=0)
+        d2 = (np.sum(np.diff(traj[:, :, :2], axis=0) ** 2, axis=2)[burn:] / (4.0 * kT * dt)).mean(axis=0)
+        out[scheme] = {"trajectory_steps_per_s": R * steps / (t2 - t1), "ms_per_step": 1e3 * (t2 - t1) / steps,
+                       "setup_s": t1 - t0, "gmres_iters_per_solve": float(it.mean()),
+                       "mean_cos4theta": float(c4.mean()), "se_cos4theta": float(c4.std(ddof=1) / math.sqrt(R)),
+                       "msd1_over_4kTdt": float(d2.mean()), "se_msd1_over_4kTdt": float(d2.std(ddof=1) / math.sqrt(R))}
+    return out
+
+
 def learned_leg(torch, fb, fbim_synth, stream, flush, reps):
     """GMRES with and without the learned coarse level on the dense suspension."""
     from paper_1709_01480_gb300 import coarse_train
@@ -575,6 +612,8 @@ def run_gpu(args):
         legs["batched"] = batched_leg(torch, fb, fbim_synth, stream, flush, 2)
     if "learned" in args.legs:
         legs["learned_coarse"] = learned_leg(torch, fb, fbim_synth, stream, flush, 2)
+    if "diffusion" in args.legs:
+        legs["free_diffusion"] = diffusion_leg(torch, fb, fbim_synth, args.diffusion_steps)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -634,7 +673,9 @@ def main():
     ap.add_argument("--r-c", type=float, default=0.0, help="pin the chosen form's cutoff (default: split tuner)")
     ap.add_argument("--grid", type=int, default=0, help="pin the chosen form's FFT grid side (default: tuner)")
     ap.add_argument("--legs", default="batched,learned",
-                    help="extra measurements: batched (independent suspensions), learned (coarse level); '' for none")
+                    help="extra measurements: batched (independent suspensions), learned (coarse level), "
+                         "diffusion (free-diffusion statistics, not in the default set); '' for none")
+    ap.add_argument("--diffusion-steps", type=int, default=400, help="steps per trajectory of the diffusion leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
