@@ -65,7 +65,7 @@ ITERS_PER_SOLVE_REF = 24
 # ncu DRAM bytes per launch of the FP32 operator's kernels, as written by the profiling
 # run of this workload: "key value" lines (config, source hash, bytes per kernel)
 DRAM_RECORD = os.path.join(ROOT, "profiles", "dram_bytes_fp32_matvec_starfish1024.txt")
-PAIR_KERNEL_SOURCE = os.path.join(ROOT, "paper_1709_01480_gb300", "csrc", "ewald_ops.cu")
+PAIR_KERNEL_SOURCE = os.path.join(ROOT, "paper_1709_01480_gb300", "csrc", "pair_spmv.cuh")
 
 
 def source_sha16(path):

@@ -32,6 +32,7 @@
 #include "dfloat.cuh"
 #include "fbim_internal.h"
 #include "ewald_types.cuh"
+#include "pair_spmv.cuh"
 
 namespace fbim {
 
@@ -63,7 +64,7 @@ template <typename T>
 __global__ void k_gather(int N, int n_p, const int* __restrict__ perm, const int* __restrict__ tperm, int want_s,
                          int want_t, const double* __restrict__ rot, const double2* __restrict__ mu,
                          typename V2<T>::type* __restrict__ mu_s, typename V2<T>::type* __restrict__ mu_t,
-                         double2* __restrict__ mu_r, float4* __restrict__ mu_df) {
+                         double2* __restrict__ mu_r, float4* __restrict__ mu_df, float4* __restrict__ mu_rdf) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= N) return;
     if (want_s) {
@@ -78,7 +79,13 @@ __global__ void k_gather(int N, int n_p, const int* __restrict__ perm, const int
         const int b = s / n_p;
         const double c = rot[2 * b], sn = rot[2 * b + 1];
         const double2 u = mu[s];
-        mu_r[s] = make_double2(c * u.x + sn * u.y, -sn * u.x + c * u.y);
+        const double rx = c * u.x + sn * u.y, ry = -sn * u.x + c * u.y;
+        if (mu_rdf) {  // the float-float band's input
+            const dfl::df a = dfl::from_double(rx), b = dfl::from_double(ry);
+            mu_rdf[s] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        } else {
+            mu_r[s] = make_double2(rx, ry);
+        }
     }
     if (want_t) {
         double2 v = mu[tperm[s]];
@@ -92,13 +99,6 @@ __global__ void k_gather(int N, int n_p, const int* __restrict__ perm, const int
 // around t's cell.  The visit order below (cells dy, dx; slots ascending) is the
 // column order of each row of the pair list.
 // ---------------------------------------------------------------------------
-template <typename T> struct PairEntry;
-template <> struct __align__(16) PairEntry<float> { float xx, xy, yy; int src; };
-template <> struct __align__(16) PairEntry<double> { double xx, xy, yy; long long src; };
-// An FP64-list entry of an FP32 handle in float-float form: the leading parts and the
-// source in the first 16 bytes, the trailing parts in the second.
-struct __align__(16) PairEntryDF { float xx_hi, xy_hi, yy_hi; int src; float xx_lo, xy_lo, yy_lo, pad; };
-
 template <typename T>
 __global__ void __launch_bounds__(128) k_pair_count(int N, int n_box, T r_c, T rc2, const int* __restrict__ perm,
                                                    const int* __restrict__ cell, const int* __restrict__ start,
@@ -289,84 +289,6 @@ __global__ void k_off_df(int N, const double2* __restrict__ off, float4* __restr
     out[s] = make_float4(x.hi, x.lo, y.hi, y.lo);
 }
 
-// One pair-list entry read with an evict-first hint: the list is streamed once per
-// product and is larger than L2, where the gathered densities should stay.
-__device__ __forceinline__ PairEntry<float> ld_entry(const PairEntry<float>* p) {
-    const int4 v = __ldcs(reinterpret_cast<const int4*>(p));
-    PairEntry<float> e;
-    e.xx = __int_as_float(v.x);
-    e.xy = __int_as_float(v.y);
-    e.yy = __int_as_float(v.z);
-    e.src = v.w;
-    return e;
-}
-__device__ __forceinline__ PairEntry<double> ld_entry(const PairEntry<double>* p) {
-    const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
-    PairEntry<double> e;
-    e.xx = a.x;
-    e.xy = a.y;
-    e.yy = b.x;
-    e.src = __double_as_longlong(b.y);
-    return e;
-}
-
-// v_s[t] = sum_k pairs[t][k] mu_s[src]: one block per 32-row slice, SPMV_P warps
-// over each row's entries (warp p takes k = p, p + SPMV_P, ..., so that a warp still
-// reads 32 consecutive entries), each thread taking its entries U at a time (U
-// independent list loads, then U independent gathers) to keep several memory
-// requests in flight; the SPMV_P partial sums are added in warp order.
-constexpr int SPMV_P = 4;
-template <typename T>
-__global__ void __launch_bounds__(32 * SPMV_P) k_pair_spmv(int N, const int* __restrict__ slice_start,
-                                                           const PairEntry<T>* __restrict__ pairs,
-                                                           const typename V2<T>::type* __restrict__ mu_s,
-                                                           typename V2<T>::type* __restrict__ v_s) {
-    constexpr int U = sizeof(T) == 4 ? 8 : 4;
-    using T2 = typename V2<T>::type;
-    __shared__ T2 red[SPMV_P][32];
-    const int sl = blockIdx.x, lane = threadIdx.x & 31, part = threadIdx.x >> 5;
-    const int t = sl * 32 + lane;
-    T ax = 0, ay = 0;
-    if (t < N) {  // the slice's rows past N have no entries
-        const int base = slice_start[sl], len = slice_start[sl + 1] - base;
-        const PairEntry<T>* row = pairs + (size_t)base * 32 + lane;
-        int k = part;
-        for (; k + (U - 1) * SPMV_P < len; k += U * SPMV_P) {
-            PairEntry<T> e[U];
-            T2 m[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) e[u] = ld_entry(row + (size_t)(k + u * SPMV_P) * 32);
-#pragma unroll
-            for (int u = 0; u < U; ++u) m[u] = __ldg(mu_s + e[u].src);
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                ax = fma(e[u].xx, m[u].x, fma(e[u].xy, m[u].y, ax));
-                ay = fma(e[u].xy, m[u].x, fma(e[u].yy, m[u].y, ay));
-            }
-        }
-        for (; k < len; k += SPMV_P) {
-            const PairEntry<T> e = ld_entry(row + (size_t)k * 32);
-            const T2 m = __ldg(mu_s + e.src);
-            ax = fma(e.xx, m.x, fma(e.xy, m.y, ax));
-            ay = fma(e.xy, m.x, fma(e.yy, m.y, ay));
-        }
-    }
-    red[part][lane].x = ax;
-    red[part][lane].y = ay;
-    __syncthreads();
-    if (part == 0 && t < N) {
-        T sx = red[0][lane].x, sy = red[0][lane].y;
-#pragma unroll
-        for (int p = 1; p < SPMV_P; ++p) {
-            sx += red[p][lane].x;
-            sy += red[p][lane].y;
-        }
-        v_s[t].x = sx;
-        v_s[t].y = sy;
-    }
-}
-
 // The FP64 real-space product of an FP32 handle on its float-float list: products
 // and sums in float-float (about 2^-46 per operation, so ~1e-13 on a row sum),
 // the sum rounded to FP64 once per row.  Same row order and U-wide batching as
@@ -471,6 +393,46 @@ __global__ void k_band(int N, int n_p, int band, const double* __restrict__ rot,
         ay += a.z * u.x + a.w * u.y;
     }
     v_band[m] = make_double2(c * ax - s * ay, s * ax + c * ay);
+}
+
+// The same band product for the FP32 operator, in float-float arithmetic on the FP32
+// pipes (about 2^-46 per operation, so the band velocities keep ~1e-14 of their size,
+// FP64-class accuracy) instead of 84 FMAs per node on the FP64 pipe.  band_df holds
+// each entry's four coefficients as float-float (a float4 of leading parts, one of
+// trailing parts); mu_rdf the rotated forces (k_gather); the rotation back to the lab
+// frame is in FP64.
+__global__ void k_band_df(int N, int n_p, int band, const double* __restrict__ rot, const float4* __restrict__ A,
+                          const float4* __restrict__ mu_rdf, double2* __restrict__ v_band) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= N) return;
+    const int b = m / n_p, j = m - b * n_p;
+    const int B = 2 * band + 1;
+    const float4* ub = mu_rdf + (size_t)b * n_p;
+    const float4* a2 = A + (size_t)j * B * 2;
+    dfl::df ax = {0.f, 0.f}, ay = {0.f, 0.f};
+    for (int o = -band; o <= band; ++o) {
+        int jj = j + o;
+        jj += (jj < 0) ? n_p : 0;
+        jj -= (jj >= n_p) ? n_p : 0;
+        const float4 u = ub[jj];
+        const float4 hi = a2[2 * (o + band)], lo = a2[2 * (o + band) + 1];
+        const dfl::df ux = {u.x, u.y}, uy = {u.z, u.w};
+        ax = dfl::add_fast(ax, dfl::add_fast(dfl::mul({hi.x, lo.x}, ux), dfl::mul({hi.y, lo.y}, uy)));
+        ay = dfl::add_fast(ay, dfl::add_fast(dfl::mul({hi.z, lo.z}, ux), dfl::mul({hi.w, lo.w}, uy)));
+    }
+    const double c = rot[2 * b], s = rot[2 * b + 1];
+    const double bx = dfl::to_double(ax), by = dfl::to_double(ay);
+    v_band[m] = make_double2(c * bx - s * by, s * bx + c * by);
+}
+
+// band_df from the FP64 band [n_p][B][4]: per entry (hi of the four, lo of the four)
+__global__ void k_band_to_df(int n_entries, const double* __restrict__ A, float4* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_entries) return;
+    dfl::df d[4];
+    for (int q = 0; q < 4; ++q) d[q] = dfl::from_double(A[4 * (size_t)i + q]);
+    out[2 * (size_t)i] = make_float4(d[0].hi, d[1].hi, d[2].hi, d[3].hi);
+    out[2 * (size_t)i + 1] = make_float4(d[0].lo, d[1].lo, d[2].lo, d[3].lo);
 }
 
 // Back to body order: v_m = v_s[slot[m]] + v_band_m (real space) + v_t[tslot[m]] (wave space).
@@ -663,12 +625,16 @@ static fbim_status autotune_wave(fbim_handle_s* h) {
     std::vector<T2> ones(h->N);
     for (auto& o : ones) o.x = o.y = T(1);
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.mu_t, ones.data(), h->N * sizeof(T2), cudaMemcpyHostToDevice, h->stream));
+    std::vector<double2> ones_n(h->N, make_double2(1.0, 1.0));  // the warp spread gathers from body order
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.mu_r, ones_n.data(), h->N * sizeof(double2), cudaMemcpyHostToDevice, h->stream));
+    FBIM_CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     cudaEvent_t ev[2];
     for (auto& x : ev) FBIM_CUDA_TRY(h, cudaEventCreate(&x));
     auto spread = [&](int v) {
         if (v == 1) {
             cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream);
-            warp_spread<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.mu_t, e.grid);
+            warp_spread<T>(h->stream, h->N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, nullptr, e.mu_r, h->tperm,
+                           e.grid);
         } else {
             tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
         }
@@ -743,6 +709,13 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, tile_set_smem<T>(TileGeom{h->M, h->TS, h->n_tile, e.P, (e.P - 1) / 2}));
     if constexpr (std::is_same<T, double>::value) {
         if (h->precision == FBIM_FP32) FBIM_TRY(wfft_setup(h));
+    } else {  // the FP32 operator's Alpert band in float-float
+        const int n_ent = h->n_p * (2 * h->band + 1);
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.band_df, (size_t)n_ent * 2 * sizeof(float4)));
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_rdf, N * sizeof(float4)));
+        k_band_to_df<<<(n_ent + 255) / 256, 256, 0, h->stream>>>(n_ent, h->band_dev, e.band_df);
+        h->launches += 1;
+        FBIM_CUDA_TRY(h, cudaGetLastError());
     }
     e.ready = true;
     FBIM_TRY(refresh_offsets<T>(h));
@@ -751,6 +724,17 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     else
         e.spread_variant = e.interp_variant = h->autotune == 2 ? 1 : 0;
     return FBIM_OK;
+}
+
+// v_band = the Alpert band applied to the rotated forces: float-float for the FP32
+// operator (band_df set), FP64 otherwise
+template <typename T>
+static void band_product(cudaStream_t st, fbim_handle_s* h, EwaldBuffers<T>& e) {
+    const int N = h->N, tb = 256;
+    if (e.band_df)
+        k_band_df<<<(N + tb - 1) / tb, tb, 0, st>>>(N, h->n_p, h->band, h->rot, e.band_df, e.mu_rdf, e.v_band);
+    else
+        k_band<<<(N + tb - 1) / tb, tb, 0, st>>>(N, h->n_p, h->band, h->rot, h->band_dev, e.mu_r, e.v_band);
 }
 
 // v_s = (real-space pair list) mu_s, on the plain or the float-float list
@@ -775,18 +759,35 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     const bool real = which & 1, wave = which & 2;
     h->mark_begin();
     const bool df = real && e.pairs_df;  // float-float FP64 list (FP32 handles)
-    k_gather<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->perm, h->tperm, real, wave, h->rot,
-                                                         (const double2*)mu, (T2*)e.mu_s, (T2*)e.mu_t, e.mu_r,
-                                                         df ? e.mu_df : nullptr);
-    h->mark(FBIM_ST_GATHER);
     // real space on the auxiliary stream, concurrent with the wave space (sequential
     // while the stage timers run, so that each stage is timed alone)
     const bool fork = real && wave && h->aux && !h->timing;
+    // the warp spread gathers its forces itself; the warp interpolation writes the sum in
+    // body order itself (after the real space has joined), so gather and finish drop out
+    const bool spread_gathers = wave && e.spread_variant == 1;
+    const bool fused_out = wave && e.interp_variant == 1 && !h->timing && (fork || !real);
+    const cudaStream_t rs = fork ? h->aux : h->stream;
     if (fork) {
         FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
         FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    }
+    int n_launch = 0;
+    if (real) {
+        k_gather<T><<<(N + tb - 1) / tb, tb, 0, rs>>>(N, h->n_p, h->perm, h->tperm, 1, 0, h->rot,
+                                                      (const double2*)mu, (T2*)e.mu_s, (T2*)e.mu_t, e.mu_r,
+                                                      df ? e.mu_df : nullptr, e.mu_rdf);
+        ++n_launch;
+    }
+    if (wave && !spread_gathers) {
+        k_gather<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->perm, h->tperm, 0, 1, h->rot,
+                                                             (const double2*)mu, (T2*)e.mu_s, (T2*)e.mu_t, e.mu_r,
+                                                             nullptr, nullptr);
+        ++n_launch;
+    }
+    h->mark(FBIM_ST_GATHER);
+    if (fork) {
         pair_product<T>(h->aux, N, e, df);
-        k_band<<<(N + tb - 1) / tb, tb, 0, h->aux>>>(N, h->n_p, h->band, h->rot, h->band_dev, e.mu_r, e.v_band);
+        band_product<T>(h->aux, h, e);
         FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_join, h->aux));
     }
     const TileGeom tg{h->M, h->TS, h->n_tile, e.P, (e.P - 1) / 2};
@@ -797,7 +798,8 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         const size_t M = h->M, Mh = h->M / 2 + 1;
         if (e.spread_variant == 1) {
             FBIM_CUDA_TRY(h, cudaMemsetAsync(e.grid, 0, 2 * M * M * sizeof(T), h->stream));
-            warp_spread<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.mu_t, e.grid);
+            warp_spread<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, nullptr, (const double2*)mu,
+                           h->tperm, e.grid);
         } else {
             tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
         }
@@ -834,20 +836,35 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         h->mark(FBIM_ST_PAIRS);
     }
     if (wave) {
-        if (e.interp_variant == 1)
+        if (fused_out) {
+            if (fork) FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+            InterpEpilogue<T> ep;
+            ep.v = (double2*)v;
+            ep.tperm = h->tperm;
+            if (real) {
+                ep.slot = h->slot;
+                ep.v_s = (const T2*)e.v_s;
+                ep.v_band = e.v_band;
+            }
+            warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t, ep);
+        } else if (e.interp_variant == 1) {
             warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
-        else
+        } else {
             tile_interp<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.grid, e.v_t);
+        }
         h->mark(FBIM_ST_INTERP);
     }
-    if (fork) FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    if (real && !fork)
-        k_band<<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, h->n_p, h->band, h->rot, h->band_dev, e.mu_r, e.v_band);
-    k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, real ? 1 : 0, wave ? 1 : 0, h->slot, h->tslot,
-                                                         (const T2*)e.v_s, (const T2*)e.v_t, e.v_band,
-                                                         (double2*)v);
+    if (!fused_out) {
+        if (fork) FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+        if (real && !fork)
+            band_product<T>(h->stream, h, e);
+        k_finish<T><<<(N + tb - 1) / tb, tb, 0, h->stream>>>(N, real ? 1 : 0, wave ? 1 : 0, h->slot, h->tslot,
+                                                             (const T2*)e.v_s, (const T2*)e.v_t, e.v_band,
+                                                             (double2*)v);
+        ++n_launch;
+    }
     h->mark(FBIM_ST_FINISH);
-    h->launches += 2 + (wave ? (e.spread_variant == 1 ? 3 : 4) : 0) + (real ? 2 : 0);
+    h->launches += n_launch + (wave ? (e.spread_variant == 1 ? 3 : 4) : 0) + (real ? 2 : 0);
     FBIM_CUDA_TRY(h, cudaGetLastError());
     h->collect();
     return FBIM_OK;
@@ -975,6 +992,8 @@ static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.pairs);
     cudaFree(e.off_df);
     cudaFree(e.mu_df);
+    cudaFree(e.band_df);
+    cudaFree(e.mu_rdf);
     cudaFree(e.pw);
     cudaFree(e.slice_start);
     cudaFree(e.row_count);

@@ -133,14 +133,48 @@ void tile_spread(cudaStream_t st, const TileGeom& tg, T a, T g0, const int* tsta
 template <typename T>
 void tile_interp(cudaStream_t st, const TileGeom& tg, T a, T g0, const int* tstart, const int2* tbase,
                  const void* tfrac, const T* grid, void* v_t);
+// Fused end of the operator for the warp-per-node interpolation: instead of the wave
+// part in tile order (v_t), write v[m] = (v_s[slot[m]] + v_band[m]) + wave_m in body
+// order, m = tperm[i] -- the sum k_finish forms, in its order; v_s and v_band null: the
+// wave part alone.  v null: the tile-order output.
+template <typename T>
+struct InterpEpilogue {
+    double2* v = nullptr;
+    const int* tperm = nullptr;
+    const int* slot = nullptr;
+    const typename V2<T>::type* v_s = nullptr;
+    const double2* v_band = nullptr;
+};
+
+template <typename T>
+__device__ __forceinline__ void interp_store(const InterpEpilogue<T>& ep, typename V2<T>::type* v_t, int i, T sx,
+                                             T sy) {
+    if (!ep.v) {
+        v_t[i].x = sx;
+        v_t[i].y = sy;
+        return;
+    }
+    const int m = ep.tperm[i];
+    double vx = 0.0, vy = 0.0;
+    if (ep.v_s) {
+        const typename V2<T>::type w = ep.v_s[ep.slot[m]];
+        const double2 b = ep.v_band[m];
+        vx = (double)w.x + b.x;
+        vy = (double)w.y + b.y;
+    }
+    ep.v[m] = make_double2(vx + (double)sx, vy + (double)sy);
+}
+
 // Warp-per-node variants (grid zeroed by the caller before warp_spread); wtab: the
-// node window weights of node_weights, or null (computed per lane).
+// node window weights of node_weights, or null (computed per lane).  The spread reads
+// its forces as mu_t (tile order), or, when tperm is given, gathers them itself from
+// the body-order FP64 forces mu: node i of the tile order is mu[tperm[i]].
 template <typename T>
 void warp_spread(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const int2* tbase, const void* tfrac,
-                 const T* wtab, const void* mu_t, T* grid);
+                 const T* wtab, const void* mu_t, const double2* mu, const int* tperm, T* grid);
 template <typename T>
 void warp_interp(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const int2* tbase, const void* tfrac,
-                 const T* wtab, const T* grid, void* v_t);
+                 const T* wtab, const T* grid, void* v_t, const InterpEpilogue<T>& ep = InterpEpilogue<T>());
 // wtab[N][2][P]: every node's column and (times g0) row window weights.  One launch.
 template <typename T>
 void node_weights(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const void* tfrac, T* wtab);

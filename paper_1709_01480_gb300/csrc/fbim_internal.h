@@ -82,6 +82,11 @@ struct EwaldBuffers {
     bool pairs_df = false;
     float4* off_df = nullptr;    // [N] (x hi, x lo, y hi, y lo), cell-sorted
     float4* mu_df = nullptr;     // [N] forces, cell-sorted
+    // Alpert band of the FP32 operator in float-float (FP32 buffers only): the band
+    // [n_p][2 band + 1] as (hi of the 2x2 entries, lo of the 2x2 entries), and the
+    // forces rotated into their body's frame (x hi, x lo, y hi, y lo), body order
+    float4* band_df = nullptr;
+    float4* mu_rdf = nullptr;
     // piecewise tables of its pair values (e1_piecewise): [K] piece centres, then
     // [2][K][kPwDeg + 1] float-float coefficients (S, then e^{-z}) as (hi, lo)
     float* pw = nullptr;

@@ -221,7 +221,7 @@ __global__ void k_check_finite(int n, const double* __restrict__ x, int* __restr
 // writes one partial per dot; the sweep's last block to finish sums the partials
 // in a fixed order, so the result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-constexpr int CG_TB = 256, CG_EPT = 4, CG_CHUNK = CG_TB * CG_EPT, CG_KCH = 64, CG_JU = 4;
+constexpr int CG_TB = 256, CG_EPT = 4, CG_CHUNK = CG_TB * CG_EPT, CG_KCH = 64;
 
 __host__ __device__ inline int hist_stride(int m) { return 2 * (m + 1) + 2; }
 
@@ -239,32 +239,7 @@ __device__ __forceinline__ void cgs_block_dots(int n, int K, const double* __res
     const int KK = K > 0 ? K : 1;
     for (int j0 = 0; j0 < KK; j0 += CG_KCH) {
         const int j1 = min(KK, j0 + CG_KCH);
-        int j = j0;
-        if (K > 0) {
-            // CG_JU basis vectors at a time: their loads are in flight together (the
-            // sweep is bound by memory latency at this occupancy); each dot keeps the
-            // one-at-a-time order of its terms
-            for (; j + CG_JU <= j1; j += CG_JU) {
-                double s[CG_JU];
-#pragma unroll
-                for (int u = 0; u < CG_JU; ++u) s[u] = 0.0;
-#pragma unroll
-                for (int u = 0; u < CG_JU; ++u) {
-                    const double* v = V + (size_t)(j + u) * ld;
-#pragma unroll
-                    for (int e = 0; e < CG_EPT; ++e) {
-                        const int i = i0 + e * CG_TB;
-                        if (i < n) s[u] = fma(__ldcg(v + i), wv[e], s[u]);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < CG_JU; ++u) {
-                    s[u] = warp_sum(s[u]);
-                    if (lane == 0) red[j + u - j0][warp] = s[u];
-                }
-            }
-        }
-        for (; j < j1; ++j) {
+        for (int j = j0; j < j1; ++j) {
             double sacc = 0.0;
             if (K > 0) {
                 const double* v = V + (size_t)j * ld;
@@ -363,25 +338,7 @@ __global__ void __launch_bounds__(CG_TB) k_cgs_update(int n, int* __restrict__ k
         const int i = i0 + e * CG_TB;
         wv[e] = i < n ? w[i] : 0.0;
     }
-    int j = 0;
-    for (; j + CG_JU <= K; j += CG_JU) {  // CG_JU basis vectors' loads in flight, terms in order
-        double vv[CG_JU][CG_EPT], hv[CG_JU];
-#pragma unroll
-        for (int u = 0; u < CG_JU; ++u) {
-            const double* v = V + (size_t)(j + u) * ld;
-            hv[u] = hrow[j + u];
-#pragma unroll
-            for (int e = 0; e < CG_EPT; ++e) {
-                const int i = i0 + e * CG_TB;
-                vv[u][e] = i < n ? __ldcg(v + i) : 0.0;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < CG_JU; ++u)
-#pragma unroll
-            for (int e = 0; e < CG_EPT; ++e) wv[e] = fma(-vv[u][e], hv[u], wv[e]);
-    }
-    for (; j < K; ++j) {
+    for (int j = 0; j < K; ++j) {
         const double* v = V + (size_t)j * ld;
         const double hj = hrow[j];
 #pragma unroll

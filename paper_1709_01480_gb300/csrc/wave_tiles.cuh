@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(256) k_spread_warp(int N, int M, int P, int hw
                                                     const int2* __restrict__ tbase,
                                                     const typename V2<T>::type* __restrict__ tfrac,
                                                     const typename V2<T>::type* __restrict__ mu_t,
+                                                    const double2* __restrict__ mu_n, const int* __restrict__ tperm,
                                                     const T* __restrict__ wtab, T* __restrict__ grid) {
     const int lane = threadIdx.x & 31;
     const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
@@ -295,7 +296,13 @@ __global__ void __launch_bounds__(256) k_spread_warp(int N, int M, int P, int hw
     if (active) {
         b = tbase[i];
         if (!wtab) f = tfrac[i];
-        mu = mu_t[i];
+        if (tperm) {  // the gather into tile order, fused
+            const double2 u = mu_n[tperm[i]];
+            mu.x = (T)u.x;
+            mu.y = (T)u.y;
+        } else {
+            mu = mu_t[i];
+        }
     }
     T wx = T(0), wy = T(0);  // column weight of column p, row weight of row p
     if (active) {
@@ -332,7 +339,7 @@ __global__ void __launch_bounds__(256) k_interp_warp(int N, int M, int P, int hw
                                                     const int2* __restrict__ tbase,
                                                     const typename V2<T>::type* __restrict__ tfrac,
                                                     const T* __restrict__ wtab, const T* __restrict__ grid,
-                                                    typename V2<T>::type* __restrict__ v_t) {
+                                                    typename V2<T>::type* __restrict__ v_t, InterpEpilogue<T> ep) {
     const int lane = threadIdx.x & 31;
     const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const bool two = P <= 16;
@@ -381,10 +388,7 @@ __global__ void __launch_bounds__(256) k_interp_warp(int N, int M, int P, int hw
         sx += __shfl_xor_sync(0xffffffffu, sx, o, width);
         sy += __shfl_xor_sync(0xffffffffu, sy, o, width);
     }
-    if (p == 0 && i < N) {
-        v_t[i].x = sx;
-        v_t[i].y = sy;
-    }
+    if (p == 0 && i < N) interp_store<T>(ep, v_t, i, sx, sy);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,7 +435,8 @@ static __device__ __forceinline__ void vec_setup(int i, int N, int lane, int P, 
 
 static __global__ void __launch_bounds__(256) k_interp_vec(int N, int M, int P, int hw, float a, float q2, float g0,
                                                    const int2* __restrict__ tbase, const float2* __restrict__ tfrac,
-                                                   const float* __restrict__ grid, float2* __restrict__ v_t) {
+                                                   const float* __restrict__ grid, float2* __restrict__ v_t,
+                                                   InterpEpilogue<float> ep) {
     constexpr int HW = (kVecPMAX - 1) / 2;
     const int lane = threadIdx.x & 31;
     const int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 2);
@@ -459,7 +464,7 @@ static __global__ void __launch_bounds__(256) k_interp_vec(int N, int M, int P, 
     sy += __shfl_xor_sync(0xffffffffu, sy, 1);
     sx += __shfl_xor_sync(0xffffffffu, sx, 2);
     sy += __shfl_xor_sync(0xffffffffu, sy, 2);
-    if (active && (lane & 3) == 0) v_t[i] = make_float2(sx, sy);
+    if (active && (lane & 3) == 0) interp_store<float>(ep, v_t, i, sx, sy);
 }
 
 template <typename T>

@@ -87,24 +87,26 @@ static bool vec_ok(const TileGeom& tg, const void* grid) {
 
 template <>
 void warp_spread<float>(cudaStream_t st, int N, const TileGeom& tg, float a, float g0, const int2* tbase,
-                      const void* tfrac, const float* wtab, const void* mu_t, float* grid) {
+                      const void* tfrac, const float* wtab, const void* mu_t, const double2* mu, const int* tperm,
+                      float* grid) {
     using T2 = typename V2<float>::type;
     k_spread_warp<float><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
-                                                            (const T2*)mu_t, wtab, grid);
+                                                            (const T2*)mu_t, mu, tperm, wtab, grid);
 }
 
 template <>
 void warp_interp<float>(cudaStream_t st, int N, const TileGeom& tg, float a, float g0, const int2* tbase,
-                      const void* tfrac, const float* wtab, const float* grid, void* v_t) {
+                      const void* tfrac, const float* wtab, const float* grid, void* v_t,
+                      const InterpEpilogue<float>& ep) {
     using T2 = typename V2<float>::type;
     if (!wtab && vec_ok(tg, grid)) {
         const float q2 = (float)std::exp(-2.0 * (double)a);
         k_interp_vec<<<(unsigned)(((size_t)N * 4 + 255) / 256), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, q2, g0, tbase,
-                                                                            (const float2*)tfrac, grid, (float2*)v_t);
+                                                                            (const float2*)tfrac, grid, (float2*)v_t, ep);
         return;
     }
     k_interp_warp<float><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
-                                                            wtab, grid, (T2*)v_t);
+                                                            wtab, grid, (T2*)v_t, ep);
 }
 
 }  // namespace fbim

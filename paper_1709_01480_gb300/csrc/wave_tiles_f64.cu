@@ -80,18 +80,20 @@ static int warp_blocks(int N, int P) {
 
 template <>
 void warp_spread<double>(cudaStream_t st, int N, const TileGeom& tg, double a, double g0, const int2* tbase,
-                      const void* tfrac, const double* wtab, const void* mu_t, double* grid) {
+                      const void* tfrac, const double* wtab, const void* mu_t, const double2* mu, const int* tperm,
+                      double* grid) {
     using T2 = typename V2<double>::type;
     k_spread_warp<double><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
-                                                            (const T2*)mu_t, wtab, grid);
+                                                            (const T2*)mu_t, mu, tperm, wtab, grid);
 }
 
 template <>
 void warp_interp<double>(cudaStream_t st, int N, const TileGeom& tg, double a, double g0, const int2* tbase,
-                      const void* tfrac, const double* wtab, const double* grid, void* v_t) {
+                      const void* tfrac, const double* wtab, const double* grid, void* v_t,
+                      const InterpEpilogue<double>& ep) {
     using T2 = typename V2<double>::type;
     k_interp_warp<double><<<warp_blocks(N, tg.P), 256, 0, st>>>(N, tg.M, tg.P, tg.hw, a, g0, tbase, (const T2*)tfrac,
-                                                            wtab, grid, (T2*)v_t);
+                                                            wtab, grid, (T2*)v_t, ep);
 }
 
 template <>
