@@ -74,6 +74,19 @@ def test_invalid_arguments_are_rejected(fb):
         fb.choose_ewald(1.0, 0.6, 1e-8)      # r_c > L/3
     with pytest.raises(fb.FbimError):
         fb.choose_ewald(1.0, 0.2, 2.0)       # tol >= 1
+    # the Brownian dynamics position update checks its arguments before any CUDA call
+    lib = fb.lib()
+    inv = 1  # FBIM_ERR_INVALID_ARG
+    fake = 4096  # never dereferenced: every call below returns before touching memory
+    assert lib.fbim_bd_update(None, 3, 0.1, 0.0, None, None, None, fake) == inv      # no U
+    assert lib.fbim_bd_update(None, 3, 0.1, 0.0, fake, None, None, None) == inv      # no Q
+    assert lib.fbim_bd_update(None, 3, 0.1, 1.0, fake, fake, None, fake) == inv      # Up without Um
+    assert lib.fbim_bd_update(None, 3, float("nan"), 0.0, fake, None, None, fake) == inv
+    assert lib.fbim_bd_update(None, 1 << 40, 0.1, 0.0, fake, None, None, fake) == inv
+    assert lib.fbim_bd_update(None, 0, 0.1, 0.0, fake, None, None, fake) == 0       # nothing to do
+    # an unknown Brownian dynamics scheme (0 EM, 1 AB2, 2 EM without RFD) is rejected
+    assert lib.fbim_bd_step(fake, 3, fake, 0.1, 1.0, 1e-3, 0, 0, None, None, None, 1e-6, 1e-6, 10, fake, 0,
+                            fake, None) == inv
 
 
 def test_ctypes_structs_match_the_header_layout(fb, tmp_path):
