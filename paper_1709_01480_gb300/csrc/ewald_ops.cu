@@ -116,12 +116,49 @@ __global__ void __launch_bounds__(128) k_pair_count(int N, int n_box, T r_c, T r
     row_count[t] = n;
 }
 
-// slice_len[s] = longest row of the 32 targets in slice s (one warp per slice).
-__global__ void k_slice_len(int n_slice, int N, const int* __restrict__ row_count, int* __restrict__ slice_len) {
+// Rows sorted by length within windows of ROW_WINDOW consecutive (cell-sorted) rows, so
+// that the 32 rows of a slice have nearly equal lengths and the sliced-ELL padding
+// shrinks (sliced ELL with a sort window, "SELL-C-sigma").  One block per window: a
+// bitonic sort of (length descending, row ascending) in shared memory; row_of[p] is the
+// row at list position p (-1 past N), pos_of[t] the position of row t.  Positions p < N
+// always hold rows: a window's missing rows sort last.
+constexpr int ROW_WINDOW = 256;
+inline size_t row_windows(size_t N) { return (N + ROW_WINDOW - 1) / ROW_WINDOW; }
+__global__ void __launch_bounds__(ROW_WINDOW) k_sort_rows(int N, const int* __restrict__ row_count,
+                                                         int* __restrict__ row_of, int* __restrict__ pos_of) {
+    __shared__ unsigned long long key[ROW_WINDOW];
+    const int i = threadIdx.x, t = blockIdx.x * ROW_WINDOW + i;
+    const unsigned hi = t < N ? (1u << 30) - (unsigned)row_count[t] : 0xffffffffu;
+    key[i] = ((unsigned long long)hi << 32) | (unsigned)t;
+    __syncthreads();
+    for (int k = 2; k <= ROW_WINDOW; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int q = i ^ j;
+            if (q > i) {
+                const unsigned long long a = key[i], b = key[q];
+                const bool up = (i & k) == 0;
+                if ((a > b) == up) {
+                    key[i] = b;
+                    key[q] = a;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    const unsigned long long kv = key[i];
+    const int p = blockIdx.x * ROW_WINDOW + i;
+    const int row = (unsigned)(kv >> 32) == 0xffffffffu ? -1 : (int)(unsigned)(kv & 0xffffffffu);
+    row_of[p] = row;
+    if (row >= 0) pos_of[row] = p;
+}
+
+// slice_len[s] = longest row of the 32 positions in slice s (one warp per slice).
+__global__ void k_slice_len(int n_slice, int N, const int* __restrict__ row_count, const int* __restrict__ row_of,
+                            int* __restrict__ slice_len) {
     const int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (sl >= n_slice) return;
-    const int t = sl * 32 + lane;
-    int v = t < N ? row_count[t] : 0;
+    const int p = sl * 32 + lane;
+    int v = p < N ? row_count[row_of[p]] : 0;
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (lane == 0) slice_len[sl] = v;
 }
@@ -132,11 +169,11 @@ template <typename T>
 __global__ void __launch_bounds__(128) k_pair_fill(int N, int n_box, T r_c, T rc2, const int* __restrict__ perm,
                                                   const int* __restrict__ cell, const int* __restrict__ start,
                                                   const typename V2<T>::type* __restrict__ off,
-                                                  const int* __restrict__ slice_start,
+                                                  const int* __restrict__ slice_start, const int* __restrict__ pos_of,
                                                   PairEntry<T>* __restrict__ pairs) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
-    const int sl = t >> 5, lane = t & 31;
+    const int p = pos_of[t], sl = p >> 5, lane = p & 31;
     const int base = slice_start[sl], len = slice_start[sl + 1] - base;
     PairEntry<T>* row = pairs + (size_t)base * 32 + lane;
     int k = 0;
@@ -177,12 +214,13 @@ __device__ __forceinline__ void pair_value(T rx, T ry, T xi2, T pref, const Cheb
 // the sliced-ELL padding idles no lane of the transcendental work.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pair_eval_rows(int N, const int* __restrict__ slice_start,
-                                                       const int* __restrict__ row_count, T xi2, T pref,
+                                                       const int* __restrict__ row_count,
+                                                       const int* __restrict__ pos_of, T xi2, T pref,
                                                        ChebE1<T> ce, PairEntry<T>* __restrict__ pairs) {
     const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (t >= N) return;
-    const int n = row_count[t];
-    PairEntry<T>* row = pairs + (size_t)slice_start[t >> 5] * 32 + (t & 31);
+    const int n = row_count[t], p = pos_of[t];
+    PairEntry<T>* row = pairs + (size_t)slice_start[p >> 5] * 32 + (p & 31);
     for (int k = lane; k < n; k += 32) {
         PairEntry<T> e = row[(size_t)k * 32];
         T xx, xy, yy;
@@ -236,6 +274,7 @@ __global__ void __launch_bounds__(256) k_pair_from32(int N, int n_box, dfl::df r
                                                     const int* __restrict__ cell, const float4* __restrict__ off,
                                                     const int* __restrict__ slice_start,
                                                     const int* __restrict__ row_count,
+                                                    const int* __restrict__ pos_of,
                                                     const PairEntry<float>* __restrict__ p32, dfl::df xi2,
                                                     dfl::df pref, const float* __restrict__ pw, int K, float inv_w,
                                                     float kscale, PairEntryDF* __restrict__ p64) {
@@ -248,10 +287,11 @@ __global__ void __launch_bounds__(256) k_pair_from32(int N, int n_box, dfl::df r
     const float2* cE = cS + K * (kPwDeg + 1);
     const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
     for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < N; t += gridDim.x * warps) {
-        const int sl = t >> 5, base = slice_start[sl], len = slice_start[sl + 1] - base, n = row_count[t];
+        const int p = pos_of[t], sl = p >> 5, base = slice_start[sl], len = slice_start[sl + 1] - base;
+        const int n = row_count[t];
         const int ct = cell[perm[t]], cxt = ct % n_box, cyt = ct / n_box;
         const float4 ot = off[t];
-        const size_t r0 = (size_t)base * 32 + (t & 31);
+        const size_t r0 = (size_t)base * 32 + (p & 31);
         for (int k = lane; k < len; k += 32) {
             PairEntryDF e;
             if (k < n) {
@@ -294,12 +334,13 @@ __global__ void k_off_df(int N, const double2* __restrict__ off, float4* __restr
 // the sum rounded to FP64 once per row.  Same row order and U-wide batching as
 // k_pair_spmv; nothing on the FP64 pipe but that final conversion.
 __global__ void __launch_bounds__(256) k_pair_spmv_df(int N, const int* __restrict__ slice_start,
+                                                     const int* __restrict__ row_of,
                                                      const PairEntryDF* __restrict__ pairs,
                                                      const float4* __restrict__ mu_df, double2* __restrict__ v_s) {
     constexpr int U = 4;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
-    const int sl = t >> 5, lane = t & 31;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;  // list position
+    if (p >= N) return;
+    const int sl = p >> 5, lane = p & 31;
     const int base = slice_start[sl], len = slice_start[sl + 1] - base;
     const PairEntryDF* row = pairs + (size_t)base * 32 + lane;
     dfl::df ax = {0.0f, 0.0f}, ay = {0.0f, 0.0f};
@@ -329,7 +370,7 @@ __global__ void __launch_bounds__(256) k_pair_spmv_df(int N, const int* __restri
             }
         }
     }
-    v_s[t] = make_double2(dfl::to_double(ax), dfl::to_double(ay));
+    v_s[row_of[p]] = make_double2(dfl::to_double(ax), dfl::to_double(ay));
 }
 
 // ---------------------------------------------------------------------------
@@ -493,6 +534,9 @@ static fbim_status build_pairs_from32(fbim_handle_s* h) {
     }
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.slice_start, f.slice_start, sizeof(int) * (n_slice + 1),
                                      cudaMemcpyDeviceToDevice, h->stream));
+    // the same positions as the FP32 list (rows sorted by length within windows)
+    FBIM_CUDA_TRY(h, cudaMemcpyAsync(e.row_of, f.row_of, sizeof(int) * (row_windows(N) * ROW_WINDOW + N),
+                                     cudaMemcpyDeviceToDevice, h->stream));
     if (!e.off_df) {
         FBIM_CUDA_TRY(h, cudaMalloc(&e.off_df, (size_t)N * sizeof(float4)));
         FBIM_CUDA_TRY(h, cudaMalloc(&e.mu_df, (size_t)N * sizeof(float4)));
@@ -537,7 +581,7 @@ static fbim_status build_pairs_from32(fbim_handle_s* h) {
     const unsigned blocks = (unsigned)std::min<long long>(((long long)N + 7) / 8, (long long)std::max(per_sm, 1) * sms);
     k_pair_from32<<<blocks, 256, smem, h->stream>>>(
         N, h->n_box, dfl::from_double(h->r_c), h->perm, h->cell, e.off_df, f.slice_start, f.row_count,
-        (const PairEntry<float>*)f.pairs, dfl::from_double(h->xi * h->xi),
+        f.row_of + row_windows(N) * ROW_WINDOW, (const PairEntry<float>*)f.pairs, dfl::from_double(h->xi * h->xi),
         dfl::from_double(1.0 / (4.0 * M_PI * h->eta)), e.pw, e.pw_K, e.pw_inv_w, e.pw_kscale, (PairEntryDF*)e.pairs);
     h->launches += 2;
     FBIM_CUDA_TRY(h, cudaGetLastError());
@@ -559,9 +603,12 @@ static fbim_status build_pairs(fbim_handle_s* h) {
     const T rc = (T)h->r_c, rc2 = (T)(h->r_c * h->r_c);
     k_pair_count<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, h->perm, h->cell, h->cell_start,
                                                             (const T2*)e.off, e.row_count, h->flags);
-    // slice lengths (one warp per slice) into slice_start, then an exclusive scan in place
+    // rows sorted by length within windows; slice lengths (one warp per slice) into
+    // slice_start, then an exclusive scan in place
+    int* pos_of = e.row_of + row_windows(N) * ROW_WINDOW;
+    k_sort_rows<<<(unsigned)row_windows(N), ROW_WINDOW, 0, h->stream>>>(N, e.row_count, e.row_of, pos_of);
     k_slice_len<<<(unsigned)(((size_t)n_slice * 32 + 255) / 256), 256, 0, h->stream>>>(n_slice, N, e.row_count,
-                                                                                        e.row_count + N);
+                                                                                        e.row_of, e.row_count + N);
     scan_exclusive(h->stream, e.row_count + N, n_slice, e.slice_start);
     int total = 0;
     FBIM_CUDA_TRY(h, cudaMemcpyAsync(&total, e.slice_start + n_slice, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -576,10 +623,11 @@ static fbim_status build_pairs(fbim_handle_s* h) {
     }
     const T pref = (T)(1.0 / (4.0 * M_PI * h->eta));
     k_pair_fill<T><<<(N + 127) / 128, 128, 0, h->stream>>>(N, h->n_box, rc, rc2, h->perm, h->cell, h->cell_start,
-                                                           (const T2*)e.off, e.slice_start, (PairEntry<T>*)e.pairs);
+                                                           (const T2*)e.off, e.slice_start, pos_of,
+                                                           (PairEntry<T>*)e.pairs);
     k_pair_eval_rows<T><<<(unsigned)(((size_t)N * 32 + 255) / 256), 256, 0, h->stream>>>(
-        N, e.slice_start, e.row_count, (T)(h->xi * h->xi), pref, cheb<T>(h), (PairEntry<T>*)e.pairs);
-    h->launches += 4;
+        N, e.slice_start, e.row_count, pos_of, (T)(h->xi * h->xi), pref, cheb<T>(h), (PairEntry<T>*)e.pairs);
+    h->launches += 5;
     FBIM_CUDA_TRY(h, cudaGetLastError());
     e.n_padded = (long long)total * 32;
     e.pairs_df = false;
@@ -697,6 +745,7 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     FBIM_CUDA_TRY(h, cudaMalloc(&e.spec, 2 * M * Mh * sizeof(C)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, scan_storage((int)n_slice) * sizeof(int)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.row_count, (n_slice * 33 + 1) * sizeof(int)));
+    FBIM_CUDA_TRY(h, cudaMalloc(&e.row_of, (row_windows(N) * ROW_WINDOW + N) * sizeof(int)));
     int n[2] = {(int)M, (int)M};
     int inembed[2] = {(int)M, (int)M};
     int onembed[2] = {(int)M, (int)Mh};
@@ -742,11 +791,12 @@ template <typename T>
 static void pair_product(cudaStream_t st, int N, EwaldBuffers<T>& e, bool df) {
     using T2 = typename V2<T>::type;
     if (df)
-        k_pair_spmv_df<<<(N + 63) / 64, 64, 0, st>>>(N, e.slice_start, (const PairEntryDF*)e.pairs, e.mu_df,
-                                                     (double2*)e.v_s);
+        k_pair_spmv_df<<<(N + 63) / 64, 64, 0, st>>>(N, e.slice_start, e.row_of, (const PairEntryDF*)e.pairs,
+                                                     e.mu_df, (double2*)e.v_s);
     else
-        k_pair_spmv<T><<<(N + 31) / 32, 32 * SPMV_P, 0, st>>>(N, e.slice_start, (const PairEntry<T>*)e.pairs,
-                                                              (const T2*)e.mu_s, (T2*)e.v_s);
+        k_pair_spmv<T><<<(N + 31) / 32, 32 * SPMV_P, 0, st>>>(N, e.slice_start, e.row_of,
+                                                              (const PairEntry<T>*)e.pairs, (const T2*)e.mu_s,
+                                                              (T2*)e.v_s);
 }
 
 template <typename T>
@@ -997,6 +1047,7 @@ static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.pw);
     cudaFree(e.slice_start);
     cudaFree(e.row_count);
+    cudaFree(e.row_of);
     if (e.plan_f) cufftDestroy(e.plan_f);
     if (e.plan_i) cufftDestroy(e.plan_i);
     e = EwaldBuffers<T>();

@@ -72,6 +72,9 @@ struct EwaldBuffers {
     void* pairs = nullptr;       // entries [slice_start[s] + k][32]: G tensor (xx, xy, yy) and source slot
     int* slice_start = nullptr;  // [n_slice + 1] entry offsets (in units of 32 entries)
     int* row_count = nullptr;    // [n_slice * 32] hits per target
+    int* row_of = nullptr;       // [n_win * 256] row at each list position (-1 past N), then
+                                 // [N] the list position of each row (rows sorted by length
+                                 // within windows of 256)
     size_t pair_cap = 0;         // allocated entries (units of 32)
     long long n_pairs = 0;       // ordered pairs within r_c (without padding)
     long long n_padded = 0;      // stored entries including padding

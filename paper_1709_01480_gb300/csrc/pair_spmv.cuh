@@ -1,7 +1,9 @@
 // Real-space pair list and its product (Sec. 3.2, Eq. Mreal-decompose: the sum over
-// node pairs within r_c).  The list is sliced ELL: slices of 32 target rows, entries
-// [slice][k][32] of the 2x2 kernel value (xx, xy, yy) and the source slot.  Its own
-// header so that the measured DRAM traffic of the product can be tied to this source.
+// node pairs within r_c).  The list is sliced ELL over list positions: the cell-sorted
+// target rows are sorted by length within windows of 256 (row_of / pos_of), slices of
+// 32 positions, entries [slice][k][32] of the 2x2 kernel value (xx, xy, yy) and the
+// source slot.  Its own header so that the measured DRAM traffic of the product can be
+// tied to this source.
 #pragma once
 #include "fbim_internal.h"
 #include "ewald_types.cuh"
@@ -37,7 +39,9 @@ __device__ __forceinline__ PairEntry<double> ld_entry(const PairEntry<double>* p
     return e;
 }
 
-// v_s[t] = sum_k pairs[t][k] mu_s[src]: one block per 32-row slice, SPMV_P warps
+// v_s[row_of[p]] = sum_k pairs[p][k] mu_s[src] over list positions p (rows sorted by
+// length within windows, so a slice's rows have nearly equal lengths): one block per
+// 32-position slice, SPMV_P warps
 // over each row's entries (warp p takes k = p, p + SPMV_P, ..., so that a warp still
 // reads 32 consecutive entries), each thread taking its entries U at a time (U
 // independent list loads, then U independent gathers) to keep several memory
@@ -45,6 +49,7 @@ __device__ __forceinline__ PairEntry<double> ld_entry(const PairEntry<double>* p
 constexpr int SPMV_P = 4;
 template <typename T>
 __global__ void __launch_bounds__(32 * SPMV_P) k_pair_spmv(int N, const int* __restrict__ slice_start,
+                                                           const int* __restrict__ row_of,
                                                            const PairEntry<T>* __restrict__ pairs,
                                                            const typename V2<T>::type* __restrict__ mu_s,
                                                            typename V2<T>::type* __restrict__ v_s) {
@@ -52,9 +57,9 @@ __global__ void __launch_bounds__(32 * SPMV_P) k_pair_spmv(int N, const int* __r
     using T2 = typename V2<T>::type;
     __shared__ T2 red[SPMV_P][32];
     const int sl = blockIdx.x, lane = threadIdx.x & 31, part = threadIdx.x >> 5;
-    const int t = sl * 32 + lane;
+    const int t = sl * 32 + lane;  // list position; the row is row_of[t]
     T ax = 0, ay = 0;
-    if (t < N) {  // the slice's rows past N have no entries
+    if (t < N) {  // the slice's positions past N have no entries
         const int base = slice_start[sl], len = slice_start[sl + 1] - base;
         const PairEntry<T>* row = pairs + (size_t)base * 32 + lane;
         int k = part;
@@ -88,8 +93,9 @@ __global__ void __launch_bounds__(32 * SPMV_P) k_pair_spmv(int N, const int* __r
             sx += red[p][lane].x;
             sy += red[p][lane].y;
         }
-        v_s[t].x = sx;
-        v_s[t].y = sy;
+        const int r = row_of[t];
+        v_s[r].x = sx;
+        v_s[r].y = sy;
     }
 }
 
