@@ -20,7 +20,9 @@ previous step's N F is carried over, and the first step uses N^n F^n for both
 Parity: pinned by what Sec. 4.4 fixes about the step: the RFD term's expectation
 over W~ equals dt kT (d/dQ . N) (checked against central differences of this
 package's N), at fixed W~ it tends to dt kT (D_W~ N) W~ as delta -> 0 at second
-order, and the deterministic part is dt N F.  ``ab2_rfd_step`` is pinned by the
+order, and the deterministic part is dt N F.  ``em_no_rfd_step`` (Eq. EM-noRFD) is
+pinned by reducing to dt N F without noise and to ``em_rfd_step`` at W~ = 0 with it.
+``ab2_rfd_step`` is pinned by the
 order of its deterministic part: on a two-body spring problem at kT = 0 its
 trajectory converges at second order in dt where the Euler step converges at first.
 """

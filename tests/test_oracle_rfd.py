@@ -113,6 +113,26 @@ def test_deterministic_part_is_dt_N_F():
     assert np.max(np.abs(got - expect)) < 1e-12 * np.max(np.abs(Q))
 
 
+def test_biased_step_is_the_rfd_step_without_its_drift():
+    """Eq. EM-noRFD: the Euler-Maruyama step without the random finite difference.  With
+    zero noise it is Q + dt N F; with noise it equals the EM-RFD step at W~ = 0 (whose
+    difference term then vanishes), the slip entering the same saddle solve."""
+    ref, Q = _case()
+    F = fbim_synth.random_forces(2, seed=5, net_zero=False)
+    dt, kT = 0.01, 1.3
+    W_r, Z = _zero_noise(Q.shape[0] * N_P)
+    got = rfd.em_no_rfd_step(Q, ref, L, XI, F, dt, kT, W_r, Z)
+    expect = Q + dt * (_mobility(Q, ref) @ F.reshape(-1)).reshape(-1, 3)
+    assert np.max(np.abs(got - expect)) < 1e-12 * np.max(np.abs(Q))
+    rng = np.random.default_rng(6)
+    W_r = rng.standard_normal((Q.shape[0] * N_P, 2))
+    Z = rng.standard_normal((16, 16, 2, 2))
+    got = rfd.em_no_rfd_step(Q, ref, L, XI, F, dt, kT, W_r, Z)
+    ref_step = rfd.em_rfd_step(Q, ref, L, XI, F, dt, kT, 1e-3, W_r, Z, np.zeros(Q.size))
+    assert np.max(np.abs(got - ref_step)) < 1e-13 * np.max(np.abs(Q))
+    assert np.max(np.abs(got - expect)) > 1e-6     # the noise moved the bodies
+
+
 def _spring_force(Q):
     """Forces and torques of a spring between the two tracking points (rest length 1.5,
     stiffness 40) and angular springs to pi/4 and pi/2 (stiffness 2): F = -dU/dQ."""
