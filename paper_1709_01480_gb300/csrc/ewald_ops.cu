@@ -650,7 +650,7 @@ fbim_status refresh_offsets(fbim_handle_s* h) {
             const TileGeom tg{h->M, h->TS, h->n_tile, e.P, (e.P - 1) / 2};
             const double alpha = 2.0 * h->xi * h->xi / e.eta_s;
             node_weights<double>(h->stream, h->N, tg, alpha * h->h * h->h, 2.0 * h->xi * h->xi / (M_PI * e.eta_s),
-                                 e.tfrac, e.wtab);
+                                 e.tfrac, e.wtab, e.wtab_df);
             h->launches += 1;
         }
     }
@@ -742,6 +742,9 @@ fbim_status ensure_ewald(fbim_handle_s* h) {
     }
     FBIM_CUDA_TRY(h, cudaMalloc(&e.grid, 2 * M * M * sizeof(T)));
     if (std::is_same<T, double>::value) FBIM_CUDA_TRY(h, cudaMalloc(&e.wtab, N * 2 * e.P * sizeof(T)));
+    // the FP64 operator of an FP32 handle interpolates in float-float (weights as pairs)
+    if (std::is_same<T, double>::value && h->precision == FBIM_FP32)
+        FBIM_CUDA_TRY(h, cudaMalloc(&e.wtab_df, N * 2 * e.P * sizeof(float2)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.spec, 2 * M * Mh * sizeof(C)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.slice_start, scan_storage((int)n_slice) * sizeof(int)));
     FBIM_CUDA_TRY(h, cudaMalloc(&e.row_count, (n_slice * 33 + 1) * sizeof(int)));
@@ -815,7 +818,12 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
     // the warp spread gathers its forces itself; the warp interpolation writes the sum in
     // body order itself (after the real space has joined), so gather and finish drop out
     const bool spread_gathers = wave && e.spread_variant == 1;
-    const bool fused_out = wave && e.interp_variant == 1 && !h->timing && (fork || !real);
+    // the FP64 operator of an FP32 handle: float-float transforms and scale, and the
+    // float-float interpolation from the transform's float-float output
+    bool own_fft = false;
+    if constexpr (std::is_same<T, double>::value) own_fft = wave && h->fft64.state == 1;
+    const bool df_interp = own_fft && e.wtab_df;
+    const bool fused_out = wave && (e.interp_variant == 1 || df_interp) && !h->timing && (fork || !real);
     const cudaStream_t rs = fork ? h->aux : h->stream;
     if (fork) {
         FBIM_CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
@@ -854,15 +862,13 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
             tile_spread<T>(h->stream, tg, ah2, g0, h->tile_start, e.tbase, e.tfrac, e.mu_t, e.grid, e.ring);
         }
         h->mark(FBIM_ST_SPREAD);
-        bool own_fft = false;  // float-float transforms and scale (FP64 operator of an FP32 handle)
         if constexpr (std::is_same<T, double>::value) {
-            own_fft = h->fft64.state == 1;
             if (own_fft) {
                 wfft_forward(h, h->stream, e.grid);
                 h->mark(FBIM_ST_FFT_F);
                 wfft_scale(h, h->stream);
                 h->mark(FBIM_ST_SCALE);
-                wfft_inverse(h, h->stream, e.grid);
+                wfft_inverse(h, h->stream, e.grid, df_interp);
                 h->mark(FBIM_ST_FFT_I);
                 h->launches += 2;
             }
@@ -886,6 +892,16 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
         h->mark(FBIM_ST_PAIRS);
     }
     if (wave) {
+        // warp interpolation, in float-float for the FP64 operator of an FP32 handle
+        auto warp_interp_any = [&](const InterpEpilogue<T>& ep) {
+            if constexpr (std::is_same<T, double>::value) {
+                if (df_interp) {
+                    interp_df(h->stream, N, tg, e.tbase, e.wtab_df, e.grid, e.v_t, ep);
+                    return;
+                }
+            }
+            warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t, ep);
+        };
         if (fused_out) {
             if (fork) FBIM_CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
             InterpEpilogue<T> ep;
@@ -896,7 +912,9 @@ fbim_status apply_operator(fbim_handle_s* h, const double* mu, double* v, int wh
                 ep.v_s = (const T2*)e.v_s;
                 ep.v_band = e.v_band;
             }
-            warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t, ep);
+            warp_interp_any(ep);
+        } else if (df_interp) {
+            warp_interp_any(InterpEpilogue<T>());
         } else if (e.interp_variant == 1) {
             warp_interp<T>(h->stream, N, tg, ah2, g0, e.tbase, e.tfrac, e.wtab, e.grid, e.v_t);
         } else {
@@ -1038,6 +1056,7 @@ static void free_one(EwaldBuffers<T>& e) {
     cudaFree(e.ring);
     cudaFree(e.grid);
     cudaFree(e.wtab);
+    cudaFree(e.wtab_df);
     cudaFree(e.spec);
     cudaFree(e.pairs);
     cudaFree(e.off_df);

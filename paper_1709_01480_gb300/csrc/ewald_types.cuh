@@ -175,8 +175,15 @@ void warp_spread(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const in
 template <typename T>
 void warp_interp(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const int2* tbase, const void* tfrac,
                  const T* wtab, const T* grid, void* v_t, const InterpEpilogue<T>& ep = InterpEpilogue<T>());
-// wtab[N][2][P]: every node's column and (times g0) row window weights.  One launch.
+// wtab[N][2][P]: every node's column and (times g0) row window weights, and (wdf not
+// null) the same as float-float pairs.  One launch.
 template <typename T>
-void node_weights(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const void* tfrac, T* wtab);
+void node_weights(cudaStream_t st, int N, const TileGeom& tg, T a, T g0, const void* tfrac, T* wtab,
+                  float2* wdf = nullptr);
+// Interpolation of the FP64 operator of an FP32 handle in float-float arithmetic: the
+// grid holds float-float pairs (wfft_inverse with df_out), the weights come from wdf;
+// the warp-per-node layout of warp_interp, its output (tile order or the epilogue) in FP64.
+void interp_df(cudaStream_t st, int N, const TileGeom& tg, const int2* tbase, const float2* wdf, const double* grid,
+               void* v_t, const InterpEpilogue<double>& ep);
 
 }  // namespace fbim

@@ -65,6 +65,7 @@ struct EwaldBuffers {
     T* ring = nullptr;       // [n_tile^2][2][W][W] halo rings of the tile spread (W = TS + P - 1)
     T* grid = nullptr;       // [2][M][M] real grid (component-major)
     T* wtab = nullptr;       // [N][2][P] node window weights, tile-sorted (FP64 buffers only)
+    float2* wtab_df = nullptr;  // the same weights as float-float pairs (FP64 buffers of FP32 handles)
     void* spec = nullptr;    // [2][M][M/2+1] complex half spectrum
     cufftHandle plan_f = 0;  // R2C / D2Z, batch 2
     cufftHandle plan_i = 0;  // C2R / Z2D, batch 2
@@ -302,6 +303,7 @@ fbim_status wfft_setup(fbim_handle_s* h);
 void wfft_free(fbim_handle_s* h);
 void wfft_forward(fbim_handle_s* h, cudaStream_t st, const double* grid);
 void wfft_scale(fbim_handle_s* h, cudaStream_t st);
-void wfft_inverse(fbim_handle_s* h, cudaStream_t st, double* grid);
+// df_out: the grid values as float-float pairs (float2 in each double's place)
+void wfft_inverse(fbim_handle_s* h, cudaStream_t st, double* grid, bool df_out = false);
 
 }  // namespace fbim

@@ -275,11 +275,12 @@ __global__ void __launch_bounds__(kThreads) k_fft_y_scale(FftPlan p, const typen
 }
 
 // T2 columns y0 .. y0 + RB - 1 -> inverse FFT over x -> grid rows (real part ->
-// component 0, imaginary part -> component 1)
+// component 0, imaginary part -> component 1); df_out: each value stored as its
+// float-float pair (hi, lo) in the grid value's 8 bytes instead of rounded to FP64
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_fft_x_inv(FftPlan p, const typename A::W* __restrict__ tw,
                                                        const typename A::S* __restrict__ T2,
-                                                       typename A::G* __restrict__ grid) {
+                                                       typename A::G* __restrict__ grid, int df_out) {
     using S = typename A::S;
     constexpr int RB = A::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -295,10 +296,17 @@ __global__ void __launch_bounds__(kThreads) k_fft_x_inv(FftPlan p, const typenam
     const S* r = fft_lines<A>(b0, b1, p, RB, tw, 1.0f);
     for (int e = threadIdx.x; e < RB * M; e += blockDim.x) {
         const size_t g = (size_t)y0 * M + e;
-        typename A::G a, c;
-        A::to_grid(A::ld(r[e]), a, c);
-        grid[g] = a;
-        grid[MM + g] = c;
+        if (df_out) {
+            const typename A::C v = A::ld(r[e]);
+            float2* gf = reinterpret_cast<float2*>(grid);
+            gf[g] = make_float2(v.re.hi, v.re.lo);
+            gf[MM + g] = make_float2(v.im.hi, v.im.lo);
+        } else {
+            typename A::G a, c;
+            A::to_grid(A::ld(r[e]), a, c);
+            grid[g] = a;
+            grid[MM + g] = c;
+        }
     }
 }
 
@@ -434,11 +442,12 @@ void wfft_scale(fbim_handle_s* h, cudaStream_t st) {
                                                              (const A::S*)d.T1, (A::S*)d.T2);
 }
 
-void wfft_inverse(fbim_handle_s* h, cudaStream_t st, double* grid) {
+void wfft_inverse(fbim_handle_s* h, cudaStream_t st, double* grid, bool df_out) {
     using A = ArD;
     const WaveFft& d = h->fft64;
     const int M = d.plan.M;
-    k_fft_x_inv<A><<<M / A::RB, kThreads, smem_x<A>(M), st>>>(d.plan, (const A::W*)d.tw, (const A::S*)d.T2, grid);
+    k_fft_x_inv<A><<<M / A::RB, kThreads, smem_x<A>(M), st>>>(d.plan, (const A::W*)d.tw, (const A::S*)d.T2, grid,
+                                                             df_out ? 1 : 0);
 }
 
 }  // namespace fbim

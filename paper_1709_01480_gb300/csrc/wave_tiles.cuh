@@ -256,9 +256,11 @@ __global__ void __launch_bounds__(256) k_interp_tiles(TileGeom tg, T a, T q2, T 
 // wtab[i][1][p] = g0 w(p - hw - f_y), p < P, by the recurrence above (three
 // exponentials per dimension).  The FP64 warp kernels read them instead of taking
 // two FP64 exponentials per lane, which the FP64 pipe makes their largest cost.
+// wdf (or null): the same weights as float-float pairs (hi = the FP32 rounding, lo =
+// the FP32 rounding of the remainder), for the float-float interpolation.
 template <typename T, int PMAX>
 __global__ void k_node_weights(int N, int P, int hw, T a, T q2, T g0, const typename V2<T>::type* __restrict__ tfrac,
-                               T* __restrict__ wtab) {
+                               T* __restrict__ wtab, float2* __restrict__ wdf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
     constexpr int HW = (PMAX - 1) / 2;
@@ -274,6 +276,14 @@ __global__ void k_node_weights(int N, int P, int hw, T a, T q2, T g0, const type
 #pragma unroll
     for (int j = 0; j < PMAX; ++j)
         if (j >= shift && j < shift + P) out[P + j - shift] = w[j];
+    if (wdf) {
+        float2* od = wdf + (size_t)i * 2 * P;
+        for (int j = 0; j < 2 * P; ++j) {
+            const double v = (double)out[j];
+            const float hi = (float)v;
+            od[j] = make_float2(hi, (float)(v - (double)hi));
+        }
+    }
 }
 
 // wtab: the node weights above, or null to compute them per lane.
