@@ -292,18 +292,39 @@ class FBIM:
         import torch
         return torch.empty(shape, dtype=torch.float64, device=like.device)
 
+    def _vec(self, t, numel, name):
+        """The library receives bare pointers: check that t is a contiguous float64 CUDA
+        tensor of numel entries on the handle's device (raw integer addresses pass as
+        given).  Returns t."""
+        if t is None or isinstance(t, int):
+            return t
+        import torch
+        if (not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_contiguous()
+                or t.device.type != "cuda" or t.device.index not in (None, self.device)
+                or (numel is not None and t.numel() != numel)):
+            what = f"{t.dtype} {tuple(t.shape)} on {t.device}" if isinstance(t, torch.Tensor) else type(t).__name__
+            raise FbimError(1, f"{name}: expected a contiguous float64 tensor of {numel} entries on "
+                               f"cuda:{self.device}, got {what}")
+        return t
+
     def apply_stokeslet(self, mu, out=None):
+        self._vec(mu, 2 * self.n, "mu")
+        self._vec(out, 2 * self.n, "out")
         v = out if out is not None else self._out(mu, (self.n, 2))
         _check(_lib.fbim_apply_stokeslet(self._h, _ptr(mu), _ptr(v)), self._h)
         return v
 
     def apply_stokeslet_fp64(self, mu, out=None):
         """The FP64 operator of the refinement residuals (FP64 whatever the handle's precision)."""
+        self._vec(mu, 2 * self.n, "mu")
+        self._vec(out, 2 * self.n, "out")
         v = out if out is not None else self._out(mu, (self.n, 2))
         _check(_lib.fbim_apply_stokeslet_fp64(self._h, _ptr(mu), _ptr(v)), self._h)
         return v
 
     def apply_real(self, mu, out=None):
+        self._vec(mu, 2 * self.n, "mu")
+        self._vec(out, 2 * self.n, "out")
         v = out if out is not None else self._out(mu, (self.n, 2))
         _check(_lib.fbim_apply_real(self._h, _ptr(mu), _ptr(v)), self._h)
         return v
@@ -326,6 +347,8 @@ class FBIM:
         return out
 
     def apply_wave(self, mu, out=None):
+        self._vec(mu, 2 * self.n, "mu")
+        self._vec(out, 2 * self.n, "out")
         v = out if out is not None else self._out(mu, (self.n, 2))
         _check(_lib.fbim_apply_wave(self._h, _ptr(mu), _ptr(v)), self._h)
         return v
@@ -333,6 +356,8 @@ class FBIM:
     def mobility_solve(self, F, slip=None, tol=1e-6, max_iter=500, want_mu=False, check=True):
         """Solve the saddle system; returns (U [n_b, 3], mu or None, iterations, relative residual)."""
         import torch
+        self._vec(F, 3 * self.n_b, "F")
+        self._vec(slip, 2 * self.n, "slip")
         U = torch.empty((self.n_b, 3), dtype=torch.float64, device=F.device)
         mu = torch.empty((self.n, 2), dtype=torch.float64, device=F.device) if want_mu else None
         it = ctypes.c_int(0)
@@ -347,6 +372,8 @@ class FBIM:
     def brownian_slip(self, kT=1.0, dt=1.0, W_r=None, Z_w=None, seed=0, counter=0, tol=1e-6, max_iter=200):
         """Random slip [N, 2]; returns (slip, Lanczos iterations)."""
         import torch
+        self._vec(W_r, 2 * self.n, "W_r")
+        self._vec(Z_w, None, "Z_w")
         dev = W_r.device if W_r is not None else torch.device("cuda", self.device)
         out = torch.empty((self.n, 2), dtype=torch.float64, device=dev)
         it = ctypes.c_int(0)
@@ -358,6 +385,9 @@ class FBIM:
     def rfd_step(self, F, Q, dt, kT=1.0, delta=1e-3, seed=0, step=0, W_r=None, Z_w=None, W_t=None, tol=1e-6,
                  max_iter=500):
         """One EM-RFD step; Q (device [n_b, 3]) is updated in place.  Returns the GMRES iterations."""
+        for t, k, name in ((F, 3 * self.n_b, "F"), (Q, 3 * self.n_b, "Q"), (W_r, 2 * self.n, "W_r"),
+                           (Z_w, None, "Z_w"), (W_t, 3 * self.n_b, "W_t")):
+            self._vec(t, k, name)
         it = ctypes.c_int(0)
         opt = lambda t: None if t is None else _ptr(t)
         _check(_lib.fbim_rfd_step(self._h, _ptr(F), float(dt), float(kT), float(delta), int(seed), int(step),
@@ -371,6 +401,9 @@ class FBIM:
         without the stochastic drift); Q is updated in place.  For "ab2", NF (device [n_b, 3])
         carries N F between steps (read when have_prev, written always).  Returns the GMRES
         iterations of the step's solves."""
+        for t, k, name in ((F, 3 * self.n_b, "F"), (Q, 3 * self.n_b, "Q"), (W_r, 2 * self.n, "W_r"),
+                           (Z_w, None, "Z_w"), (W_t, 3 * self.n_b, "W_t"), (NF, 3 * self.n_b, "NF")):
+            self._vec(t, k, name)
         it = ctypes.c_int(0)
         opt = lambda t: None if t is None else _ptr(t)
         sch = {"em": 0, "ab2": 1, "em_no_rfd": 2}[scheme]

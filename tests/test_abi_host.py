@@ -115,3 +115,25 @@ def test_ctypes_structs_match_the_header_layout(fb, tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(cls), cname
         for fname, _ in cls._fields_:
             assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_binding_checks_tensors_before_calling_the_library(fb):
+    """The binding hands bare pointers to the library: a tensor of the wrong type, size,
+    layout or device is refused on the host, before any library call (the handle below
+    does not exist, so reaching the library would fail differently)."""
+    import torch
+    op = fb.FBIM.__new__(fb.FBIM)
+    op.n_b, op.n_p, op.device, op._h = 2, 4, 0, None
+    bad = [torch.zeros((8, 2), dtype=torch.float32),          # FP32
+           torch.zeros((8, 2), dtype=torch.float64),          # host memory
+           torch.zeros((2, 8), dtype=torch.float64).t(),      # not contiguous
+           torch.zeros((7, 2), dtype=torch.float64)]          # wrong size
+    for t in bad:
+        with pytest.raises(fb.FbimError):
+            op.apply_stokeslet(t)
+        with pytest.raises(fb.FbimError):
+            op.apply_real_noalloc(t, t)
+    with pytest.raises(fb.FbimError):
+        op.mobility_solve(torch.zeros((2, 3), dtype=torch.float32))
+    with pytest.raises(fb.FbimError):
+        op.bd_step(torch.zeros((2, 3), dtype=torch.float64), torch.zeros((2, 3), dtype=torch.float64), 1e-3)
