@@ -17,7 +17,7 @@ with FP64 refinement; the plain form runs everything in FP64.  L2 is flushed
 The matvec alone (node-matvecs/s) and its per-stage times are measured too; the
 roofline object refers to the pair SpMV of the FP32 matvec (the step's top kernel).
 
-Two further measurements ride along (``--legs``): ``batched`` runs 64
+Further measurements ride along (``--legs``): ``batched`` runs 64
 independent suspensions (16-512 bodies, 96 nodes each, area fractions
 0.1-0.35) through the graph-captured batch: 8 batched Brownian slips per
 suspension, solved with forces, and the RFD +- pair (handles moved to
@@ -25,9 +25,9 @@ Q +- delta/2 W~) in the same batched solve; and
 ``learned`` times the mobility solve of a dense 4096-body suspension (area
 fraction 0.40) with and without the learned coarse level.
 
-An opt-in leg (``--legs diffusion``) runs the free diffusion of a four-fold starfish
-in the unit cell (Sec. 4.4.1) as 64 batched trajectories with and without the random
-finite difference and reports the equilibrium statistics.
+A third leg (``diffusion``) runs the free diffusion of a four-fold starfish in the unit
+cell (Sec. 4.4.1) as 64 batched trajectories with and without the random finite
+difference and reports the equilibrium statistics.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
 instead, on a bounded sample of the same workload.
@@ -672,10 +672,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--r-c", type=float, default=0.0, help="pin the chosen form's cutoff (default: split tuner)")
     ap.add_argument("--grid", type=int, default=0, help="pin the chosen form's FFT grid side (default: tuner)")
-    ap.add_argument("--legs", default="batched,learned",
+    ap.add_argument("--legs", default="batched,learned,diffusion",
                     help="extra measurements: batched (independent suspensions), learned (coarse level), "
-                         "diffusion (free-diffusion statistics, not in the default set); '' for none")
-    ap.add_argument("--diffusion-steps", type=int, default=400, help="steps per trajectory of the diffusion leg")
+                         "diffusion (free-diffusion statistics); 'none' for none")
+    ap.add_argument("--diffusion-steps", type=int, default=500, help="steps per trajectory of the diffusion leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
